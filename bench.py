@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of inexact policy iteration on the banded 4M-state MDP.
+
+Workload (seeded, synthetic): n = 2^22 states, m = 8 actions, 16 successors
+per (s, a) drawn without replacement from the clipped band [s-4096, s+4096],
+Dirichlet(0.5) probabilities (FP32), g ~ U[0,1], gamma = 0.99; 536,870,912
+nonzeros (4.3 GB of col+val, larger than the 129 MB L2).
+
+One step = one mdp_solve from V = 0 to a Bellman residual ||TV - V||_inf <= 1e-9
+(float-float outer iterate, GMRES(30) inner solves to 0.1 ||TV - V||_inf).
+Metric: effective transitions/s = nonzeros touched per second, with every
+Bellman sweep counted at nnz and every policy-row SpMV at the policy's nnz.
+
+Prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
+timed instead (Bellman sweeps over a bounded sample of the same workload).
+Under torchrun each rank solves its own replica (weak scaling, no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective transitions/s (nnz*iters/s)"
+UNIT = "transitions/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=None, help="state count override (same recipe)")
+    p.add_argument("--tol", type=float, default=1e-9)
+    p.add_argument("--restart", type=int, default=30)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--profile-bellman", type=int, default=0,
+                   help="only run N float-float Bellman backups (for ncu captures)")
+    p.add_argument("--profile-solve", action="store_true",
+                   help="one solve, nothing else (for ncu launch lists)")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _workload(n=None, s0=0, s1=None):
+    import synth
+    return synth.banded_4m(n=n, s0=s0, s1=s1)
+
+
+def _cpu_sample_bellman(n, seconds, s1=1 << 18):
+    """Time the FP64 oracle's Bellman sweep on states [0, s1) of the workload."""
+    import oracle
+    blk = _workload(n=n, s0=0, s1=min(s1, n if n else 1 << 22))
+    V = np.random.default_rng(0).random(blk.n) * 100
+    oracle.bellman(blk, V)  # load + warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.bellman(blk, V)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return dict(value=blk.nnz * reps / el, unit=UNIT, cores=int(omp) if omp else cores,
+                kind="oracle",
+                sample=(f"FP64 oracle Bellman sweep (T V with greedy argmin) over states "
+                        f"[0, {blk.n_local}) of the workload ({blk.nnz} nnz), {reps} sweeps, "
+                        f"{el:.1f} s"))
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    n = args.n
+    blk = _workload(n=n, s0=0, s1=min(1 << 18, n if n else 1 << 22))
+    V = np.random.default_rng(0).random(blk.n) * 100
+    for _ in range(max(args.warmup, 0)):
+        oracle.bellman(blk, V)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        TV, _ = oracle.bellman(blk, V)
+    el = time.perf_counter() - t0
+    value = blk.nnz * args.steps / el
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"FP64 oracle Bellman sweep over states [0, {blk.n_local}) of the banded "
+              f"workload ({blk.nnz} nnz) per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": blk.name, "n_states": 1 << 22 if n is None else n, "m": 8,
+                       "successors": 16, "band": 4096, "gamma": 0.99, "seed": 2,
+                       "sample_states": blk.n_local},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2502_14474_gb300 import MDP, capi
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    host = _workload(n=args.n)
+    nnz = host.nnz
+    h = MDP.from_csr(host)
+    dev = torch.device("cuda", local)
+    opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart)
+
+    if args.profile_bellman:
+        V = torch.zeros(host.n, dtype=torch.float64, device=dev)
+        for _ in range(args.profile_bellman):
+            out = h.bellman(V, want_v=True, want_pi=True, want_r=True)
+            V = out["V"]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_bellman": args.profile_bellman, "res_inf": out["res_inf"]}))
+        return 0
+    if args.profile_solve:
+        _, _, st = h.solve(**opts)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_solve": st}))
+        return 0
+
+    # ---- warm-up -------------------------------------------------------------
+    for _ in range(args.warmup):
+        V, pi, st = h.solve(**opts)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K full solves, per-kernel events on the solve stream ----
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+                           if ws == 1 else local)
+    h.profile(True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        V, pi, st = h.solve(**opts)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = h.profile_read()
+    h.profile(False)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    trans = sum(s["transitions"] for s in stats)
+    value = trans * ws / (ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel (largest event-timed total) ----------
+    kinds = prof["kinds"]
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    dk = kinds[dom]
+    peak, peak_src = _peaks()
+    achieved = (dk["bytes"] / dk["launches"]) / (dk["ms"] / dk["launches"] / 1e3) / 1e9 \
+        if dk["launches"] else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None,
+                "bytes_per_launch": dk["bytes"] / max(1, dk["launches"]),
+                "ms_per_launch": dk["ms"] / max(1, dk["launches"]),
+                "launches": dk["launches"]}
+    per_kernel = {k: {"launches": v["launches"], "skipped": v["skipped"],
+                      "ms_total": round(v["ms"], 3),
+                      "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"]
+                      else None}
+                  for k, v in kinds.items() if v["launches"] or v["skipped"]}
+
+    # ---- end to end through the public API with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        hp = {k: pin(getattr(host, k)) for k in ("row_ptr", "col", "val", "g")}
+        Vh = torch.empty(host.n, dtype=torch.float64).pin_memory()
+        pih = torch.empty(host.n, dtype=torch.int32).pin_memory()
+        h.close()
+        h = None
+        torch.cuda.empty_cache()
+        h2d = sum(x.numel() * x.element_size() for x in hp.values())
+        d2h = Vh.numel() * 8 + pih.numel() * 4
+        e2e_steps = max(1, min(args.steps, 3))
+
+        def one():
+            m = MDP(host.n, host.m, hp["row_ptr"].numpy(), hp["col"].numpy(), hp["val"].numpy(),
+                    hp["g"].numpy(), host.gamma)
+            Vd, pid, s = m.solve(**opts)
+            Vh.copy_(Vd, non_blocking=True)
+            pih.copy_(pid, non_blocking=True)
+            torch.cuda.synchronize()
+            m.close()
+            return s
+        one()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        tr = 0.0
+        for _ in range(e2e_steps):
+            tr += one()["transitions"]
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": tr * ws / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "ms_per_step": float(te.item()) / e2e_steps * 1e3}
+    if h is not None:
+        h.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_sample_bellman(args.n, args.cpu_seconds)
+
+    if rank == 0:
+        st0 = stats[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": host.name, "n_states": host.n, "m": host.m, "nnz": nnz,
+                       "successors": 16, "band": 4096, "gamma": host.gamma, "seed": 2,
+                       "tol": args.tol, "inner": f"gmres({args.restart})", "eta": 0.1,
+                       "outer_iterate": "float-float (hi+lo FP32)", "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{ws}"},
+            "time_to_tol_s": ms_max / args.steps / 1e3,
+            "solve": {"outer_iters": st0["outer_iters"], "inner_iters": st0["inner_iters"],
+                      "bellman_sweeps": st0["bellman_sweeps"],
+                      "policy_sweeps": st0["policy_sweeps"],
+                      "residual_inf": st0["residual_inf"],
+                      "transitions_per_solve": st0["transitions"],
+                      "residual_history": st0["residual_history"],
+                      "inner_history": st0["inner_history"]},
+            "roofline": roofline,
+            "kernels": per_kernel,
+            "gpu_launches": prof["total_launches"],
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -46,6 +47,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile oracle.c (gcc -O2, OpenMP over states; the sums stay sequential)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    stamp = os.path.join(_OUT_DIR, "HOST_ARCH")
+    if not (os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()):
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH

@@ -1,0 +1,277 @@
+"""ctypes binding of the C ABI in include/mdp.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of its own: all work runs in the CUDA library.  Array arguments
+are torch tensors (their data pointers are passed) or raw integer addresses.
+A non-OK status raises MDPError carrying mdp_last_error().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MDP_F32, MDP_F64, MDP_BF16, MDP_F16 = 0, 1, 2, 3
+MDP_OK = 0
+STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_ARG", 2: "MDP_ERR_NOT_STOCHASTIC", 3: "MDP_ERR_OOM",
+                4: "MDP_ERR_CUDA", 5: "MDP_ERR_NOT_CONVERGED", 6: "MDP_ERR_TIMEOUT",
+                7: "MDP_ERR_CANCELLED", 8: "MDP_ERR_BAD_CSR", 9: "MDP_ERR_NONFINITE"}
+MDP_FLAG_HOST_INPUT = 0x1
+MDP_FLAG_NO_VALIDATE = 0x2
+MDP_INNER_GMRES, MDP_INNER_RICHARDSON = 0, 1
+MDP_HISTORY = 128
+
+# Every symbol include/mdp.h declares (checked by the tests).
+EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
+                   "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
+                   "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read"])
+
+PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
+              "gmres_update", "richardson", "other"]
+
+
+class MDPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        self.status_name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{self.status_name}: {msg}")
+
+
+class mdp_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
+                ("restart", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("max_inner", ctypes.c_int32), ("inner", ctypes.c_int32),
+                ("cgs2", ctypes.c_int32), ("low_precision_inner", ctypes.c_int32)]
+
+
+class mdp_solve_stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("bellman_sweeps", ctypes.c_int32), ("policy_sweeps", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("n_history", ctypes.c_int32),
+                ("residual_inf", ctypes.c_double), ("transitions", ctypes.c_double),
+                ("residual_history", ctypes.c_double * MDP_HISTORY),
+                ("inner_history", ctypes.c_int32 * MDP_HISTORY)]
+
+    def as_dict(self):
+        k = self.n_history
+        return dict(outer_iters=self.outer_iters, inner_iters=self.inner_iters,
+                    bellman_sweeps=self.bellman_sweeps, policy_sweeps=self.policy_sweeps,
+                    converged=bool(self.converged), residual_inf=self.residual_inf,
+                    transitions=self.transitions,
+                    residual_history=list(self.residual_history[:k]),
+                    inner_history=list(self.inner_history[:max(0, self.outer_iters)]))
+
+
+class mdp_eval_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("policy_sweeps", ctypes.c_int32),
+                ("residual_2", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, cycles=self.cycles, converged=bool(self.converged),
+                    policy_sweeps=self.policy_sweeps, residual_2=self.residual_2)
+
+
+class mdp_info_t(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_int64), ("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_actions", ctypes.c_int32), ("vec_width", ctypes.c_int32),
+                ("uniform_len", ctypes.c_int32), ("idx64", ctypes.c_int32),
+                ("band", ctypes.c_int64), ("has_low_precision", ctypes.c_int32),
+                ("store_t", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+                ("gamma", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mdp_profile_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("skipped", ctypes.c_int64 * 8),
+                ("ms", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8),
+                ("total_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        kinds = {}
+        for i, name in enumerate(PROF_KINDS):
+            kinds[name] = dict(launches=self.launches[i], skipped=self.skipped[i],
+                               ms=self.ms[i], bytes=self.bytes[i])
+        return dict(kinds=kinds, total_launches=self.total_launches)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libmdp_gb300.so (building it with nvcc first if it is missing).
+
+    Raises if the library cannot be built or loaded: there is no fallback.
+    """
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                               "paper_2502_14474_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P, I32, I64, D, U64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                               ctypes.c_uint64)
+        lib.mdp_create.argtypes = [ctypes.POINTER(P), I64, I32, P, P, P, ctypes.c_int, P,
+                                   ctypes.c_int, D, ctypes.c_int, P, U64]
+        lib.mdp_create.restype = ctypes.c_int
+        lib.mdp_destroy.argtypes = [P]
+        lib.mdp_destroy.restype = None
+        lib.mdp_bellman.argtypes = [P, P, ctypes.c_int, P, P, P, ctypes.POINTER(D),
+                                    ctypes.POINTER(D), P]
+        lib.mdp_bellman.restype = ctypes.c_int
+        lib.mdp_policy_eval.argtypes = [P, P, P, ctypes.c_int, D, I32, I32,
+                                        ctypes.POINTER(mdp_eval_stats), P]
+        lib.mdp_policy_eval.restype = ctypes.c_int
+        lib.mdp_default_opts.argtypes = [ctypes.POINTER(mdp_solve_opts)]
+        lib.mdp_default_opts.restype = None
+        lib.mdp_solve.argtypes = [P, ctypes.POINTER(mdp_solve_opts), P, ctypes.c_int, P, P,
+                                  ctypes.POINTER(mdp_solve_stats), P]
+        lib.mdp_solve.restype = ctypes.c_int
+        lib.mdp_info.argtypes = [P, ctypes.POINTER(mdp_info_t)]
+        lib.mdp_info.restype = ctypes.c_int
+        lib.mdp_bytes_required.argtypes = [I64, I32, I64, ctypes.c_int, ctypes.c_int, I32]
+        lib.mdp_bytes_required.restype = ctypes.c_size_t
+        lib.mdp_cancel.argtypes = [P]
+        lib.mdp_cancel.restype = None
+        lib.mdp_profile_enable.argtypes = [P, ctypes.c_int]
+        lib.mdp_profile_enable.restype = ctypes.c_int
+        lib.mdp_profile_read.argtypes = [P, ctypes.POINTER(mdp_profile_t)]
+        lib.mdp_profile_read.restype = ctypes.c_int
+        lib.mdp_last_error.argtypes = []
+        lib.mdp_last_error.restype = ctypes.c_char_p
+        lib.mdp_version.argtypes = []
+        lib.mdp_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Data pointer of a tensor / numpy array, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int):
+    if rc != MDP_OK:
+        msg = load().mdp_last_error().decode(errors="replace")
+        raise MDPError(rc, msg)
+
+
+def mdp_last_error() -> str:
+    return load().mdp_last_error().decode(errors="replace")
+
+
+def mdp_version() -> str:
+    return load().mdp_version().decode()
+
+
+def mdp_create(n_states, n_actions, row_ptr, col, val, val_t, cost, cost_t, gamma, store_t,
+               stream=None, flags=0):
+    """Returns the handle (an integer address)."""
+    h = ctypes.c_void_p()
+    rc = load().mdp_create(ctypes.byref(h), int(n_states), int(n_actions), _ptr(row_ptr),
+                           _ptr(col), _ptr(val), int(val_t), _ptr(cost), int(cost_t), float(gamma),
+                           int(store_t), _stream(stream), int(flags))
+    _check(rc)
+    return h.value
+
+
+def mdp_destroy(h):
+    if h:
+        load().mdp_destroy(h)
+
+
+def mdp_bellman(h, V_in, v_t, V_out=None, pi_out=None, r_out=None, want_norms=True,
+                stream=None):
+    """Returns (res_inf, res_2) when want_norms, else None."""
+    ri, r2 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().mdp_bellman(h, _ptr(V_in), int(v_t), _ptr(V_out), _ptr(pi_out), _ptr(r_out),
+                            ctypes.byref(ri) if want_norms else None,
+                            ctypes.byref(r2) if want_norms else None, _stream(stream))
+    _check(rc)
+    return (ri.value, r2.value) if want_norms else None
+
+
+def mdp_policy_eval(h, pi, v_inout, v_t, tol, restart=30, max_iters=10000, stream=None,
+                    raise_on_not_converged=True):
+    st = mdp_eval_stats()
+    rc = load().mdp_policy_eval(h, _ptr(pi), _ptr(v_inout), int(v_t), float(tol), int(restart),
+                                int(max_iters), ctypes.byref(st), _stream(stream))
+    if rc != MDP_OK and not (rc == 5 and not raise_on_not_converged):
+        _check(rc)
+    d = st.as_dict()
+    d["status"] = STATUS_NAMES.get(rc, rc)
+    return d
+
+
+def mdp_default_opts() -> mdp_solve_opts:
+    o = mdp_solve_opts()
+    load().mdp_default_opts(ctypes.byref(o))
+    return o
+
+
+def mdp_solve(h, opts=None, V_init=None, vinit_t=MDP_F64, V_out=None, pi_out=None, stream=None,
+              raise_on_not_converged=True):
+    st = mdp_solve_stats()
+    rc = load().mdp_solve(h, ctypes.byref(opts) if opts is not None else None, _ptr(V_init),
+                          int(vinit_t), _ptr(V_out), _ptr(pi_out), ctypes.byref(st),
+                          _stream(stream))
+    if rc != MDP_OK and not (rc == 5 and not raise_on_not_converged):
+        _check(rc)
+    d = st.as_dict()
+    d["status"] = STATUS_NAMES.get(rc, rc)
+    return d
+
+
+def mdp_info(h) -> dict:
+    info = mdp_info_t()
+    _check(load().mdp_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def mdp_bytes_required(n_states, n_actions, nnz, val_t=MDP_F32, store_t=MDP_F32, restart=30):
+    return int(load().mdp_bytes_required(int(n_states), int(n_actions), int(nnz), int(val_t),
+                                         int(store_t), int(restart)))
+
+
+def mdp_cancel(h):
+    load().mdp_cancel(h)
+
+
+def mdp_profile_enable(h, on=True):
+    _check(load().mdp_profile_enable(h, 1 if on else 0))
+
+
+def mdp_profile_read(h) -> dict:
+    p = mdp_profile_t()
+    _check(load().mdp_profile_read(h, ctypes.byref(p)))
+    return p.as_dict()

@@ -1,0 +1,890 @@
+// C ABI of the solver (include/mdp.h): handle management and the host-side
+// drivers of policy evaluation (restarted GMRES) and inexact policy iteration.
+//
+// The host enqueues kernels asynchronously and synchronises only where a
+// decision needs a scalar: once per outer iteration (the Bellman residual)
+// and once per GMRES restart cycle (its step count and convergence flag).
+// Within a cycle the kernels decide on the device (DevState::active).
+#include <stddef.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/mdp.h"
+#include "launch.h"
+
+using namespace mdpk;
+
+namespace {
+
+thread_local std::string g_err;
+
+mdp_status fail(mdp_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mdp_status fail(mdp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Prefix of DevState that the host reads back after a synchronisation.
+struct StatusHead {
+  unsigned counter[kNumCounters];
+  double res_inf;
+  double res_2;
+  int active, jdone, converged, breakdown, restart, target_rel;
+  double eta, target, beta, est;
+};
+static_assert(offsetof(StatusHead, est) == offsetof(DevState, est), "DevState prefix layout");
+constexpr size_t kHeadBytes = sizeof(StatusHead);
+
+struct ProfRec {
+  int kind;
+  int j;          // Arnoldi step of K2/K3 launches, -1 otherwise
+  bool skipped;   // the launch returned at once (its GMRES cycle was over)
+  double bytes;
+  cudaEvent_t a, b;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> free_ev;
+  std::vector<ProfRec> pending;
+  mdp_profile_t agg;
+};
+
+}  // namespace
+
+struct mdp_s {
+  int device = 0;
+  Mat A;
+  bool broken = false;
+  std::atomic<int> cancel{0};
+  // owned device memory
+  void* rp = nullptr;
+  int32_t* col = nullptr;
+  float* val = nullptr;
+  float* val_lo = nullptr;
+  float* g = nullptr;
+  float* g_lo = nullptr;
+  void* val16 = nullptr;
+  float* row_scale = nullptr;
+  float2* V = nullptr;      // float-float iterate
+  float2* W1 = nullptr;     // float-float scratch (mdp_bellman input)
+  float2* W2 = nullptr;     // float-float scratch (mdp_bellman output)
+  int32_t* pi = nullptr;    // policy buffer
+  float* basis = nullptr;   // (restart_cap + 1) x ld
+  int64_t ld = 0;
+  int restart_cap = 0;
+  float* d0 = nullptr;      // Richardson vectors
+  float* d1 = nullptr;
+  double* partials = nullptr;
+  DevState* st = nullptr;
+  int* flag = nullptr;      // policy range check
+  StatusHead* head = nullptr;  // pinned host mirror
+  size_t bytes = 0;
+  // analysis
+  int64_t band = 0;
+  int32_t min_len = 0, max_len = 0;
+  int aligned = 0;
+  int32_t store_t = MDP_F32;
+  int32_t val_t = MDP_F32;
+  Prof prof;
+  int64_t launches = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define CK(h, call)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      if (h) (h)->broken = true;                                                         \
+      return fail(MDP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+    }                                                                                    \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(mdp_s* h, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) {
+    *p = static_cast<T*>(q);
+    h->bytes += bytes;
+  }
+  return e;
+}
+
+// ---- profiling -------------------------------------------------------------
+cudaEvent_t ev_get(mdp_s* h) {
+  if (!h->prof.free_ev.empty()) {
+    cudaEvent_t e = h->prof.free_ev.back();
+    h->prof.free_ev.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Run one library launch call `f` (which issues `nlaunch` kernels) of the
+// given kind; with timing on, bracket it by events on the same stream.
+template <class F>
+cudaError_t run(mdp_s* h, cudaStream_t s, int kind, int nlaunch, double bytes, int j, F f) {
+  h->launches += nlaunch;
+  if (!h->prof.on) return f();
+  ProfRec r{kind, j, false, bytes, ev_get(h), ev_get(h)};
+  if (!r.a || !r.b) return f();
+  cudaEventRecord(r.a, s);
+  cudaError_t e = f();
+  cudaEventRecord(r.b, s);
+  h->prof.pending.push_back(r);
+  return e;
+}
+
+// Accumulate every pending record (their events must be complete).
+void prof_flush(mdp_s* h) {
+  for (ProfRec& r : h->prof.pending) {
+    if (r.skipped) {
+      h->prof.agg.skipped[r.kind] += 1;
+    } else {
+      float ms = 0.f;
+      cudaEventSynchronize(r.b);
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        h->prof.agg.ms[r.kind] += ms;
+        h->prof.agg.launches[r.kind] += 1;
+        h->prof.agg.bytes[r.kind] += r.bytes;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    h->prof.free_ev.push_back(r.a);
+    h->prof.free_ev.push_back(r.b);
+  }
+  h->prof.pending.clear();
+}
+
+// ---- algorithmic bytes per launch (gathers of the value vector excluded) ----
+double rp_bytes(const Mat& A) { return A.uniform_len > 0 ? 0.0 : (A.idx64 ? 8.0 : 4.0); }
+double policy_len(const Mat& A) {
+  return A.uniform_len > 0 ? A.uniform_len : static_cast<double>(A.nnz) / A.rows;
+}
+double bytes_bellman(const Mat& A, bool ff, bool v_out) {
+  const double n = A.n, rows = A.rows, nnz = A.nnz;
+  const double vb = ff ? 8.0 : 4.0;
+  return nnz * (8.0 + (A.val_lo ? 4.0 : 0.0)) + rows * (rp_bytes(A) + 4.0 + (A.g_lo ? 4.0 : 0.0)) +
+         n * (vb + 4.0 + 4.0 + (v_out ? vb : 0.0));
+}
+double bytes_policy_resid(const Mat& A) {
+  const double n = A.n;
+  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (8.0 + (A.val_lo ? 4.0 : 0.0)) + 4.0 +
+              (A.g_lo ? 4.0 : 0.0) + 8.0 + 4.0);
+}
+double bytes_spmv(const Mat& A, bool lp, int j) {
+  const double n = A.n;
+  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
+              (lp ? 4.0 : 0.0) + 4.0 + 4.0 + 4.0 * (j + 1));
+}
+double bytes_ortho(const Mat& A, int j, int cgs2) {
+  const double n = A.n;
+  const double one = 4.0 * (j + 1) * n + 8.0 * n;
+  return cgs2 ? 2.0 * one + 4.0 * (j + 2) * n : one;
+}
+double bytes_update(const Mat& A, int J) { return 4.0 * J * A.n + 16.0 * A.n; }
+double bytes_richardson(const Mat& A, bool lp) {
+  const double n = A.n;
+  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
+              (lp ? 4.0 : 0.0) + 12.0);
+}
+
+void free_all(mdp_s* h) {
+  void* ptrs[] = {h->rp, h->col, h->val, h->val_lo, h->g, h->g_lo, h->val16, h->row_scale,
+                  h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->head) cudaFreeHost(h->head);
+  for (ProfRec& r : h->prof.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : h->prof.free_ev) cudaEventDestroy(e);
+}
+
+#define ALLOC(h, p, bytes)                                                                      \
+  do {                                                                                          \
+    cudaError_t e_ = dalloc((h), &(p), (bytes));                                                \
+    if (e_ != cudaSuccess) {                                                                    \
+      cudaGetLastError();                                                                       \
+      return fail(MDP_ERR_OOM, "device allocation of %zu bytes failed: %s", (size_t)(bytes), \
+                  cudaGetErrorString(e_));                                                      \
+    }                                                                                           \
+  } while (0)
+
+size_t partials_len(int num_sms) { return static_cast<size_t>(num_sms) * 8 * (kMaxBasis + 1); }
+
+mdp_status ensure_basis(mdp_s* h, int restart) {
+  if (restart <= h->restart_cap && h->basis) return MDP_OK;
+  if (h->basis) {
+    cudaFree(h->basis);
+    h->bytes -= static_cast<size_t>(h->restart_cap + 1) * h->ld * sizeof(float);
+    h->basis = nullptr;
+  }
+  ALLOC(h, h->basis, static_cast<size_t>(restart + 1) * h->ld * sizeof(float));
+  h->restart_cap = restart;
+  return MDP_OK;
+}
+
+mdp_status ensure_richardson(mdp_s* h) {
+  if (h->d0) return MDP_OK;
+  ALLOC(h, h->d0, static_cast<size_t>(h->A.n) * sizeof(float));
+  ALLOC(h, h->d1, static_cast<size_t>(h->A.n) * sizeof(float));
+  return MDP_OK;
+}
+
+// Read the status prefix of the device state (synchronises the stream).
+mdp_status read_head(mdp_s* h, cudaStream_t s, bool flush = true) {
+  CK(h, cudaMemcpyAsync(h->head, h->st, kHeadBytes, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (flush) prof_flush(h);
+  return MDP_OK;
+}
+
+__global__ void k_set_cycle(DevState* st, int restart, int target_rel, double eta, double target,
+                            int set_target) {
+  st->restart = restart;
+  st->target_rel = target_rel;
+  st->eta = eta;
+  if (set_target) st->target = target;
+}
+
+__global__ void k_check_policy(int64_t n, int32_t m, const int32_t* __restrict__ pi, int* flag) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t a = pi[s];
+    if (a < 0 || a >= m) atomicOr(flag, 1);
+  }
+}
+
+mdp_status set_cycle(mdp_s* h, int restart, int target_rel, double eta, double target,
+                     int set_target, cudaStream_t s) {
+  CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+       k_set_cycle<<<1, 1, 0, s>>>(h->st, restart, target_rel, eta, target, set_target);
+       return cudaGetLastError();
+     }));
+  return MDP_OK;
+}
+
+mdp_status check_policy(mdp_s* h, const int32_t* pi, cudaStream_t s) {
+  CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+  unsigned nb = static_cast<unsigned>(std::min<int64_t>((h->A.n + 255) / 256, h->A.num_sms * 8));
+  CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+       k_check_policy<<<nb, 256, 0, s>>>(h->A.n, h->A.m, pi, h->flag);
+       return cudaGetLastError();
+     }));
+  int f = 0;
+  CK(h, cudaMemcpyAsync(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (f) return fail(MDP_ERR_ARG, "policy has an action outside [0, %d)", h->A.m);
+  return MDP_OK;
+}
+
+// One GMRES restart cycle on the current device residual (already in u_0 with
+// the cycle begun by the kernel that produced it).  Enqueues up to `steps`
+// Arnoldi steps and the solution update, then reads the cycle's outcome.
+mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+                       cudaStream_t s, int* jdone, int* converged) {
+  const size_t first = h->prof.pending.size();
+  for (int j = 0; j < steps; ++j) {
+    CK(h, run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp, j), j, [&] {
+         return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
+       }));
+    CK(h, run(h, s, MDP_PROF_ARNOLDI_ORTHO, cgs2 ? 3 : 1, bytes_ortho(h->A, j, cgs2), j, [&] {
+         return launch_arnoldi_ortho(h->A, h->basis, h->ld, j, steps, cgs2, h->partials, h->st, s);
+       }));
+  }
+  const size_t upd = h->prof.pending.size();
+  CK(h, run(h, s, MDP_PROF_GMRES_UPDATE, 1, 0.0, -1, [&] {
+       return launch_gmres_update(h->A, h->basis, h->ld, h->V, h->st, s);
+     }));
+  mdp_status rc = read_head(h, s, false);
+  if (rc != MDP_OK) return rc;
+  *jdone = h->head->jdone;
+  *converged = h->head->converged;
+  // launches of steps past the end of the cycle returned at once
+  for (size_t i = first; i < h->prof.pending.size(); ++i) {
+    ProfRec& r = h->prof.pending[i];
+    if (r.j >= *jdone) r.skipped = true;
+    if (i == upd) {
+      r.bytes = bytes_update(h->A, *jdone);
+      r.skipped = *jdone == 0;
+    }
+  }
+  prof_flush(h);
+  return MDP_OK;
+}
+
+bool dtype_ok_vec(mdp_dtype t) { return t == MDP_F32 || t == MDP_F64; }
+
+int pow2_floor(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mdp_last_error(void) { return g_err.c_str(); }
+
+const char* mdp_version(void) { return "mdp-gb300 0.1 (sm_103a)"; }
+
+void mdp_default_opts(mdp_solve_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-9;
+  o->inner_rtol = 0.1;
+  o->restart = 30;
+  o->max_outer = 1000;
+  o->max_inner = 10000;
+  o->inner = MDP_INNER_GMRES;
+  o->cgs2 = 0;
+  o->low_precision_inner = 0;
+}
+
+size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, mdp_dtype store_t,
+                          int32_t restart) {
+  if (n <= 0 || m <= 0 || nnz < 0) return 0;
+  const int64_t rows = n * m;
+  const bool idx64 = nnz >= (int64_t(1) << 31);
+  const int64_t ld = static_cast<int64_t>(round_up(static_cast<size_t>(n), 64));
+  size_t b = 0;
+  b += static_cast<size_t>(rows + 1) * (idx64 ? 8 : 4);
+  b += static_cast<size_t>(nnz) * (4 + 4 + (val_t == MDP_F64 ? 4 : 0));
+  b += static_cast<size_t>(rows) * 4 * 2;  // g (+ g_lo bound)
+  if (store_t == MDP_BF16 || store_t == MDP_F16) b += static_cast<size_t>(nnz) * 2 + rows * 4;
+  b += static_cast<size_t>(n) * (8 * 3 + 4);
+  b += static_cast<size_t>(restart + 1) * ld * 4;
+  b += sizeof(DevState) + (1 << 20);
+  return b;
+}
+
+mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
+                      const int32_t* col, const void* val, mdp_dtype val_t, const void* cost,
+                      mdp_dtype cost_t, double gamma, mdp_dtype store_t, void* stream,
+                      uint64_t flags) {
+  if (!out) return fail(MDP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || m <= 0) return fail(MDP_ERR_ARG, "n_states and n_actions must be >= 1");
+  if (n > (int64_t(1) << 31) - 1) return fail(MDP_ERR_ARG, "n_states must fit int32 columns");
+  if (n > INT64_MAX / m) return fail(MDP_ERR_ARG, "n_states * n_actions overflows");
+  if (!row_ptr || !col || !val || !cost) return fail(MDP_ERR_ARG, "NULL array argument");
+  if (!dtype_ok_vec(val_t) || !dtype_ok_vec(cost_t))
+    return fail(MDP_ERR_ARG, "val_t and cost_t must be MDP_F32 or MDP_F64");
+  if (store_t != MDP_F32 && store_t != MDP_BF16 && store_t != MDP_F16)
+    return fail(MDP_ERR_ARG, "store_t must be MDP_F32, MDP_BF16 or MDP_F16");
+  if (!(gamma >= 0.0 && gamma < 1.0)) return fail(MDP_ERR_ARG, "gamma must be in [0, 1)");
+  const bool host_in = (flags & MDP_FLAG_HOST_INPUT) != 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t rows = n * m;
+
+  mdp_s* h = new mdp_s();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(MDP_ERR_CUDA, "no CUDA device");
+  }
+  auto bail = [&](mdp_status st) {
+    free_all(h);
+    delete h;
+    return st;
+  };
+  int num_sms = 1;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device);
+
+  // nnz from the last row pointer
+  int64_t nnz = 0;
+  if (host_in) {
+    nnz = row_ptr[rows];
+  } else {
+    if (cudaMemcpy(&nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(MDP_ERR_ARG, "row_ptr is not a readable device pointer"));
+    }
+  }
+  if (nnz < rows) return bail(fail(MDP_ERR_NOT_STOCHASTIC, "nnz < n*m: some row is empty"));
+  const int idx64 = nnz >= (int64_t(1) << 31) ? 1 : 0;
+
+  // staging of host inputs
+  const int64_t* rp_in = row_ptr;
+  const int32_t* col_in = col;
+  const void* val_in = val;
+  const void* g_in = cost;
+  void* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto free_tmp = [&]() {
+    for (void*& p : tmp)
+      if (p) {
+        cudaFree(p);
+        p = nullptr;
+      }
+  };
+  const size_t vbytes = static_cast<size_t>(nnz) * (val_t == MDP_F64 ? 8 : 4);
+  const size_t gbytes = static_cast<size_t>(rows) * (cost_t == MDP_F64 ? 8 : 4);
+  if (host_in) {
+    const size_t sz[4] = {static_cast<size_t>(rows + 1) * 8, static_cast<size_t>(nnz) * 4, vbytes,
+                          gbytes};
+    const void* src[4] = {row_ptr, col, val, cost};
+    for (int i = 0; i < 4; ++i) {
+      if (cudaMalloc(&tmp[i], sz[i]) != cudaSuccess) {
+        cudaGetLastError();
+        free_tmp();
+        return bail(fail(MDP_ERR_OOM, "staging allocation failed"));
+      }
+      if (cudaMemcpyAsync(tmp[i], src[i], sz[i], cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        free_tmp();
+        return bail(fail(MDP_ERR_CUDA, "host to device copy failed"));
+      }
+    }
+    rp_in = static_cast<const int64_t*>(tmp[0]);
+    col_in = static_cast<const int32_t*>(tmp[1]);
+    val_in = tmp[2];
+    g_in = tmp[3];
+  }
+
+#define CALLOC(p, bytes)                                                          \
+  do {                                                                            \
+    if (dalloc(h, &(p), (bytes)) != cudaSuccess) {                               \
+      cudaGetLastError();                                                         \
+      free_tmp();                                                                 \
+      return bail(fail(MDP_ERR_OOM, "device allocation of %zu bytes failed",      \
+                       (size_t)(bytes)));                                         \
+    }                                                                             \
+  } while (0)
+#define CCK(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      free_tmp();                                                                 \
+      return bail(fail(MDP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)));   \
+    }                                                                             \
+  } while (0)
+
+  CALLOC(h->rp, static_cast<size_t>(rows + 1) * (idx64 ? 8 : 4));
+  CALLOC(h->col, static_cast<size_t>(nnz) * 4);
+  CALLOC(h->val, static_cast<size_t>(nnz) * 4);
+  if (val_t == MDP_F64) CALLOC(h->val_lo, static_cast<size_t>(nnz) * 4);
+  CALLOC(h->g, static_cast<size_t>(rows) * 4);
+  if (cost_t == MDP_F64) CALLOC(h->g_lo, static_cast<size_t>(rows) * 4);
+  PrepFlags* dflags = nullptr;
+  CALLOC(dflags, sizeof(PrepFlags));
+  PrepFlags init;
+  memset(&init, 0, sizeof(init));
+  init.min_len = 0x7fffffff;
+  CCK(cudaMemcpyAsync(dflags, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CCK(cudaMemcpyAsync(h->col, col_in, static_cast<size_t>(nnz) * 4, cudaMemcpyDeviceToDevice, s));
+  const double tol = (flags & MDP_FLAG_NO_VALIDATE) ? INFINITY : 1e-5;
+  CCK(launch_prep_rows(n, m, rp_in, h->col, val_in, val_t == MDP_F64, g_in, cost_t == MDP_F64,
+                       tol, h->rp, idx64, h->g, h->g_lo, dflags, num_sms, s));
+  CCK(launch_prep_vals(nnz, val_in, val_t == MDP_F64, h->val, h->val_lo, num_sms, s));
+  PrepFlags fl;
+  CCK(cudaMemcpyAsync(&fl, dflags, sizeof(fl), cudaMemcpyDeviceToHost, s));
+  CCK(cudaStreamSynchronize(s));
+  cudaFree(dflags);
+  h->bytes -= sizeof(PrepFlags);
+  free_tmp();
+  if (fl.bad_csr)
+    return bail(fail(MDP_ERR_BAD_CSR, "row_ptr not monotone from 0 or a column outside [0, n)"));
+  if (fl.nonfinite) return bail(fail(MDP_ERR_NONFINITE, "NaN or Inf in probabilities or costs"));
+  if (fl.negative) return bail(fail(MDP_ERR_NOT_STOCHASTIC, "negative probability"));
+  if (fl.not_stochastic)
+    return bail(fail(MDP_ERR_NOT_STOCHASTIC,
+                     "a row of P is empty or sums to 1 +- %.3g (max error %.3g)", tol,
+                     fl.max_sum_err));
+
+  Mat& A = h->A;
+  A.n = n;
+  A.rows = rows;
+  A.nnz = nnz;
+  A.m = m;
+  A.idx64 = idx64;
+  A.rp = h->rp;
+  A.col = h->col;
+  A.val = h->val;
+  A.val_lo = h->val_lo;
+  A.g = h->g;
+  A.g_lo = h->g_lo;
+  A.gamma = gamma;
+  A.num_sms = num_sms;
+  h->min_len = fl.min_len;
+  h->max_len = fl.max_len;
+  h->band = static_cast<int64_t>(fl.band);
+  h->aligned = fl.not_aligned ? 0 : 1;
+  h->val_t = val_t;
+  A.uniform_len = (fl.min_len == fl.max_len) ? fl.min_len : 0;
+  // lanes per row: about 4 entries per lane with 16-byte loads for rows of 12+
+  // entries, one entry per lane below that
+  const double mean = static_cast<double>(nnz) / static_cast<double>(rows);
+  A.vec4 = mean >= 12.0 ? 1 : 0;
+  int vw = pow2_floor(std::max(1, static_cast<int>(std::lround(A.vec4 ? mean / 4.0 : mean))));
+  A.vw = std::min(32, std::max(1, vw));
+
+  h->store_t = store_t;
+  A.store_t = store_t;
+  if (store_t == MDP_BF16 || store_t == MDP_F16) {
+    CALLOC(h->val16, static_cast<size_t>(nnz) * 2);
+    CALLOC(h->row_scale, static_cast<size_t>(rows) * 4);
+    CCK(launch_prep_lowp(A, h->val16, h->row_scale, store_t, s));
+    A.val16 = h->val16;
+    A.row_scale = h->row_scale;
+  }
+
+  // work memory
+  h->ld = static_cast<int64_t>(round_up(static_cast<size_t>(n), 64));
+  CALLOC(h->V, static_cast<size_t>(n) * sizeof(float2));
+  CALLOC(h->W1, static_cast<size_t>(n) * sizeof(float2));
+  CALLOC(h->W2, static_cast<size_t>(n) * sizeof(float2));
+  CALLOC(h->pi, static_cast<size_t>(n) * sizeof(int32_t));
+  CALLOC(h->partials, partials_len(num_sms) * sizeof(double));
+  CALLOC(h->st, sizeof(DevState));
+  CALLOC(h->flag, sizeof(int));
+  CCK(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
+  if (cudaMallocHost(&h->head, kHeadBytes) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(MDP_ERR_OOM, "pinned host allocation failed"));
+  }
+  if (ensure_basis(h, 30) != MDP_OK) return bail(MDP_ERR_OOM);
+  CCK(cudaStreamSynchronize(s));
+#undef CALLOC
+#undef CCK
+  *out = h;
+  return MDP_OK;
+}
+
+void mdp_destroy(mdp_t h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+void mdp_cancel(mdp_t h) {
+  if (h) h->cancel.store(1);
+}
+
+mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
+  if (!h || !info) return fail(MDP_ERR_ARG, "NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->n_states = h->A.n;
+  info->n_rows = h->A.rows;
+  info->nnz = h->A.nnz;
+  info->n_actions = h->A.m;
+  info->vec_width = h->A.vw;
+  info->uniform_len = h->A.uniform_len;
+  info->idx64 = h->A.idx64;
+  info->band = h->band;
+  info->has_low_precision = h->val16 != nullptr;
+  info->store_t = h->store_t;
+  info->device_bytes = h->bytes;
+  info->gamma = h->A.gamma;
+  return MDP_OK;
+}
+
+mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, int32_t* pi_out,
+                       float* r_out, double* res_inf, double* res_2, void* stream) {
+  if (!h) return fail(MDP_ERR_ARG, "NULL handle");
+  if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
+  if (!V_in) return fail(MDP_ERR_ARG, "V_in is NULL");
+  if (!dtype_ok_vec(v_t)) return fail(MDP_ERR_ARG, "v_t must be MDP_F32 or MDP_F64");
+  if (V_out && V_out == V_in) return fail(MDP_ERR_ARG, "V_out must not alias V_in");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (v_t == MDP_F32) {
+    CK(h, run(h, s, MDP_PROF_BELLMAN_F32, 1, bytes_bellman(h->A, false, V_out != nullptr), -1, [&] {
+         return launch_bellman(h->A, false, V_in, V_out, pi_out, r_out, h->partials, h->st, 0, s);
+       }));
+  } else {
+    CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+              [&] { return launch_to_ff(h->A.n, V_in, 1, h->W1, h->A.num_sms, s); }));
+    CK(h, run(h, s, MDP_PROF_BELLMAN_FF, 1, bytes_bellman(h->A, true, V_out != nullptr), -1, [&] {
+         return launch_bellman(h->A, true, h->W1, V_out ? h->W2 : nullptr, pi_out, r_out,
+                               h->partials, h->st, 0, s);
+       }));
+    if (V_out)
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+                [&] { return launch_from_ff(h->A.n, h->W2, V_out, 1, h->A.num_sms, s); }));
+  }
+  if (res_inf || res_2) {
+    mdp_status rc = read_head(h, s);
+    if (rc != MDP_OK) return rc;
+    if (res_inf) *res_inf = h->head->res_inf;
+    if (res_2) *res_2 = h->head->res_2;
+  }
+  return MDP_OK;
+}
+
+mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype v_t, double tol,
+                           int32_t restart, int32_t max_iters, mdp_eval_stats* stats,
+                           void* stream) {
+  if (!h) return fail(MDP_ERR_ARG, "NULL handle");
+  if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
+  if (!pi || !v_inout) return fail(MDP_ERR_ARG, "NULL argument");
+  if (!dtype_ok_vec(v_t)) return fail(MDP_ERR_ARG, "v_t must be MDP_F32 or MDP_F64");
+  if (restart < 1 || restart > kMaxRestart) return fail(MDP_ERR_ARG, "restart must be in [1, 64]");
+  if (!(tol >= 0.0)) return fail(MDP_ERR_ARG, "tol must be >= 0");
+  if (max_iters < 0) return fail(MDP_ERR_ARG, "max_iters must be >= 0");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->cancel.store(0);
+  mdp_status rc = check_policy(h, pi, s);
+  if (rc != MDP_OK) return rc;
+  rc = ensure_basis(h, restart);
+  if (rc != MDP_OK) return rc;
+  CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+       return launch_to_ff(h->A.n, v_inout, v_t == MDP_F64, h->V, h->A.num_sms, s);
+     }));
+  rc = set_cycle(h, restart, 0, 0.0, tol, 1, s);
+  if (rc != MDP_OK) return rc;
+  mdp_eval_stats es;
+  memset(&es, 0, sizeof(es));
+  CK(h, run(h, s, MDP_PROF_POLICY_RESID, 1, bytes_policy_resid(h->A), -1, [&] {
+       return launch_policy_residual(h->A, pi, h->V, h->basis, h->partials, h->st, s);
+     }));
+  es.policy_sweeps = 1;
+  rc = read_head(h, s);
+  if (rc != MDP_OK) return rc;
+  double res = h->head->res_2;
+  mdp_status result = MDP_OK;
+  while (!(res <= tol)) {
+    if (es.iters >= max_iters) {
+      result = fail(MDP_ERR_NOT_CONVERGED, "policy evaluation hit max_iters=%d (residual %.3e)",
+                    max_iters, res);
+      break;
+    }
+    if (h->cancel.load()) {
+      result = fail(MDP_ERR_CANCELLED, "cancelled");
+      break;
+    }
+    const int steps = std::min(restart, max_iters - es.iters);
+    rc = set_cycle(h, steps, 0, 0.0, tol, 1, s);
+    if (rc != MDP_OK) return rc;
+    int jdone = 0, conv = 0;
+    rc = gmres_cycle(h, pi, steps, false, 0, s, &jdone, &conv);
+    if (rc != MDP_OK) return rc;
+    es.iters += jdone;
+    es.cycles += 1;
+    es.policy_sweeps += jdone;
+    // refinement residual of the updated iterate (also begins the next cycle)
+    CK(h, run(h, s, MDP_PROF_POLICY_RESID, 1, bytes_policy_resid(h->A), -1, [&] {
+         return launch_policy_residual(h->A, pi, h->V, h->basis, h->partials, h->st, s);
+       }));
+    es.policy_sweeps += 1;
+    rc = read_head(h, s);
+    if (rc != MDP_OK) return rc;
+    const double prev = res;
+    res = h->head->res_2;
+    if (jdone == 0 && !(res < prev)) {
+      result = fail(MDP_ERR_NOT_CONVERGED, "GMRES stagnated at residual %.3e", res);
+      break;
+    }
+  }
+  es.residual_2 = res;
+  es.converged = res <= tol;
+  CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+       return launch_from_ff(h->A.n, h->V, v_inout, v_t == MDP_F64, h->A.num_sms, s);
+     }));
+  CK(h, cudaStreamSynchronize(s));
+  prof_flush(h);
+  if (stats) *stats = es;
+  return result;
+}
+
+mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
+                     mdp_dtype vinit_t, double* V_out, int32_t* pi_out, mdp_solve_stats* stats,
+                     void* stream) {
+  if (!h) return fail(MDP_ERR_ARG, "NULL handle");
+  if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
+  if (!V_out) return fail(MDP_ERR_ARG, "V_out is NULL");
+  mdp_solve_opts o;
+  if (opts_in) o = *opts_in;
+  else mdp_default_opts(&o);
+  if (V_init && !dtype_ok_vec(vinit_t)) return fail(MDP_ERR_ARG, "vinit_t must be F32 or F64");
+  if (o.restart < 1 || o.restart > kMaxRestart) return fail(MDP_ERR_ARG, "restart in [1, 64]");
+  if (!(o.tol >= 0.0) || !(o.inner_rtol > 0.0)) return fail(MDP_ERR_ARG, "bad tolerances");
+  if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_ERR_ARG, "bad iteration limits");
+  if (o.inner != MDP_INNER_GMRES && o.inner != MDP_INNER_RICHARDSON)
+    return fail(MDP_ERR_ARG, "unknown inner solver");
+  const bool lp = o.low_precision_inner != 0;
+  if (lp && !h->val16) return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->cancel.store(0);
+  mdp_status rc = MDP_OK;
+  if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart);
+  else rc = ensure_richardson(h);
+  if (rc != MDP_OK) return rc;
+  const Mat& A = h->A;
+  if (V_init)
+    CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+         return launch_to_ff(A.n, V_init, vinit_t == MDP_F64, h->V, A.num_sms, s);
+       }));
+  else CK(h, cudaMemsetAsync(h->V, 0, static_cast<size_t>(A.n) * sizeof(float2), s));
+  rc = set_cycle(h, o.restart, 1, o.inner_rtol, 0.0, 0, s);
+  if (rc != MDP_OK) return rc;
+
+  mdp_solve_stats ss;
+  memset(&ss, 0, sizeof(ss));
+  const double policy_nnz =
+      A.uniform_len > 0 ? static_cast<double>(A.n) * A.uniform_len
+                        : static_cast<double>(A.nnz) / static_cast<double>(A.m);
+  double transitions = 0.0;
+  mdp_status result = MDP_OK;
+  for (int k = 0;; ++k) {
+    // improvement + high-precision residual (+ GMRES cycle start from r)
+    float* r_dst = o.inner == MDP_INNER_GMRES ? h->basis : reinterpret_cast<float*>(h->W1);
+    CK(h, run(h, s, MDP_PROF_BELLMAN_FF, 1, bytes_bellman(A, true, false), -1, [&] {
+         return launch_bellman(A, true, h->V, nullptr, h->pi, r_dst, h->partials, h->st,
+                               o.inner == MDP_INNER_GMRES ? 1 : 0, s);
+       }));
+    ss.bellman_sweeps += 1;
+    transitions += static_cast<double>(A.nnz);
+    rc = read_head(h, s);
+    if (rc != MDP_OK) return rc;
+    const double res = h->head->res_inf;
+    if (ss.n_history < MDP_HISTORY) ss.residual_history[ss.n_history++] = res;
+    ss.residual_inf = res;
+    if (res <= o.tol) {
+      ss.converged = 1;
+      break;
+    }
+    if (!std::isfinite(res)) {
+      result = fail(MDP_ERR_NOT_CONVERGED, "non-finite Bellman residual");
+      break;
+    }
+    if (k >= o.max_outer) {
+      result = fail(MDP_ERR_NOT_CONVERGED, "max_outer=%d reached (residual %.3e)", o.max_outer, res);
+      break;
+    }
+    if (h->cancel.load()) {
+      result = fail(MDP_ERR_CANCELLED, "cancelled");
+      break;
+    }
+    ss.outer_iters += 1;
+    const double target = o.inner_rtol * res;
+    int used = 0;
+    if (o.inner == MDP_INNER_GMRES) {
+      // the Bellman kernel began the first cycle: target = eta * res_inf
+      for (;;) {
+        const int steps = std::min(o.restart, o.max_inner - used);
+        if (steps != o.restart) {
+          rc = set_cycle(h, steps, 1, o.inner_rtol, 0.0, 0, s);
+          if (rc != MDP_OK) return rc;
+        }
+        int jdone = 0, conv = 0;
+        rc = gmres_cycle(h, h->pi, steps, lp, o.cgs2, s, &jdone, &conv);
+        if (rc != MDP_OK) return rc;
+        used += jdone;
+        ss.policy_sweeps += jdone;
+        transitions += policy_nnz * jdone;
+        if (conv || used >= o.max_inner || jdone == 0) break;
+        if (h->cancel.load()) break;
+        // refinement residual of the policy system, next cycle from it
+        CK(h, run(h, s, MDP_PROF_POLICY_RESID, 1, bytes_policy_resid(A), -1, [&] {
+             return launch_policy_residual(A, h->pi, h->V, h->basis, h->partials, h->st, s);
+           }));
+        ss.policy_sweeps += 1;
+        transitions += policy_nnz;
+        rc = read_head(h, s);
+        if (rc != MDP_OK) return rc;
+        if (!h->head->active) break;  // already below the target
+      }
+      if (o.restart != std::min(o.restart, o.max_inner)) {
+        rc = set_cycle(h, o.restart, 1, o.inner_rtol, 0.0, 0, s);
+        if (rc != MDP_OK) return rc;
+      }
+    } else {
+      // modified policy iteration in correction form: d_1 = r, d_{k+1} = r + gamma P_pi d_k;
+      // V + d_k equals T_pi^k V, and ||d_{k+1} - d_k||_2 is the residual of d_k.
+      const float* rsave = reinterpret_cast<const float*>(h->W1);
+      float* da = h->d0;
+      float* db = h->d1;
+      CK(h, cudaMemcpyAsync(da, rsave, static_cast<size_t>(A.n) * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s));
+      used = 1;
+      while (used < o.max_inner) {
+        CK(h, run(h, s, MDP_PROF_RICHARDSON, 1, bytes_richardson(A, lp), -1, [&] {
+             return launch_richardson(A, lp, h->pi, rsave, da, db, h->partials, h->st, s);
+           }));
+        used += 1;
+        ss.policy_sweeps += 1;
+        transitions += policy_nnz;
+        std::swap(da, db);
+        rc = read_head(h, s);
+        if (rc != MDP_OK) return rc;
+        if (h->head->res_2 <= target) break;
+      }
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+                [&] { return launch_ff_axpy(A.n, h->V, da, A.num_sms, s); }));
+    }
+    ss.inner_iters += used;
+    if (ss.outer_iters - 1 < MDP_HISTORY) ss.inner_history[ss.outer_iters - 1] = used;
+  }
+  CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+            [&] { return launch_from_ff(A.n, h->V, V_out, 1, A.num_sms, s); }));
+  if (pi_out)
+    CK(h, cudaMemcpyAsync(pi_out, h->pi, static_cast<size_t>(A.n) * sizeof(int32_t),
+                          cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaStreamSynchronize(s));
+  prof_flush(h);
+  ss.transitions = transitions;
+  if (stats) *stats = ss;
+  return result;
+}
+
+mdp_status mdp_profile_enable(mdp_t h, int on) {
+  if (!h) return fail(MDP_ERR_ARG, "NULL handle");
+  DeviceGuard dg(h->device);
+  for (ProfRec& r : h->prof.pending) cudaEventSynchronize(r.b);
+  prof_flush(h);
+  memset(&h->prof.agg, 0, sizeof(h->prof.agg));
+  h->launches = 0;
+  h->prof.on = on != 0;
+  return MDP_OK;
+}
+
+mdp_status mdp_profile_read(mdp_t h, mdp_profile_t* out) {
+  if (!h || !out) return fail(MDP_ERR_ARG, "NULL argument");
+  DeviceGuard dg(h->device);
+  for (ProfRec& r : h->prof.pending) cudaEventSynchronize(r.b);
+  prof_flush(h);
+  *out = h->prof.agg;
+  out->total_launches = h->launches;
+  return MDP_OK;
+}
+
+}  // extern "C"

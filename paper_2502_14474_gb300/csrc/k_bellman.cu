@@ -1,0 +1,330 @@
+// K1 / K6: fused Bellman backup, greedy improvement and Bellman residual.
+//
+//   Q(s,a)  = g(s,a) + gamma * sum_e P_e V(col_e)   over row r = s*m + a
+//   V'(s)   = min_a Q(s,a),  pi(s) = lowest a attaining the minimum
+//   r(s)    = V'(s) - V(s),  ||r||_inf and ||r||_2 (FP64, fixed-order)
+//
+// (madupite, "Problem Setting and Solution Methods": the improvement step of
+// policy iteration; applied alone it is value iteration.)
+//
+// Work decomposition: a CTA owns a contiguous range of state tiles (T states
+// = T*m rows each).  Within a tile, vectors of VW lanes compute the row sums
+// (coalesced col/val streams, V gathered through L1/L2) and drop Q into a
+// shared-memory tile stored action-major; then one thread per state takes the
+// min/argmin over its m actions and writes V', pi, r.  Blocked tile ranges
+// keep each CTA's V window (the band around its states) hot in L1.
+//
+// FF = float-float: V is float2 (hi, lo), the row sums are error-free
+// TwoSum/TwoProd accumulations, gamma and g are float-float; this is the
+// high-precision residual of the outer iteration.  Otherwise FP32 throughout.
+#include "k_rows.cuh"
+#include "launch.h"
+
+namespace mdpk {
+
+template <bool FF, typename IdxT, int VW>
+__global__ void __launch_bounds__(kThreads)
+    k_bellman(Csr<IdxT> P, Grid G, const void* __restrict__ Vin, void* __restrict__ Vout,
+              int32_t* __restrict__ pi_out, float* __restrict__ r_out,
+              double* __restrict__ partials, DevState* __restrict__ st, int init_gmres) {
+  extern __shared__ float smem[];
+  __shared__ double red[kThreads / 32];
+  constexpr int NV = kThreads / VW;
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const int m = P.m;
+  const int T = G.tile_states;
+  const int RT = T * m;
+  float* q_hi = smem;
+  float* q_lo = smem + RT;
+  const float* Vf = static_cast<const float*>(Vin);
+  const float2* Vff = static_cast<const float2*>(Vin);
+  const bool vec4 = P.vec4 != 0;
+
+  double my_max = 0.0, my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s0 = tile * T;
+    const int64_t r0 = s0 * m;
+    const int64_t rows_here = min(static_cast<int64_t>(RT), (P.n - s0) * m);
+    for (int base = 0; base < RT; base += NV) {
+      const int lr = base + vec;
+      int64_t b = 0, e = 0;
+      if (lr < rows_here) row_bounds<IdxT>(P.rp, P.uniform_len, r0 + lr, b, e);
+      float hi, lo = 0.f;
+      if constexpr (FF) {
+        row_dot_ff<VW>(P.col, P.val, P.val_lo, Vff, b, e, lane, vec4, hi, lo);
+        group_sum_ff<VW>(hi, lo);
+      } else {
+        hi = row_dot_f32<VW, float>(P.col, P.val, Vf, b, e, lane, vec4);
+        hi = group_sum<VW>(hi);
+      }
+      if (lane == 0 && lr < rows_here) {
+        const int a = lr % m;
+        const int sl = lr / m;
+        const int64_t r = r0 + lr;
+        if constexpr (FF) {
+          const ff sum = ff_norm(hi, lo);
+          const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+          const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+          q_hi[a * T + sl] = q.hi;
+          q_lo[a * T + sl] = q.lo;
+        } else {
+          q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += kThreads) {
+      const int64_t s = s0 + t;
+      if (s < P.n) {
+        float bh = q_hi[t], bl = FF ? q_lo[t] : 0.f;
+        int arg = 0;
+        for (int a = 1; a < m; ++a) {
+          const float h = q_hi[a * T + t];
+          const float l = FF ? q_lo[a * T + t] : 0.f;
+          if (h < bh || (FF && h == bh && l < bl)) {
+            bh = h;
+            bl = l;
+            arg = a;
+          }
+        }
+        float r;
+        if constexpr (FF) {
+          const float2 v = Vff[s];
+          r = __fadd_rn(__fsub_rn(bh, v.x), __fsub_rn(bl, v.y));
+          if (Vout) static_cast<float2*>(Vout)[s] = make_float2(bh, bl);
+        } else {
+          r = bh - Vf[s];
+          if (Vout) static_cast<float*>(Vout)[s] = bh;
+        }
+        if (pi_out) pi_out[s] = arg;
+        if (r_out) r_out[s] = r;
+        const double rd = static_cast<double>(r);
+        my_max = fmax(my_max, fabs(rd));
+        my_sq += rd * rd;
+      }
+    }
+    __syncthreads();
+  }
+
+  const double bmax = block_max_d(my_max, red);
+  const double bsq = block_sum_d(my_sq, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bmax;
+    partials[2 * blockIdx.x + 1] = bsq;
+  }
+  if (last_block(&st->counter[kCntBellman])) {
+    double mx = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += kThreads) {
+      mx = fmax(mx, __ldcg(partials + 2 * i));
+      sq += __ldcg(partials + 2 * i + 1);
+    }
+    mx = block_max_d(mx, red);
+    sq = block_sum_d(sq, red);
+    if (threadIdx.x == 0) {
+      st->res_inf = mx;
+      st->res_2 = sqrt(sq);
+      st->counter[kCntBellman] = 0;
+      if (init_gmres) {
+        if (st->target_rel) st->target = st->eta * mx;
+        gmres_begin(st, sqrt(sq));
+      }
+    }
+  }
+}
+
+// Policy residual in float-float: r(s) = g(s,pi) + gamma * sum P_pi V - V(s).
+// One vector per state; a CTA owns a contiguous range of NV-state tiles.
+template <typename IdxT, int VW>
+__global__ void __launch_bounds__(kThreads)
+    k_policy_residual(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi,
+                      const float2* __restrict__ V, float* __restrict__ r_out,
+                      double* __restrict__ partials, DevState* __restrict__ st) {
+  __shared__ double red[kThreads / 32];
+  constexpr int NV = kThreads / VW;
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const bool vec4 = P.vec4 != 0;
+  double my_max = 0.0, my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * NV + vec;
+    int64_t b = 0, e = 0, r = 0;
+    if (s < P.n) {
+      r = s * P.m + __ldg(pi + s);
+      row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+    }
+    float hi, lo;
+    row_dot_ff<VW>(P.col, P.val, P.val_lo, V, b, e, lane, vec4, hi, lo);
+    group_sum_ff<VW>(hi, lo);
+    if (lane == 0 && s < P.n) {
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+      const float2 v = V[s];
+      const float rr = __fadd_rn(__fsub_rn(q.hi, v.x), __fsub_rn(q.lo, v.y));
+      r_out[s] = rr;
+      const double rd = static_cast<double>(rr);
+      my_max = fmax(my_max, fabs(rd));
+      my_sq += rd * rd;
+    }
+  }
+  const double bmax = block_max_d(my_max, red);
+  const double bsq = block_sum_d(my_sq, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bmax;
+    partials[2 * blockIdx.x + 1] = bsq;
+  }
+  if (last_block(&st->counter[kCntPolicy])) {
+    double mx = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += kThreads) {
+      mx = fmax(mx, __ldcg(partials + 2 * i));
+      sq += __ldcg(partials + 2 * i + 1);
+    }
+    mx = block_max_d(mx, red);
+    sq = block_sum_d(sq, red);
+    if (threadIdx.x == 0) {
+      st->res_inf = mx;
+      st->res_2 = sqrt(sq);
+      st->counter[kCntPolicy] = 0;
+      gmres_begin(st, sqrt(sq));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename IdxT>
+static Csr<IdxT> make_csr(const Mat& A) {
+  Csr<IdxT> P;
+  P.rp = static_cast<const IdxT*>(A.rp);
+  P.col = A.col;
+  P.val = A.val;
+  P.val_lo = A.val_lo;
+  P.g = A.g;
+  P.g_lo = A.g_lo;
+  P.val16 = A.val16;
+  P.row_scale = A.row_scale;
+  P.n = A.n;
+  P.m = A.m;
+  P.vec4 = A.vec4;
+  P.uniform_len = A.uniform_len;
+  P.gamma = static_cast<float>(A.gamma);
+  P.gamma_hi = static_cast<float>(A.gamma);
+  P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma_hi));
+  return P;
+}
+
+// Blocks resident per SM for a kernel at a given dynamic shared memory size.
+template <typename K>
+static int occupancy(K kernel, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  return nb;
+}
+
+static Grid make_grid(int64_t n_tiles, int max_blocks, int tile_states) {
+  Grid G;
+  G.tile_states = tile_states;
+  G.n_tiles = n_tiles;
+  int64_t blocks = n_tiles < max_blocks ? n_tiles : max_blocks;
+  if (blocks < 1) blocks = 1;
+  G.tiles_per_block = (n_tiles + blocks - 1) / blocks;
+  if (G.tiles_per_block < 1) G.tiles_per_block = 1;
+  return G;
+}
+
+static int64_t n_blocks(const Grid& G) {
+  int64_t b = (G.n_tiles + G.tiles_per_block - 1) / G.tiles_per_block;
+  return b < 1 ? 1 : b;
+}
+
+// Bellman tile: about 512 rows, at least one state, at most kThreads states.
+static int bellman_tile_states(int m) {
+  int T = 512 / m;
+  if (T < 1) T = 1;
+  if (T > kThreads) T = kThreads;
+  return T;
+}
+
+template <bool FF, typename IdxT, int VW>
+static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t* pi, float* r,
+                              double* partials, DevState* st, int init_gmres, cudaStream_t s) {
+  const int T = bellman_tile_states(A.m);
+  const size_t smem = static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);
+  auto kern = k_bellman<FF, IdxT, VW>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+  static int occ = occupancy(kern, smem);
+  const int64_t n_tiles = (A.n + T - 1) / T;
+  const Grid G = make_grid(n_tiles, A.num_sms * occ, T);
+  Csr<IdxT> P = make_csr<IdxT>(A);
+  kern<<<static_cast<unsigned>(n_blocks(G)), kThreads, smem, s>>>(P, G, V, V_out, pi, r, partials,
+                                                                   st, init_gmres);
+  return cudaGetLastError();
+}
+
+template <bool FF, typename IdxT>
+static cudaError_t bellman_idx(const Mat& A, const void* V, void* V_out, int32_t* pi, float* r,
+                               double* partials, DevState* st, int init_gmres, cudaStream_t s) {
+  switch (A.vw) {
+    case 1: return bellman_vw<FF, IdxT, 1>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+    case 2: return bellman_vw<FF, IdxT, 2>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+    case 4: return bellman_vw<FF, IdxT, 4>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+    case 8: return bellman_vw<FF, IdxT, 8>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+    case 16: return bellman_vw<FF, IdxT, 16>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+    default: return bellman_vw<FF, IdxT, 32>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+  }
+}
+
+cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, int32_t* pi,
+                           float* r, double* partials, DevState* st, int init_gmres,
+                           cudaStream_t s) {
+  if (A.idx64) {
+    return ff ? bellman_idx<true, int64_t>(A, V, V_out, pi, r, partials, st, init_gmres, s)
+              : bellman_idx<false, int64_t>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+  }
+  return ff ? bellman_idx<true, int32_t>(A, V, V_out, pi, r, partials, st, init_gmres, s)
+            : bellman_idx<false, int32_t>(A, V, V_out, pi, r, partials, st, init_gmres, s);
+}
+
+template <typename IdxT, int VW>
+static cudaError_t presid_vw(const Mat& A, const int32_t* pi, const float2* V, float* r,
+                             double* partials, DevState* st, cudaStream_t s) {
+  auto kern = k_policy_residual<IdxT, VW>;
+  static int occ = occupancy(kern, 0);
+  constexpr int NV = kThreads / VW;
+  const int64_t n_tiles = (A.n + NV - 1) / NV;
+  const Grid G = make_grid(n_tiles, A.num_sms * occ, NV);
+  Csr<IdxT> P = make_csr<IdxT>(A);
+  kern<<<static_cast<unsigned>(n_blocks(G)), kThreads, 0, s>>>(P, G, pi, V, r, partials, st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT>
+static cudaError_t presid_idx(const Mat& A, const int32_t* pi, const float2* V, float* r,
+                              double* partials, DevState* st, cudaStream_t s) {
+  switch (A.vw) {
+    case 1: return presid_vw<IdxT, 1>(A, pi, V, r, partials, st, s);
+    case 2: return presid_vw<IdxT, 2>(A, pi, V, r, partials, st, s);
+    case 4: return presid_vw<IdxT, 4>(A, pi, V, r, partials, st, s);
+    case 8: return presid_vw<IdxT, 8>(A, pi, V, r, partials, st, s);
+    case 16: return presid_vw<IdxT, 16>(A, pi, V, r, partials, st, s);
+    default: return presid_vw<IdxT, 32>(A, pi, V, r, partials, st, s);
+  }
+}
+
+cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2* V, float* r,
+                                   double* partials, DevState* st, cudaStream_t s) {
+  return A.idx64 ? presid_idx<int64_t>(A, pi, V, r, partials, st, s)
+                 : presid_idx<int32_t>(A, pi, V, r, partials, st, s);
+}
+
+}  // namespace mdpk

@@ -1,0 +1,538 @@
+// GMRES(k) for the policy-evaluation system (I - gamma P_pi) d = r.
+//
+// madupite ("Problem Setting and Solution Methods") evaluates each policy only
+// approximately, with an inner Krylov solver, GMRES being the method of the
+// inexact GMRES policy iteration it cites.  The Arnoldi process below is the
+// classical Gram-Schmidt variant (Saad & Schultz 1986; Saad 2003, Alg. 6.9
+// with CGS in place of MGS), with an optional second Gram-Schmidt pass, and
+// the least-squares problem is solved by Givens rotations (Saad 2003, 6.5.3).
+//
+// Basis storage: u_0..u_k as FP32 columns of length n (leading dimension ld),
+// with v_i = u_i * scale_i; the scale of a new vector is applied lazily by
+// every reader, which saves a normalisation pass over the basis.
+//
+// Per Arnoldi step j the host enqueues:
+//   K2  k_arnoldi_spmv : w = v_j - gamma P_pi v_j (row s*m+pi(s) gathered from
+//                        the full CSR), stored in u_{j+1}; h_i = <w, v_i>, i <= j
+//                        (block partials, last block reduces in FP64).
+//   K3  k_arnoldi_ortho: u_{j+1} = w - sum h_i v_i, ||u_{j+1}||_2; the last
+//                        block appends column j of H, applies the Givens
+//                        rotations, updates |g_{j+1}| and decides convergence
+//                        (K4, a single thread in FP64).
+// and at the end of a cycle
+//   K5  k_gmres_update : V += sum_i y_i v_i in float-float.
+// Every kernel of a step first reads st->active and returns at once when the
+// cycle has ended, so a whole cycle can be enqueued without host round trips.
+#include "k_rows.cuh"
+#include "launch.h"
+
+namespace mdpk {
+
+static int64_t grid_blocks(const Grid& G) {
+  int64_t b = (G.n_tiles + G.tiles_per_block - 1) / G.tiles_per_block;
+  return b < 1 ? 1 : b;
+}
+
+static Grid grid_for(int64_t n_tiles, int max_blocks, int tile_states) {
+  Grid G;
+  G.tile_states = tile_states;
+  G.n_tiles = n_tiles;
+  int64_t blocks = n_tiles < max_blocks ? n_tiles : max_blocks;
+  if (blocks < 1) blocks = 1;
+  G.tiles_per_block = (n_tiles + blocks - 1) / blocks;
+  if (G.tiles_per_block < 1) G.tiles_per_block = 1;
+  return G;
+}
+
+template <typename K>
+static int occ_of(K kernel) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  return nb;
+}
+
+// Block-reduce acc[0..j] (FP32 per thread) and publish FP64 block partials
+// partials[blockIdx.x * MAXB + i].  All threads must call it.
+template <int MAXB>
+__device__ __forceinline__ void publish_dots(const float (&acc)[MAXB], int j, double* partials,
+                                             float (*wsum)[MAXB]) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    if (i <= j) {
+      const float v = warp_sum(acc[i]);
+      if (l == 0) wsum[w][i] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    double s = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) s += static_cast<double>(wsum[k][i]);
+    partials[static_cast<int64_t>(blockIdx.x) * MAXB + i] = s;
+  }
+}
+
+// Sum the block partials of dots 0..j in a fixed order (last block only).
+template <int MAXB>
+__device__ __forceinline__ void reduce_dots(const double* partials, int j, double* out,
+                                            const double* scale) {
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    double s = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b)
+      s += __ldcg(partials + static_cast<int64_t>(b) * MAXB + i);
+    out[i] = s * scale[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: policy-row SpMV + Gram-Schmidt dot products.  SPMV=false computes only
+// the dots of the stored u_{j+1} (second Gram-Schmidt pass, into st->h2).
+// ---------------------------------------------------------------------------
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
+__global__ void __launch_bounds__(kThreads)
+    k_arnoldi_spmv(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, float* __restrict__ basis,
+                   int64_t ld, int j, double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
+  __shared__ float w_tile[kThreads];
+  __shared__ float wsum[kThreads / 32][MAXB];
+  constexpr int NV = kThreads / VW;
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const bool vec4 = P.vec4 != 0;
+  const float* uj = basis + static_cast<int64_t>(j) * ld;
+  float* uw = basis + static_cast<int64_t>(j + 1) * ld;
+  const float sj = static_cast<float>(st->scale[j]);
+  const PV* val = SPMV ? (sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
+                                          : static_cast<const PV*>(P.val16))
+                       : nullptr;
+  const bool lp = sizeof(PV) != 4;
+  float acc[MAXB];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) acc[i] = 0.f;
+
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s0 = tile * kThreads;
+    if constexpr (SPMV) {
+      for (int base = 0; base < kThreads; base += NV) {
+        const int sl = base + vec;
+        const int64_t s = s0 + sl;
+        int64_t b = 0, e = 0, r = 0;
+        if (s < P.n) {
+          r = s * P.m + __ldg(pi + s);
+          row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+        }
+        float d = row_dot_f32<VW, PV>(P.col, val, uj, b, e, lane, vec4);
+        d = group_sum<VW>(d);
+        if (lane == 0 && s < P.n) {
+          if (lp) d *= __ldcs(P.row_scale + r);
+          w_tile[sl] = sj * fmaf(-P.gamma, d, uj[s]);
+        }
+      }
+      __syncthreads();
+    }
+    const int64_t s = s0 + threadIdx.x;
+    if (s < P.n) {
+      float w;
+      if constexpr (SPMV) {
+        w = w_tile[threadIdx.x];
+        uw[s] = w;
+      } else {
+        w = uw[s];
+      }
+#pragma unroll
+      for (int i = 0; i < MAXB; ++i)
+        if (i <= j) acc[i] = fmaf(w, basis[static_cast<int64_t>(i) * ld + s], acc[i]);
+    }
+    if constexpr (SPMV) __syncthreads();
+  }
+  publish_dots<MAXB>(acc, j, partials, wsum);
+  if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
+    double* out = SPMV ? st->H + static_cast<int64_t>(j) * kMaxBasis : st->h2;
+    reduce_dots<MAXB>(partials, j, out, st->scale);
+    if (threadIdx.x == 0) st->counter[SPMV ? kCntDots : kCntDots2] = 0;
+  }
+}
+
+// K4 (single thread): append ||w|| to column j, rotate, test convergence; at
+// the end of the cycle back-solve R y = g.
+__device__ void givens_step(DevState* st, int j, double nrm) {
+  double* h = st->H + static_cast<int64_t>(j) * kMaxBasis;
+  double colmax = 0.0;
+  for (int i = 0; i <= j; ++i) colmax = fmax(colmax, fabs(h[i]));
+  const bool breakdown = !(nrm > 1e-14 * colmax) || !(nrm > 1e-300);
+  h[j + 1] = nrm;
+  st->scale[j + 1] = breakdown ? 0.0 : 1.0 / nrm;
+  for (int i = 0; i < j; ++i) {
+    const double t = st->cs[i] * h[i] + st->sn[i] * h[i + 1];
+    h[i + 1] = -st->sn[i] * h[i] + st->cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = breakdown ? 0.0 : h[j + 1];
+  const double den = hypot(a, b);
+  double c = 1.0, sn = 0.0;
+  if (den > 0.0) {
+    c = a / den;
+    sn = b / den;
+  }
+  st->cs[j] = c;
+  st->sn[j] = sn;
+  h[j] = den > 0.0 ? den : a;
+  h[j + 1] = 0.0;
+  st->gv[j + 1] = -sn * st->gv[j];
+  st->gv[j] = c * st->gv[j];
+  const double est = fabs(st->gv[j + 1]);
+  st->est = est;
+  st->jdone = j + 1;
+  const bool conv = breakdown || est <= st->target;
+  if (conv || j + 1 >= st->restart) {
+    st->active = 0;
+    st->converged = conv ? 1 : 0;
+    st->breakdown = breakdown ? 1 : 0;
+    const int J = j + 1;
+    for (int i = J - 1; i >= 0; --i) {
+      double t = st->gv[i];
+      for (int k = i + 1; k < J; ++k) t -= st->H[static_cast<int64_t>(k) * kMaxBasis + i] * st->y[k];
+      const double d = st->H[static_cast<int64_t>(i) * kMaxBasis + i];
+      st->y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: u_{j+1} -= sum_i c_i u_i with c_i = h_i * scale_i, then ||u_{j+1}||_2.
+// mode 0: CGS with H(:, j), then Givens.  mode 1: first pass of CGS2 (no norm).
+// mode 2: second pass of CGS2 with st->h2 (added into H), then Givens.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+    k_arnoldi_ortho(int64_t n, Grid G, float* __restrict__ basis, int64_t ld, int j, int mode,
+                    double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
+  __shared__ float coef[kMaxBasis];
+  __shared__ double red[kThreads / 32];
+  const double* h = mode == 2 ? st->h2 : st->H + static_cast<int64_t>(j) * kMaxBasis;
+  for (int i = threadIdx.x; i <= j; i += kThreads)
+    coef[i] = static_cast<float>(h[i] * st->scale[i]);
+  __syncthreads();
+  float* uw = basis + static_cast<int64_t>(j + 1) * ld;
+  float acc = 0.f;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * kThreads + threadIdx.x;
+    if (s < n) {
+      float w = uw[s];
+      int i = 0;
+      for (; i + 3 <= j; i += 4) {
+        const float b0 = basis[static_cast<int64_t>(i) * ld + s];
+        const float b1 = basis[static_cast<int64_t>(i + 1) * ld + s];
+        const float b2 = basis[static_cast<int64_t>(i + 2) * ld + s];
+        const float b3 = basis[static_cast<int64_t>(i + 3) * ld + s];
+        w = fmaf(-coef[i], b0, w);
+        w = fmaf(-coef[i + 1], b1, w);
+        w = fmaf(-coef[i + 2], b2, w);
+        w = fmaf(-coef[i + 3], b3, w);
+      }
+      for (; i <= j; ++i) w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + s], w);
+      uw[s] = w;
+      acc = fmaf(w, w, acc);
+    }
+  }
+  if (mode == 1) return;
+  const double bs = block_sum_d(static_cast<double>(acc), red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (last_block(&st->counter[mode == 2 ? kCntOrtho2 : kCntOrtho])) {
+    double sq = 0.0;
+    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kThreads)
+      sq += __ldcg(partials + b);
+    sq = block_sum_d(sq, red);
+    if (threadIdx.x == 0) {
+      st->counter[mode == 2 ? kCntOrtho2 : kCntOrtho] = 0;
+      if (mode == 2) {
+        double* hc = st->H + static_cast<int64_t>(j) * kMaxBasis;
+        for (int i = 0; i <= j; ++i) hc[i] += st->h2[i];
+      }
+      givens_step(st, j, sqrt(sq));
+    }
+  }
+}
+
+// K5: V += sum_{i < jdone} y_i scale_i u_i  (FP32 correction, float-float V).
+__global__ void __launch_bounds__(kThreads)
+    k_gmres_update(int64_t n, Grid G, const float* __restrict__ basis, int64_t ld,
+                   float2* __restrict__ V, const DevState* __restrict__ st) {
+  __shared__ float coef[kMaxRestart];
+  const int J = st->jdone;
+  if (J == 0) return;
+  for (int i = threadIdx.x; i < J; i += kThreads)
+    coef[i] = static_cast<float>(st->y[i] * st->scale[i]);
+  __syncthreads();
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * kThreads + threadIdx.x;
+    if (s < n) {
+      float d = 0.f;
+      for (int i = 0; i < J; ++i) d = fmaf(coef[i], basis[static_cast<int64_t>(i) * ld + s], d);
+      const float2 v = V[s];
+      const ff r = ff_add_f(ff{v.x, v.y}, d);
+      V[s] = make_float2(r.hi, r.lo);
+    }
+  }
+}
+
+// Richardson sweep of the correction system: d_out = r + gamma P_pi d_in;
+// ||d_out - d_in||_2 (the residual of d_in) into st->res_2.
+template <typename IdxT, int VW, typename PV>
+__global__ void __launch_bounds__(kThreads)
+    k_richardson(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, const float* __restrict__ r,
+                 const float* __restrict__ d_in, float* __restrict__ d_out,
+                 double* __restrict__ partials, DevState* __restrict__ st) {
+  __shared__ double red[kThreads / 32];
+  constexpr int NV = kThreads / VW;
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const bool lp = sizeof(PV) != 4;
+  const PV* val = sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
+                                  : static_cast<const PV*>(P.val16);
+  double my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * NV + vec;
+    int64_t b = 0, e = 0, row = 0;
+    if (s < P.n) {
+      row = s * P.m + __ldg(pi + s);
+      row_bounds<IdxT>(P.rp, P.uniform_len, row, b, e);
+    }
+    float d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+    d = group_sum<VW>(d);
+    if (lane == 0 && s < P.n) {
+      if (lp) d *= __ldcs(P.row_scale + row);
+      const float nv = fmaf(P.gamma, d, r[s]);
+      d_out[s] = nv;
+      const double df = static_cast<double>(nv - d_in[s]);
+      my_sq += df * df;
+    }
+  }
+  const double bs = block_sum_d(my_sq, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (last_block(&st->counter[kCntMisc])) {
+    double sq = 0.0;
+    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kThreads)
+      sq += __ldcg(partials + b);
+    sq = block_sum_d(sq, red);
+    if (threadIdx.x == 0) {
+      st->counter[kCntMisc] = 0;
+      st->res_2 = sqrt(sq);
+    }
+  }
+}
+
+__global__ void k_ff_axpy(int64_t n, float2* __restrict__ V, const float* __restrict__ d) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float2 v = V[s];
+    const ff r = ff_add_f(ff{v.x, v.y}, d[s]);
+    V[s] = make_float2(r.hi, r.lo);
+  }
+}
+
+__global__ void k_to_ff(int64_t n, const void* __restrict__ src, int f64, float2* __restrict__ dst) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (f64) {
+      const double v = static_cast<const double*>(src)[s];
+      const float hi = static_cast<float>(v);
+      dst[s] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+    } else {
+      dst[s] = make_float2(static_cast<const float*>(src)[s], 0.f);
+    }
+  }
+}
+
+__global__ void k_from_ff(int64_t n, const float2* __restrict__ src, void* __restrict__ dst,
+                          int f64) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float2 v = src[s];
+    if (f64)
+      static_cast<double*>(dst)[s] = static_cast<double>(v.x) + static_cast<double>(v.y);
+    else
+      static_cast<float*>(dst)[s] = __fadd_rn(v.x, v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename IdxT>
+static Csr<IdxT> csr_of(const Mat& A) {
+  Csr<IdxT> P;
+  P.rp = static_cast<const IdxT*>(A.rp);
+  P.col = A.col;
+  P.val = A.val;
+  P.val_lo = A.val_lo;
+  P.g = A.g;
+  P.g_lo = A.g_lo;
+  P.val16 = A.val16;
+  P.row_scale = A.row_scale;
+  P.n = A.n;
+  P.m = A.m;
+  P.vec4 = A.vec4;
+  P.uniform_len = A.uniform_len;
+  P.gamma = static_cast<float>(A.gamma);
+  P.gamma_hi = P.gamma;
+  P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma));
+  return P;
+}
+
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
+static cudaError_t spmv_go(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                           double* partials, DevState* st, cudaStream_t s) {
+  auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV>;
+  static int occ = occ_of(kern);
+  const Grid G = grid_for((A.n + kThreads - 1) / kThreads, A.num_sms * occ, kThreads);
+  kern<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(csr_of<IdxT>(A), G, pi, basis,
+                                                                   ld, j, partials, st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT, int VW, typename PV, bool SPMV>
+static cudaError_t spmv_b(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                          int restart, double* partials, DevState* st, cudaStream_t s) {
+  if (restart + 1 <= 32) return spmv_go<IdxT, VW, PV, 32, SPMV>(A, pi, basis, ld, j, partials, st, s);
+  return spmv_go<IdxT, VW, PV, kMaxBasis, SPMV>(A, pi, basis, ld, j, partials, st, s);
+}
+
+template <typename IdxT, typename PV, bool SPMV>
+static cudaError_t spmv_v(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                          int restart, double* partials, DevState* st, cudaStream_t s) {
+  if (!SPMV) return spmv_b<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+  switch (A.vw) {
+    case 1: return spmv_b<IdxT, 1, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 2: return spmv_b<IdxT, 2, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 4: return spmv_b<IdxT, 4, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 8: return spmv_b<IdxT, 8, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 16: return spmv_b<IdxT, 16, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    default: return spmv_b<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+  }
+}
+
+template <typename IdxT>
+static cudaError_t spmv_i(const Mat& A, bool lp, const int32_t* pi, float* basis, int64_t ld,
+                          int j, int restart, double* partials, DevState* st, cudaStream_t s) {
+  if (!lp) return spmv_v<IdxT, float, true>(A, pi, basis, ld, j, restart, partials, st, s);
+  if (A.store_t == 3)
+    return spmv_v<IdxT, __half, true>(A, pi, basis, ld, j, restart, partials, st, s);
+  return spmv_v<IdxT, __nv_bfloat16, true>(A, pi, basis, ld, j, restart, partials, st, s);
+}
+
+cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
+                                int64_t ld, int j, int restart, double* partials, DevState* st,
+                                cudaStream_t s) {
+  return A.idx64 ? spmv_i<int64_t>(A, lp, pi, basis, ld, j, restart, partials, st, s)
+                 : spmv_i<int32_t>(A, lp, pi, basis, ld, j, restart, partials, st, s);
+}
+
+static Grid stream_grid(int64_t n, int num_sms, int occ) {
+  return grid_for((n + kThreads - 1) / kThreads, num_sms * occ, kThreads);
+}
+
+cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
+                                 int cgs2, double* partials, DevState* st, cudaStream_t s) {
+  static int occ = occ_of(k_arnoldi_ortho);
+  const Grid G = stream_grid(A.n, A.num_sms, occ);
+  const unsigned nb = static_cast<unsigned>(grid_blocks(G));
+  if (!cgs2) {
+    k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 0, partials, st);
+    return cudaGetLastError();
+  }
+  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 1, partials, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = A.idx64 ? spmv_v<int64_t, float, false>(A, nullptr, basis, ld, j, restart, partials, st, s)
+              : spmv_v<int32_t, float, false>(A, nullptr, basis, ld, j, restart, partials, st, s);
+  if (e != cudaSuccess) return e;
+  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 2, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* V, DevState* st,
+                                cudaStream_t s) {
+  static int occ = occ_of(k_gmres_update);
+  const Grid G = stream_grid(A.n, A.num_sms, occ);
+  k_gmres_update<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(A.n, G, basis, ld, V,
+                                                                            st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT, int VW, typename PV>
+static cudaError_t rich_go(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
+                           float* d_out, double* partials, DevState* st, cudaStream_t s) {
+  auto kern = k_richardson<IdxT, VW, PV>;
+  static int occ = occ_of(kern);
+  constexpr int NV = kThreads / VW;
+  const Grid G = grid_for((A.n + NV - 1) / NV, A.num_sms * occ, NV);
+  kern<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(csr_of<IdxT>(A), G, pi, r, d_in,
+                                                                   d_out, partials, st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT, typename PV>
+static cudaError_t rich_v(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
+                          float* d_out, double* partials, DevState* st, cudaStream_t s) {
+  switch (A.vw) {
+    case 1: return rich_go<IdxT, 1, PV>(A, pi, r, d_in, d_out, partials, st, s);
+    case 2: return rich_go<IdxT, 2, PV>(A, pi, r, d_in, d_out, partials, st, s);
+    case 4: return rich_go<IdxT, 4, PV>(A, pi, r, d_in, d_out, partials, st, s);
+    case 8: return rich_go<IdxT, 8, PV>(A, pi, r, d_in, d_out, partials, st, s);
+    case 16: return rich_go<IdxT, 16, PV>(A, pi, r, d_in, d_out, partials, st, s);
+    default: return rich_go<IdxT, 32, PV>(A, pi, r, d_in, d_out, partials, st, s);
+  }
+}
+
+template <typename IdxT>
+static cudaError_t rich_i(const Mat& A, bool lp, const int32_t* pi, const float* r,
+                          const float* d_in, float* d_out, double* partials, DevState* st,
+                          cudaStream_t s) {
+  if (!lp) return rich_v<IdxT, float>(A, pi, r, d_in, d_out, partials, st, s);
+  if (A.store_t == 3) return rich_v<IdxT, __half>(A, pi, r, d_in, d_out, partials, st, s);
+  return rich_v<IdxT, __nv_bfloat16>(A, pi, r, d_in, d_out, partials, st, s);
+}
+
+cudaError_t launch_richardson(const Mat& A, bool lp, const int32_t* pi, const float* r,
+                              const float* d_in, float* d_out, double* partials, DevState* st,
+                              cudaStream_t s) {
+  return A.idx64 ? rich_i<int64_t>(A, lp, pi, r, d_in, d_out, partials, st, s)
+                 : rich_i<int32_t>(A, lp, pi, r, d_in, d_out, partials, st, s);
+}
+
+static unsigned ew_blocks(int64_t n, int num_sms) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
+  if (b > cap) b = cap;
+  return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_ff_axpy(int64_t n, float2* V, const float* d, int num_sms, cudaStream_t s) {
+  k_ff_axpy<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, V, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, float2* dst, int num_sms,
+                         cudaStream_t s) {
+  k_to_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, src_f64, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int num_sms,
+                           cudaStream_t s) {
+  k_from_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, dst, dst_f64);
+  return cudaGetLastError();
+}
+
+}  // namespace mdpk

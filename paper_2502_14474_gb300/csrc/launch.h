@@ -1,0 +1,94 @@
+// Host-side launchers of the solver kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mdp_internal.cuh"
+
+namespace mdpk {
+
+// Device view of one handle's matrix, as the launchers need it.
+struct Mat {
+  int64_t n = 0, rows = 0, nnz = 0;
+  int32_t m = 0;
+  int32_t idx64 = 0;        // row pointers are int64
+  const void* rp = nullptr;
+  const int32_t* col = nullptr;
+  const float* val = nullptr;
+  const float* val_lo = nullptr;
+  const float* g = nullptr;
+  const float* g_lo = nullptr;
+  const void* val16 = nullptr;
+  const float* row_scale = nullptr;
+  int32_t store_t = 0;      // MDP_F32 / MDP_BF16 / MDP_F16 of val16
+  int32_t uniform_len = 0;
+  int32_t vec4 = 0;
+  int32_t vw = 4;           // lanes per row
+  double gamma = 0.0;
+  int num_sms = 1;
+};
+
+// K1 / K6: Bellman backup + greedy + residual.  ff selects float-float (V is
+// float2 hi/lo) versus FP32 (V is float).  init_gmres: the last block also
+// starts a GMRES cycle from r (target = eta*||r||_inf when st->target_rel).
+cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, int32_t* pi,
+                           float* r, double* partials, DevState* st, int init_gmres,
+                           cudaStream_t s);
+
+// Policy residual in float-float: r = g_pi + gamma P_pi V - V, ||r||, and a
+// GMRES cycle start (target kept as set on the device state).
+cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2* V, float* r,
+                                   double* partials, DevState* st, cudaStream_t s);
+
+// Arnoldi step j (K2): w = v_j - gamma P_pi v_j into u_{j+1}, dots <w, v_i>.
+// lp: use the 16-bit probabilities with row renormalisation.
+cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
+                                int64_t ld, int j, int restart, double* partials, DevState* st,
+                                cudaStream_t s);
+
+// K3 (+K4 in its last block): w -= sum h_i v_i, ||w||, Givens, convergence.
+cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
+                                 int cgs2, double* partials, DevState* st, cudaStream_t s);
+
+// K5: V += sum_i y_i v_i over the completed steps (float-float V).
+cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* V,
+                                DevState* st, cudaStream_t s);
+
+// Richardson sweep of the correction system (modified policy iteration):
+// d_out = r + gamma P_pi d_in, ||d_out - d_in||_2 into st->res_2.
+cudaError_t launch_richardson(const Mat& A, bool lp, const int32_t* pi, const float* r,
+                              const float* d_in, float* d_out, double* partials, DevState* st,
+                              cudaStream_t s);
+
+// V += d (float-float V, FP32 d).
+cudaError_t launch_ff_axpy(int64_t n, float2* V, const float* d, int num_sms, cudaStream_t s);
+
+// Conversions between caller vectors and the float-float iterate.
+cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, float2* dst, int num_sms,
+                         cudaStream_t s);
+cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int num_sms,
+                           cudaStream_t s);
+
+// Matrix preparation (mdp_create).
+struct PrepFlags {
+  unsigned bad_csr;        // row pointer or column index invalid
+  unsigned nonfinite;      // NaN / Inf in val or cost
+  unsigned negative;       // a negative probability
+  unsigned not_stochastic; // |row sum - 1| > tol or empty row
+  unsigned not_aligned;    // some row start is not a multiple of 4
+  int32_t min_len, max_len;
+  unsigned long long band; // max |col - s|
+  double max_sum_err;
+};
+
+cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const int32_t* col_in,
+                             const void* val_in, int val_f64, const void* g_in, int g_f64,
+                             double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
+                             PrepFlags* flags, int num_sms, cudaStream_t s);
+cudaError_t launch_prep_vals(int64_t nnz, const void* val_in, int val_f64, float* val_out,
+                             float* val_lo_out, int num_sms, cudaStream_t s);
+cudaError_t launch_prep_lowp(const Mat& A, void* val16, float* row_scale, int store_t,
+                             cudaStream_t s);
+
+}  // namespace mdpk

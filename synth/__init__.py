@@ -25,6 +25,7 @@ import ctypes
 import dataclasses
 import math
 import os
+import platform
 import subprocess
 import threading
 
@@ -41,6 +42,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile synth.c into a shared library (gcc, -O2, OpenMP)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    stamp = os.path.join(_OUT_DIR, "HOST_ARCH")
+    if not (os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()):
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH

@@ -25,3 +25,18 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def banded_4m_host():
+    """The full-size banded workload (n = 2^22, m = 8, 16 successors in a +-4096 band)."""
+    import synth
+    return synth.banded_4m()
+
+
+@pytest.fixture(scope="session")
+def banded_4m_gpu(banded_4m_host):
+    from paper_2502_14474_gb300 import MDP
+    h = MDP.from_csr(banded_4m_host)
+    yield banded_4m_host, h
+    h.close()
