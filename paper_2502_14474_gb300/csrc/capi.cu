@@ -547,9 +547,12 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   h->val_t = val_t;
   A.uniform_len = (fl.min_len == fl.max_len) ? fl.min_len : 0;
   // lanes per row: about 4 entries per lane with 16-byte loads for rows of 12+
-  // entries, one entry per lane below that
+  // entries whose starts are all 16-byte aligned, one entry per lane otherwise.
+  // (With aligned starts every row splits the same way, so a row's summation
+  // order depends only on its entries: identical rows give identical sums and
+  // exact ties resolve to the lowest action.)
   const double mean = static_cast<double>(nnz) / static_cast<double>(rows);
-  A.vec4 = mean >= 12.0 ? 1 : 0;
+  A.vec4 = (mean >= 12.0 && h->aligned) ? 1 : 0;
   int vw = pow2_floor(std::max(1, static_cast<int>(std::lround(A.vec4 ? mean / 4.0 : mean))));
   A.vw = std::min(32, std::max(1, vw));
 

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads)
         float r;
         if constexpr (FF) {
           const float2 v = Vff[s];
-          r = __fadd_rn(__fsub_rn(bh, v.x), __fsub_rn(bl, v.y));
+          r = ff_diff_to_float(bh, bl, v.x, v.y);
           if (Vout) static_cast<float2*>(Vout)[s] = make_float2(bh, bl);
         } else {
           r = bh - Vf[s];
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kThreads)
       const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
       const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
       const float2 v = V[s];
-      const float rr = __fadd_rn(__fsub_rn(q.hi, v.x), __fsub_rn(q.lo, v.y));
+      const float rr = ff_diff_to_float(q.hi, q.lo, v.x, v.y);
       r_out[s] = rr;
       const double rd = static_cast<double>(rr);
       my_max = fmax(my_max, fabs(rd));

@@ -53,23 +53,14 @@ static int occ_of(K kernel) {
   return nb;
 }
 
-// Block-reduce acc[0..j] (FP32 per thread) and publish FP64 block partials
-// partials[blockIdx.x * MAXB + i].  All threads must call it.
+// Publish the per-warp dot sums wacc[warp][0..j] as FP64 block partials
+// partials[blockIdx.x * MAXB + i] (fixed order).  All threads must call it.
 template <int MAXB>
-__device__ __forceinline__ void publish_dots(const float (&acc)[MAXB], int j, double* partials,
-                                             float (*wsum)[MAXB]) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    if (i <= j) {
-      const float v = warp_sum(acc[i]);
-      if (l == 0) wsum[w][i] = v;
-    }
-  }
+__device__ __forceinline__ void publish_dots(int j, double* partials, const float (*wacc)[MAXB]) {
   __syncthreads();
   for (int i = threadIdx.x; i <= j; i += kThreads) {
     double s = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) s += static_cast<double>(wsum[k][i]);
+    for (int k = 0; k < kThreads / 32; ++k) s += static_cast<double>(wacc[k][i]);
     partials[static_cast<int64_t>(blockIdx.x) * MAXB + i] = s;
   }
 }
@@ -89,17 +80,25 @@ __device__ __forceinline__ void reduce_dots(const double* partials, int j, doubl
 // ---------------------------------------------------------------------------
 // K2: policy-row SpMV + Gram-Schmidt dot products.  SPMV=false computes only
 // the dots of the stored u_{j+1} (second Gram-Schmidt pass, into st->h2).
+//
+// Tile = 4*kThreads states.  Phase A: vectors of VW lanes compute w for the
+// tile into shared memory.  Phase B: thread t owns states 4t..4t+3 of the
+// tile, stores w (float4) and streams each basis vector once; every warp
+// reduces its partial dot with shuffles and accumulates it per warp in
+// shared memory, so no per-thread accumulator array occupies registers.
 // ---------------------------------------------------------------------------
 template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
 __global__ void __launch_bounds__(kThreads)
     k_arnoldi_spmv(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, float* __restrict__ basis,
                    int64_t ld, int j, double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
-  __shared__ float w_tile[kThreads];
-  __shared__ float wsum[kThreads / 32][MAXB];
+  constexpr int TS = 4 * kThreads;
+  __shared__ __align__(16) float w_tile[TS];
+  __shared__ float wacc[kThreads / 32][MAXB];
   constexpr int NV = kThreads / VW;
   const int lane = threadIdx.x % VW;
   const int vec = threadIdx.x / VW;
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const bool vec4 = P.vec4 != 0;
   const float* uj = basis + static_cast<int64_t>(j) * ld;
   float* uw = basis + static_cast<int64_t>(j + 1) * ld;
@@ -108,16 +107,16 @@ __global__ void __launch_bounds__(kThreads)
                                           : static_cast<const PV*>(P.val16))
                        : nullptr;
   const bool lp = sizeof(PV) != 4;
-  float acc[MAXB];
-#pragma unroll
-  for (int i = 0; i < MAXB; ++i) acc[i] = 0.f;
+  for (int i = threadIdx.x; i < (kThreads / 32) * MAXB; i += kThreads) (&wacc[0][0])[i] = 0.f;
+  __syncthreads();
 
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s0 = tile * kThreads;
+    const int64_t s0 = tile * TS;
     if constexpr (SPMV) {
-      for (int base = 0; base < kThreads; base += NV) {
+#pragma unroll 4
+      for (int base = 0; base < TS; base += NV) {
         const int sl = base + vec;
         const int64_t s = s0 + sl;
         int64_t b = 0, e = 0, r = 0;
@@ -134,22 +133,47 @@ __global__ void __launch_bounds__(kThreads)
       }
       __syncthreads();
     }
-    const int64_t s = s0 + threadIdx.x;
-    if (s < P.n) {
-      float w;
+    // phase B: thread t owns states s0 + 4t .. s0 + 4t + 3
+    const int64_t sq = s0 + 4 * threadIdx.x;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sq + 3 < P.n) {
       if constexpr (SPMV) {
-        w = w_tile[threadIdx.x];
-        uw[s] = w;
+        w = reinterpret_cast<const float4*>(w_tile)[threadIdx.x];
+        *reinterpret_cast<float4*>(uw + sq) = w;
       } else {
-        w = uw[s];
+        w = *reinterpret_cast<const float4*>(uw + sq);
       }
-#pragma unroll
-      for (int i = 0; i < MAXB; ++i)
-        if (i <= j) acc[i] = fmaf(w, basis[static_cast<int64_t>(i) * ld + s], acc[i]);
+    } else if (sq < P.n) {
+      float t4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < 4 && sq + q < P.n; ++q) {
+        if constexpr (SPMV) {
+          t4[q] = w_tile[4 * threadIdx.x + q];
+          uw[sq + q] = t4[q];
+        } else {
+          t4[q] = uw[sq + q];
+        }
+      }
+      w = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+    const bool full = sq + 3 < P.n;
+#pragma unroll 4
+    for (int i = 0; i <= j; ++i) {
+      const float* bi = basis + static_cast<int64_t>(i) * ld;
+      float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (full) {
+        b4 = *reinterpret_cast<const float4*>(bi + sq);
+      } else if (sq < P.n) {
+        b4.x = bi[sq];
+        if (sq + 1 < P.n) b4.y = bi[sq + 1];
+        if (sq + 2 < P.n) b4.z = bi[sq + 2];
+      }
+      float p = fmaf(w.x, b4.x, fmaf(w.y, b4.y, fmaf(w.z, b4.z, w.w * b4.w)));
+      p = warp_sum(p);
+      if (wl == 0) wacc[warp][i] += p;
     }
     if constexpr (SPMV) __syncthreads();
   }
-  publish_dots<MAXB>(acc, j, partials, wsum);
+  publish_dots<MAXB>(j, partials, wacc);
   if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
     double* out = SPMV ? st->H + static_cast<int64_t>(j) * kMaxBasis : st->h2;
     reduce_dots<MAXB>(partials, j, out, st->scale);
@@ -219,26 +243,44 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   float* uw = basis + static_cast<int64_t>(j + 1) * ld;
   float acc = 0.f;
+  // thread-quad q owns states 4q .. 4q+3 (the last quad may be partial)
+  const int64_t nq = (n + 3) / 4;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s = tile * kThreads + threadIdx.x;
-    if (s < n) {
-      float w = uw[s];
+    const int64_t q = tile * kThreads + threadIdx.x;
+    if (q >= nq) continue;
+    const int64_t s = 4 * q;
+    if (s + 3 < n) {
+      float4 w = *reinterpret_cast<const float4*>(uw + s);
       int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        const float b0 = basis[static_cast<int64_t>(i) * ld + s];
-        const float b1 = basis[static_cast<int64_t>(i + 1) * ld + s];
-        const float b2 = basis[static_cast<int64_t>(i + 2) * ld + s];
-        const float b3 = basis[static_cast<int64_t>(i + 3) * ld + s];
-        w = fmaf(-coef[i], b0, w);
-        w = fmaf(-coef[i + 1], b1, w);
-        w = fmaf(-coef[i + 2], b2, w);
-        w = fmaf(-coef[i + 3], b3, w);
+      for (; i + 1 <= j; i += 2) {
+        const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
+        const float4 b1 =
+            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 1) * ld + s);
+        const float c0 = coef[i], c1 = coef[i + 1];
+        w.x = fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x));
+        w.y = fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y));
+        w.z = fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z));
+        w.w = fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w));
       }
-      for (; i <= j; ++i) w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + s], w);
-      uw[s] = w;
-      acc = fmaf(w, w, acc);
+      for (; i <= j; ++i) {
+        const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
+        const float c0 = coef[i];
+        w.x = fmaf(-c0, b0.x, w.x);
+        w.y = fmaf(-c0, b0.y, w.y);
+        w.z = fmaf(-c0, b0.z, w.z);
+        w.w = fmaf(-c0, b0.w, w.w);
+      }
+      *reinterpret_cast<float4*>(uw + s) = w;
+      acc = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, acc))));
+    } else {
+      for (int64_t t = s; t < n; ++t) {
+        float w = uw[t];
+        for (int i = 0; i <= j; ++i) w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + t], w);
+        uw[t] = w;
+        acc = fmaf(w, w, acc);
+      }
     }
   }
   if (mode == 1) return;
@@ -270,16 +312,37 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = threadIdx.x; i < J; i += kThreads)
     coef[i] = static_cast<float>(st->y[i] * st->scale[i]);
   __syncthreads();
+  const int64_t nq = (n + 3) / 4;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s = tile * kThreads + threadIdx.x;
-    if (s < n) {
-      float d = 0.f;
-      for (int i = 0; i < J; ++i) d = fmaf(coef[i], basis[static_cast<int64_t>(i) * ld + s], d);
-      const float2 v = V[s];
-      const ff r = ff_add_f(ff{v.x, v.y}, d);
-      V[s] = make_float2(r.hi, r.lo);
+    const int64_t q = tile * kThreads + threadIdx.x;
+    if (q >= nq) continue;
+    const int64_t s = 4 * q;
+    if (s + 3 < n) {
+      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < J; ++i) {
+        const float4 b = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
+        const float c = coef[i];
+        d.x = fmaf(c, b.x, d.x);
+        d.y = fmaf(c, b.y, d.y);
+        d.z = fmaf(c, b.z, d.z);
+        d.w = fmaf(c, b.w, d.w);
+      }
+      float4* v4 = reinterpret_cast<float4*>(V + s);  // two float2 per float4
+      float4 va = v4[0], vb = v4[1];
+      ff r0 = ff_add_f(ff{va.x, va.y}, d.x), r1 = ff_add_f(ff{va.z, va.w}, d.y);
+      ff r2 = ff_add_f(ff{vb.x, vb.y}, d.z), r3 = ff_add_f(ff{vb.z, vb.w}, d.w);
+      v4[0] = make_float4(r0.hi, r0.lo, r1.hi, r1.lo);
+      v4[1] = make_float4(r2.hi, r2.lo, r3.hi, r3.lo);
+    } else {
+      for (int64_t t = s; t < n; ++t) {
+        float d = 0.f;
+        for (int i = 0; i < J; ++i) d = fmaf(coef[i], basis[static_cast<int64_t>(i) * ld + t], d);
+        const float2 v = V[t];
+        const ff r = ff_add_f(ff{v.x, v.y}, d);
+        V[t] = make_float2(r.hi, r.lo);
+      }
     }
   }
 }
@@ -395,7 +458,8 @@ static cudaError_t spmv_go(const Mat& A, const int32_t* pi, float* basis, int64_
                            double* partials, DevState* st, cudaStream_t s) {
   auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV>;
   static int occ = occ_of(kern);
-  const Grid G = grid_for((A.n + kThreads - 1) / kThreads, A.num_sms * occ, kThreads);
+  const Grid G = grid_for((A.n + 4 * kThreads - 1) / (4 * kThreads), A.num_sms * occ,
+                          4 * kThreads);
   kern<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(csr_of<IdxT>(A), G, pi, basis,
                                                                    ld, j, partials, st);
   return cudaGetLastError();
@@ -438,8 +502,10 @@ cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float*
                  : spmv_i<int32_t>(A, lp, pi, basis, ld, j, restart, partials, st, s);
 }
 
+// Grid over thread-quads (4 states per thread) for the basis streams.
 static Grid stream_grid(int64_t n, int num_sms, int occ) {
-  return grid_for((n + kThreads - 1) / kThreads, num_sms * occ, kThreads);
+  const int64_t nq = (n + 3) / 4;
+  return grid_for((nq + kThreads - 1) / kThreads, num_sms * occ, kThreads);
 }
 
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,

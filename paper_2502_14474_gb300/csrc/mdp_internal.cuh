@@ -77,6 +77,14 @@ __device__ __forceinline__ void ff_acc(float& s_hi, float& s_lo, float p, float 
   s_lo = __fadd_rn(s_lo, __fadd_rn(e, pl));
 }
 
+// (ahi + alo) - (bhi + blo) rounded once to FP32: TwoSum makes the difference
+// of the high parts exact before the low parts are added.
+__device__ __forceinline__ float ff_diff_to_float(float ahi, float alo, float bhi, float blo) {
+  float s, e;
+  two_sum(ahi, -bhi, s, e);
+  return __fadd_rn(s, __fadd_rn(e, __fsub_rn(alo, blo)));
+}
+
 __device__ __forceinline__ bool ff_less(ff a, ff b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }

@@ -207,6 +207,6 @@ def test_banded_4m_full_size_sampled(banded_4m_gpu):
             TV, pi, Q, _ = oracle.bellman(blk, Vd, want_q=True)
             assert np.max(np.abs(TVg[s0:s1] - TV)) <= tol
             check_greedy(pig[s0:s1], pi, Q, tol)
-        # residual norm against its definition on the whole vector
+        # residual norm against its definition on the whole vector (r is FP32)
         r = TVg - Vd
-        assert abs(out["res_inf"] - np.max(np.abs(r))) <= 2 * tol
+        assert abs(out["res_inf"] - np.max(np.abs(r))) <= 2 * tol + 2.0 ** -24 * np.max(np.abs(r))
