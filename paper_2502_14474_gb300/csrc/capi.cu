@@ -8,6 +8,7 @@
 #include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -555,6 +556,11 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   A.vec4 = (mean >= 12.0 && h->aligned) ? 1 : 0;
   int vw = pow2_floor(std::max(1, static_cast<int>(std::lround(A.vec4 ? mean / 4.0 : mean))));
   A.vw = std::min(32, std::max(1, vw));
+  A.band = h->band;
+  // stage V in shared memory when the band window fits (2*band + 2*tile <= 16384
+  // float-float slots) and the matrix is large enough to amortise the fills
+  A.window = (h->band <= 7680 && n >= 16 * (2 * h->band + 1)) ? 1 : 0;
+  if (getenv("MDP_NO_WINDOW")) A.window = 0;
 
   h->store_t = store_t;
   A.store_t = store_t;

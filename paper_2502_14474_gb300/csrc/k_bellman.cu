@@ -196,6 +196,161 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Banded variant: the value vector is staged in a shared-memory ring.
+//
+// When every successor lies within `band` states of its source state, a CTA
+// that walks a contiguous range of tiles needs only V[s0 - band, s0 + T + band)
+// for the tile starting at s0.  That window lives in a ring of R >= 2*band + 2*T
+// slots (entry c at slot c & (R-1)); while the tile's rows gather from the
+// ring, the CTA already writes the next tile's leading edge
+// [s0 + T + band, s0 + 2T + band), whose slots differ from every live slot
+// because R exceeds the distance between them.  Gathers become shared-memory
+// loads instead of scattered 32-byte L2 sectors.
+// ---------------------------------------------------------------------------
+template <bool FF>
+struct RingOf;
+template <>
+struct RingOf<true> {
+  using T = float2;
+  using G = RingFF;
+};
+template <>
+struct RingOf<false> {
+  using T = float;
+  using G = RingF32;
+};
+
+template <typename VT, int NT>
+__device__ __forceinline__ void ring_fill(VT* ring, int mask, const VT* __restrict__ src,
+                                          int64_t lo, int64_t hi) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
+}
+
+template <bool FF, typename IdxT, int VW, int NT>
+__global__ void __launch_bounds__(NT)
+    k_bellman_win(Csr<IdxT> P, Grid G, int64_t band, int ring_log2, const void* __restrict__ Vin,
+                  void* __restrict__ Vout, int32_t* __restrict__ pi_out,
+                  float* __restrict__ r_out, double* __restrict__ partials,
+                  DevState* __restrict__ st, int init_gmres) {
+  using VT = typename RingOf<FF>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  constexpr int NV = NT / VW;
+  const int R = 1 << ring_log2;
+  const int mask = R - 1;
+  VT* ring = reinterpret_cast<VT*>(smem_raw);
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const int m = P.m;
+  const int T = G.tile_states;
+  const int RT = T * m;
+  float* q_hi = reinterpret_cast<float*>(ring + R);
+  float* q_lo = q_hi + RT;
+  const VT* V = static_cast<const VT*>(Vin);
+  const typename RingOf<FF>::G gx{ring, mask};
+  const bool vec4 = P.vec4 != 0;
+
+  double my_max = 0.0, my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  if (t_begin < t_end) {
+    const int64_t s_first = t_begin * T;
+    ring_fill<VT, NT>(ring, mask, V, max(int64_t(0), s_first - band), min(P.n, s_first + T + band));
+  }
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s0 = tile * T;
+    const int64_t r0 = s0 * m;
+    __syncthreads();  // window of this tile complete; q tile free
+    if (tile + 1 < t_end)
+      ring_fill<VT, NT>(ring, mask, V, s0 + T + band, min(P.n, s0 + 2 * T + band));
+    const int64_t rows_here = min(static_cast<int64_t>(RT), (P.n - s0) * m);
+    for (int base = 0; base < RT; base += NV) {
+      const int lr = base + vec;
+      int64_t b = 0, e = 0;
+      if (lr < rows_here) row_bounds<IdxT>(P.rp, P.uniform_len, r0 + lr, b, e);
+      float hi, lo = 0.f;
+      if constexpr (FF) {
+        row_dot_ff<VW>(P.col, P.val, P.val_lo, gx, b, e, lane, vec4, hi, lo);
+        group_sum_ff<VW>(hi, lo);
+      } else {
+        hi = row_dot_f32<VW, float>(P.col, P.val, gx, b, e, lane, vec4);
+        hi = group_sum<VW>(hi);
+      }
+      if (lane == 0 && lr < rows_here) {
+        const int a = lr % m;
+        const int sl = lr / m;
+        const int64_t r = r0 + lr;
+        if constexpr (FF) {
+          const ff sum = ff_norm(hi, lo);
+          const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+          const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+          q_hi[a * T + sl] = q.hi;
+          q_lo[a * T + sl] = q.lo;
+        } else {
+          q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += NT) {
+      const int64_t s = s0 + t;
+      if (s < P.n) {
+        float bh = q_hi[t], bl = FF ? q_lo[t] : 0.f;
+        int arg = 0;
+        for (int a = 1; a < m; ++a) {
+          const float h = q_hi[a * T + t];
+          const float l = FF ? q_lo[a * T + t] : 0.f;
+          if (h < bh || (FF && h == bh && l < bl)) {
+            bh = h;
+            bl = l;
+            arg = a;
+          }
+        }
+        float r;
+        if constexpr (FF) {
+          const float2 v = ring[s & mask];
+          r = ff_diff_to_float(bh, bl, v.x, v.y);
+          if (Vout) static_cast<float2*>(Vout)[s] = make_float2(bh, bl);
+        } else {
+          r = bh - ring[s & mask];
+          if (Vout) static_cast<float*>(Vout)[s] = bh;
+        }
+        if (pi_out) pi_out[s] = arg;
+        if (r_out) r_out[s] = r;
+        const double rd = static_cast<double>(r);
+        my_max = fmax(my_max, fabs(rd));
+        my_sq += rd * rd;
+      }
+    }
+  }
+
+  const double bmax = block_max_nt<NT>(my_max, red);
+  const double bsq = block_sum_nt<NT>(my_sq, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bmax;
+    partials[2 * blockIdx.x + 1] = bsq;
+  }
+  if (last_block(&st->counter[kCntBellman])) {
+    double mx = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += NT) {
+      mx = fmax(mx, __ldcg(partials + 2 * i));
+      sq += __ldcg(partials + 2 * i + 1);
+    }
+    mx = block_max_nt<NT>(mx, red);
+    sq = block_sum_nt<NT>(sq, red);
+    if (threadIdx.x == 0) {
+      st->res_inf = mx;
+      st->res_2 = sqrt(sq);
+      st->counter[kCntBellman] = 0;
+      if (init_gmres) {
+        if (st->target_rel) st->target = st->eta * mx;
+        gmres_begin(st, sqrt(sq));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename IdxT>
@@ -253,9 +408,50 @@ static int bellman_tile_states(int m) {
   return T;
 }
 
+// Ring slots needed for band B and tile T (power of two >= 2B + 2T), or 0 when
+// the ring would not fit the shared-memory budget.
+int window_log2(int64_t band, int T, size_t entry_bytes, size_t budget) {
+  const int64_t need = 2 * band + 2 * static_cast<int64_t>(T);
+  int lg = 0;
+  while ((int64_t(1) << lg) < need) ++lg;
+  if ((size_t(1) << lg) * entry_bytes > budget) return 0;
+  return lg;
+}
+
+template <bool FF, typename IdxT, int VW, int NT>
+static cudaError_t bellman_win(const Mat& A, int lg, int T, const void* V, void* V_out,
+                               int32_t* pi, float* r, double* partials, DevState* st,
+                               int init_gmres, cudaStream_t s) {
+  const size_t entry = FF ? sizeof(float2) : sizeof(float);
+  const size_t smem = (size_t(1) << lg) * entry + static_cast<size_t>(T) * A.m * sizeof(float) *
+                                                        (FF ? 2 : 1);
+  auto kern = k_bellman_win<FF, IdxT, VW, NT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const int64_t n_tiles = (A.n + T - 1) / T;
+  const Grid G = make_grid(n_tiles, A.num_sms * occ, T);
+  Csr<IdxT> P = make_csr<IdxT>(A);
+  kern<<<static_cast<unsigned>(n_blocks(G)), NT, smem, s>>>(P, G, A.band, lg, V, V_out, pi, r,
+                                                            partials, st, init_gmres);
+  return cudaGetLastError();
+}
+
 template <bool FF, typename IdxT, int VW>
 static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t* pi, float* r,
                               double* partials, DevState* st, int init_gmres, cudaStream_t s) {
+  if (A.window) {
+    // 1024 threads per CTA for the float-float ring (one CTA per SM), 512 for FP32
+    constexpr int NT = FF ? 1024 : 512;
+    int T = (NT / VW) * 4 / A.m;  // about four passes of NT/VW rows per tile
+    if (T < 1) T = 1;
+    if (T > NT) T = NT;
+    const int lg = window_log2(A.band, T, FF ? 8 : 4, 128 * 1024);
+    if (lg > 0)
+      return bellman_win<FF, IdxT, VW, NT>(A, lg, T, V, V_out, pi, r, partials, st, init_gmres, s);
+  }
   const int T = bellman_tile_states(A.m);
   const size_t smem = static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);
   auto kern = k_bellman<FF, IdxT, VW>;

@@ -53,134 +53,6 @@ static int occ_of(K kernel) {
   return nb;
 }
 
-// Publish the per-warp dot sums wacc[warp][0..j] as FP64 block partials
-// partials[blockIdx.x * MAXB + i] (fixed order).  All threads must call it.
-template <int MAXB>
-__device__ __forceinline__ void publish_dots(int j, double* partials, const float (*wacc)[MAXB]) {
-  __syncthreads();
-  for (int i = threadIdx.x; i <= j; i += kThreads) {
-    double s = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) s += static_cast<double>(wacc[k][i]);
-    partials[static_cast<int64_t>(blockIdx.x) * MAXB + i] = s;
-  }
-}
-
-// Sum the block partials of dots 0..j in a fixed order (last block only).
-template <int MAXB>
-__device__ __forceinline__ void reduce_dots(const double* partials, int j, double* out,
-                                            const double* scale) {
-  for (int i = threadIdx.x; i <= j; i += kThreads) {
-    double s = 0.0;
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b)
-      s += __ldcg(partials + static_cast<int64_t>(b) * MAXB + i);
-    out[i] = s * scale[i];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// K2: policy-row SpMV + Gram-Schmidt dot products.  SPMV=false computes only
-// the dots of the stored u_{j+1} (second Gram-Schmidt pass, into st->h2).
-//
-// Tile = 4*kThreads states.  Phase A: vectors of VW lanes compute w for the
-// tile into shared memory.  Phase B: thread t owns states 4t..4t+3 of the
-// tile, stores w (float4) and streams each basis vector once; every warp
-// reduces its partial dot with shuffles and accumulates it per warp in
-// shared memory, so no per-thread accumulator array occupies registers.
-// ---------------------------------------------------------------------------
-template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
-__global__ void __launch_bounds__(kThreads)
-    k_arnoldi_spmv(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, float* __restrict__ basis,
-                   int64_t ld, int j, double* __restrict__ partials, DevState* __restrict__ st) {
-  if (!st->active) return;
-  constexpr int TS = 4 * kThreads;
-  __shared__ __align__(16) float w_tile[TS];
-  __shared__ float wacc[kThreads / 32][MAXB];
-  constexpr int NV = kThreads / VW;
-  const int lane = threadIdx.x % VW;
-  const int vec = threadIdx.x / VW;
-  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  const bool vec4 = P.vec4 != 0;
-  const float* uj = basis + static_cast<int64_t>(j) * ld;
-  float* uw = basis + static_cast<int64_t>(j + 1) * ld;
-  const float sj = static_cast<float>(st->scale[j]);
-  const PV* val = SPMV ? (sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
-                                          : static_cast<const PV*>(P.val16))
-                       : nullptr;
-  const bool lp = sizeof(PV) != 4;
-  for (int i = threadIdx.x; i < (kThreads / 32) * MAXB; i += kThreads) (&wacc[0][0])[i] = 0.f;
-  __syncthreads();
-
-  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
-  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
-  for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s0 = tile * TS;
-    if constexpr (SPMV) {
-#pragma unroll 4
-      for (int base = 0; base < TS; base += NV) {
-        const int sl = base + vec;
-        const int64_t s = s0 + sl;
-        int64_t b = 0, e = 0, r = 0;
-        if (s < P.n) {
-          r = s * P.m + __ldg(pi + s);
-          row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
-        }
-        float d = row_dot_f32<VW, PV>(P.col, val, uj, b, e, lane, vec4);
-        d = group_sum<VW>(d);
-        if (lane == 0 && s < P.n) {
-          if (lp) d *= __ldcs(P.row_scale + r);
-          w_tile[sl] = sj * fmaf(-P.gamma, d, uj[s]);
-        }
-      }
-      __syncthreads();
-    }
-    // phase B: thread t owns states s0 + 4t .. s0 + 4t + 3
-    const int64_t sq = s0 + 4 * threadIdx.x;
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (sq + 3 < P.n) {
-      if constexpr (SPMV) {
-        w = reinterpret_cast<const float4*>(w_tile)[threadIdx.x];
-        *reinterpret_cast<float4*>(uw + sq) = w;
-      } else {
-        w = *reinterpret_cast<const float4*>(uw + sq);
-      }
-    } else if (sq < P.n) {
-      float t4[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < 4 && sq + q < P.n; ++q) {
-        if constexpr (SPMV) {
-          t4[q] = w_tile[4 * threadIdx.x + q];
-          uw[sq + q] = t4[q];
-        } else {
-          t4[q] = uw[sq + q];
-        }
-      }
-      w = make_float4(t4[0], t4[1], t4[2], t4[3]);
-    }
-    const bool full = sq + 3 < P.n;
-#pragma unroll 4
-    for (int i = 0; i <= j; ++i) {
-      const float* bi = basis + static_cast<int64_t>(i) * ld;
-      float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (full) {
-        b4 = *reinterpret_cast<const float4*>(bi + sq);
-      } else if (sq < P.n) {
-        b4.x = bi[sq];
-        if (sq + 1 < P.n) b4.y = bi[sq + 1];
-        if (sq + 2 < P.n) b4.z = bi[sq + 2];
-      }
-      float p = fmaf(w.x, b4.x, fmaf(w.y, b4.y, fmaf(w.z, b4.z, w.w * b4.w)));
-      p = warp_sum(p);
-      if (wl == 0) wacc[warp][i] += p;
-    }
-    if constexpr (SPMV) __syncthreads();
-  }
-  publish_dots<MAXB>(j, partials, wacc);
-  if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
-    double* out = SPMV ? st->H + static_cast<int64_t>(j) * kMaxBasis : st->h2;
-    reduce_dots<MAXB>(partials, j, out, st->scale);
-    if (threadIdx.x == 0) st->counter[SPMV ? kCntDots : kCntDots2] = 0;
-  }
-}
-
 // K4 (single thread): append ||w|| to column j, rotate, test convergence; at
 // the end of the cycle back-solve R y = g.
 __device__ void givens_step(DevState* st, int j, double nrm) {
@@ -453,53 +325,12 @@ static Csr<IdxT> csr_of(const Mat& A) {
   return P;
 }
 
-template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
-static cudaError_t spmv_go(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                           double* partials, DevState* st, cudaStream_t s) {
-  auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV>;
-  static int occ = occ_of(kern);
-  const Grid G = grid_for((A.n + 4 * kThreads - 1) / (4 * kThreads), A.num_sms * occ,
-                          4 * kThreads);
-  kern<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(csr_of<IdxT>(A), G, pi, basis,
-                                                                   ld, j, partials, st);
-  return cudaGetLastError();
-}
-
-template <typename IdxT, int VW, typename PV, bool SPMV>
-static cudaError_t spmv_b(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                          int restart, double* partials, DevState* st, cudaStream_t s) {
-  if (restart + 1 <= 32) return spmv_go<IdxT, VW, PV, 32, SPMV>(A, pi, basis, ld, j, partials, st, s);
-  return spmv_go<IdxT, VW, PV, kMaxBasis, SPMV>(A, pi, basis, ld, j, partials, st, s);
-}
-
-template <typename IdxT, typename PV, bool SPMV>
-static cudaError_t spmv_v(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                          int restart, double* partials, DevState* st, cudaStream_t s) {
-  if (!SPMV) return spmv_b<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-  switch (A.vw) {
-    case 1: return spmv_b<IdxT, 1, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    case 2: return spmv_b<IdxT, 2, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    case 4: return spmv_b<IdxT, 4, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    case 8: return spmv_b<IdxT, 8, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    case 16: return spmv_b<IdxT, 16, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    default: return spmv_b<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-  }
-}
-
-template <typename IdxT>
-static cudaError_t spmv_i(const Mat& A, bool lp, const int32_t* pi, float* basis, int64_t ld,
-                          int j, int restart, double* partials, DevState* st, cudaStream_t s) {
-  if (!lp) return spmv_v<IdxT, float, true>(A, pi, basis, ld, j, restart, partials, st, s);
-  if (A.store_t == 3)
-    return spmv_v<IdxT, __half, true>(A, pi, basis, ld, j, restart, partials, st, s);
-  return spmv_v<IdxT, __nv_bfloat16, true>(A, pi, basis, ld, j, restart, partials, st, s);
-}
-
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
                                 int64_t ld, int j, int restart, double* partials, DevState* st,
                                 cudaStream_t s) {
-  return A.idx64 ? spmv_i<int64_t>(A, lp, pi, basis, ld, j, restart, partials, st, s)
-                 : spmv_i<int32_t>(A, lp, pi, basis, ld, j, restart, partials, st, s);
+  if (!lp) return launch_arnoldi_spmv_f32(A, pi, basis, ld, j, restart, partials, st, s);
+  if (A.store_t == 3) return launch_arnoldi_spmv_f16(A, pi, basis, ld, j, restart, partials, st, s);
+  return launch_arnoldi_spmv_bf16(A, pi, basis, ld, j, restart, partials, st, s);
 }
 
 // Grid over thread-quads (4 states per thread) for the basis streams.
@@ -520,8 +351,7 @@ cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, 
   k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 1, partials, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = A.idx64 ? spmv_v<int64_t, float, false>(A, nullptr, basis, ld, j, restart, partials, st, s)
-              : spmv_v<int32_t, float, false>(A, nullptr, basis, ld, j, restart, partials, st, s);
+  e = launch_arnoldi_dots(A, basis, ld, j, restart, partials, st, s);
   if (e != cudaSuccess) return e;
   k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 2, partials, st);
   return cudaGetLastError();

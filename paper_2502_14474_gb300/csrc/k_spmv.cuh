@@ -1,0 +1,302 @@
+// K2: Arnoldi step j of GMRES on (I - gamma P_pi) -- the policy-row SpMV
+// w = v_j - gamma P_pi v_j, gathering row s*m + pi(s) straight from the full
+// CSR (no reassembly of P_pi), fused with the classical Gram-Schmidt dot
+// products h_i = <w, v_i>, i <= j (Saad 2003, Alg. 6.9 with CGS).
+//
+// Tile = 4*NT states.  Phase A: vectors of VW lanes compute w for the tile
+// into shared memory (banded matrices: v_j gathered from a shared-memory ring
+// window, see k_bellman.cu; uniform rows of 4*VW entries: RB rows per vector
+// with all loads issued first).  Phase B: thread t owns states 4t..4t+3 of
+// the tile, stores w as float4 and streams each basis vector once; every warp
+// reduces its partial dot with shuffles and accumulates it per warp in shared
+// memory; the block's FP64 partials are reduced in a fixed order by the last
+// block.  Included by one translation unit per probability type.
+#pragma once
+
+#include "k_rows.cuh"
+#include "launch.h"
+
+namespace mdpk {
+
+template <int MAXB, int NT>
+__device__ __forceinline__ void publish_dots_nt(int j, double* partials,
+                                                const float (*wacc)[MAXB]) {
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += NT) {
+    double s = 0.0;
+    for (int k = 0; k < NT / 32; ++k) s += static_cast<double>(wacc[k][i]);
+    partials[static_cast<int64_t>(blockIdx.x) * MAXB + i] = s;
+  }
+}
+
+template <int MAXB, int NT>
+__device__ __forceinline__ void reduce_dots_nt(const double* partials, int j, double* out,
+                                               const double* scale) {
+  for (int i = threadIdx.x; i <= j; i += NT) {
+    double s = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b)
+      s += __ldcg(partials + static_cast<int64_t>(b) * MAXB + i);
+    out[i] = s * scale[i];
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float* __restrict__ src,
+                                              int64_t lo, int64_t hi) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
+}
+
+constexpr int kSpmvRB = 2;  // rows in flight per vector on the uniform fast path
+
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, int NT, bool WIN>
+__global__ void __launch_bounds__(NT)
+    k_arnoldi_spmv(Csr<IdxT> P, Grid G, int64_t band, int ring_log2,
+                   const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
+                   double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
+  constexpr int TS = 4 * NT;
+  constexpr int NV = NT / VW;
+  constexpr int RB = kSpmvRB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) float w_tile[TS];
+  __shared__ float wacc[NT / 32][MAXB];
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const bool vec4 = P.vec4 != 0;
+  const float* uj = basis + static_cast<int64_t>(j) * ld;
+  float* uw = basis + static_cast<int64_t>(j + 1) * ld;
+  const float sj = static_cast<float>(st->scale[j]);
+  const PV* val = SPMV ? (sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
+                                          : static_cast<const PV*>(P.val16))
+                       : nullptr;
+  const bool lp = sizeof(PV) != 4;
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  const int mask = (1 << ring_log2) - 1;
+  for (int i = threadIdx.x; i < (NT / 32) * MAXB; i += NT) (&wacc[0][0])[i] = 0.f;
+
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  if (WIN && SPMV && t_begin < t_end) {
+    const int64_t sf = t_begin * TS;
+    ring_fill_f32<NT>(ring, mask, uj, max(int64_t(0), sf - band), min(P.n, sf + TS + band));
+  }
+  __syncthreads();
+  const bool fast = P.uniform_len == 4 * VW && vec4;
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s0 = tile * TS;
+    if constexpr (SPMV) {
+      if (WIN && tile + 1 < t_end)  // next tile's leading edge; disjoint from live slots
+        ring_fill_f32<NT>(ring, mask, uj, s0 + TS + band, min(P.n, s0 + 2 * TS + band));
+      auto body = [&](auto gx, auto xs) {
+        if (fast) {
+          for (int base = 0; base < TS; base += NV * RB) {
+            int64_t b[RB], rr[RB];
+            bool valid[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+              const int64_t s = s0 + base + u * NV + vec;
+              valid[u] = s < P.n;
+              rr[u] = valid[u] ? s * P.m + __ldg(pi + s) : 0;
+              b[u] = rr[u] * P.uniform_len;
+            }
+            float d[RB];
+            rows_dot_f32_k4vw<VW, RB, PV>(P.col, val, gx, b, valid, lane, d);
+#pragma unroll
+            for (int u = 0; u < RB; ++u) d[u] = group_sum<VW>(d[u]);
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+              const int sl = base + u * NV + vec;
+              if (lane == 0 && valid[u]) {
+                float dd = d[u];
+                if (lp) dd *= __ldcs(P.row_scale + rr[u]);
+                w_tile[sl] = sj * fmaf(-P.gamma, dd, xs(s0 + sl));
+              }
+            }
+          }
+        } else {
+          for (int base = 0; base < TS; base += NV) {
+            const int sl = base + vec;
+            const int64_t s = s0 + sl;
+            int64_t b = 0, e = 0, r = 0;
+            if (s < P.n) {
+              r = s * P.m + __ldg(pi + s);
+              row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+            }
+            float d = row_dot_f32<VW, PV>(P.col, val, gx, b, e, lane, vec4);
+            d = group_sum<VW>(d);
+            if (lane == 0 && s < P.n) {
+              if (lp) d *= __ldcs(P.row_scale + r);
+              w_tile[sl] = sj * fmaf(-P.gamma, d, xs(s));
+            }
+          }
+        }
+      };
+      if constexpr (WIN) {
+        body(RingF32{ring, mask}, [&](int64_t s) { return ring[s & mask]; });
+      } else {
+        body(GatherF32{uj}, [&](int64_t s) { return uj[s]; });
+      }
+      __syncthreads();
+    }
+    // phase B: thread t owns states s0 + 4t .. s0 + 4t + 3
+    const int64_t sq = s0 + 4 * threadIdx.x;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool full = sq + 3 < P.n;
+    if (full) {
+      if constexpr (SPMV) {
+        w = reinterpret_cast<const float4*>(w_tile)[threadIdx.x];
+        *reinterpret_cast<float4*>(uw + sq) = w;
+      } else {
+        w = *reinterpret_cast<const float4*>(uw + sq);
+      }
+    } else if (sq < P.n) {
+      float t4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < 4 && sq + q < P.n; ++q) {
+        if constexpr (SPMV) {
+          t4[q] = w_tile[4 * threadIdx.x + q];
+          uw[sq + q] = t4[q];
+        } else {
+          t4[q] = uw[sq + q];
+        }
+      }
+      w = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+#pragma unroll 4
+    for (int i = 0; i <= j; ++i) {
+      const float* bi = basis + static_cast<int64_t>(i) * ld;
+      float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (full) {
+        b4 = *reinterpret_cast<const float4*>(bi + sq);
+      } else if (sq < P.n) {
+        b4.x = bi[sq];
+        if (sq + 1 < P.n) b4.y = bi[sq + 1];
+        if (sq + 2 < P.n) b4.z = bi[sq + 2];
+      }
+      float p = fmaf(w.x, b4.x, fmaf(w.y, b4.y, fmaf(w.z, b4.z, w.w * b4.w)));
+      p = warp_sum(p);
+      if (wl == 0) wacc[warp][i] += p;
+    }
+    if constexpr (SPMV) __syncthreads();
+  }
+  publish_dots_nt<MAXB, NT>(j, partials, wacc);
+  if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
+    double* out = SPMV ? st->H + static_cast<int64_t>(j) * kMaxBasis : st->h2;
+    reduce_dots_nt<MAXB, NT>(partials, j, out, st->scale);
+    if (threadIdx.x == 0) st->counter[SPMV ? kCntDots : kCntDots2] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+template <typename IdxT>
+inline Csr<IdxT> csr_view(const Mat& A) {
+  Csr<IdxT> P;
+  P.rp = static_cast<const IdxT*>(A.rp);
+  P.col = A.col;
+  P.val = A.val;
+  P.val_lo = A.val_lo;
+  P.g = A.g;
+  P.g_lo = A.g_lo;
+  P.val16 = A.val16;
+  P.row_scale = A.row_scale;
+  P.n = A.n;
+  P.m = A.m;
+  P.vec4 = A.vec4;
+  P.uniform_len = A.uniform_len;
+  P.gamma = static_cast<float>(A.gamma);
+  P.gamma_hi = P.gamma;
+  P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma));
+  return P;
+}
+
+inline Grid tiles_grid(int64_t n_tiles, int max_blocks, int tile_states) {
+  Grid G;
+  G.tile_states = tile_states;
+  G.n_tiles = n_tiles;
+  int64_t blocks = n_tiles < max_blocks ? n_tiles : max_blocks;
+  if (blocks < 1) blocks = 1;
+  G.tiles_per_block = (n_tiles + blocks - 1) / blocks;
+  if (G.tiles_per_block < 1) G.tiles_per_block = 1;
+  return G;
+}
+
+inline int64_t tiles_blocks(const Grid& G) {
+  int64_t b = (G.n_tiles + G.tiles_per_block - 1) / G.tiles_per_block;
+  return b < 1 ? 1 : b;
+}
+
+// Power-of-two ring size >= 2*band + 2*tile, or 0 when it exceeds `budget` bytes.
+inline int ring_log2_for(int64_t band, int64_t tile, size_t entry, size_t budget) {
+  const int64_t need = 2 * band + 2 * tile;
+  int lg = 0;
+  while ((int64_t(1) << lg) < need) ++lg;
+  if ((size_t(1) << lg) * entry > budget) return 0;
+  return lg;
+}
+
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, int NT, bool WIN>
+cudaError_t spmv_launch(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                        int lg, double* partials, DevState* st, cudaStream_t s) {
+  auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV, NT, WIN>;
+  const size_t smem = WIN ? (size_t(1) << lg) * sizeof(float) : 0;
+  if (smem > 0)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  constexpr int TS = 4 * NT;
+  const Grid G = tiles_grid((A.n + TS - 1) / TS, A.num_sms * occ, TS);
+  kern<<<static_cast<unsigned>(tiles_blocks(G)), NT, smem, s>>>(csr_view<IdxT>(A), G, A.band, lg,
+                                                                pi, basis, ld, j, partials, st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
+cudaError_t spmv_win_or_not(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                            double* partials, DevState* st, cudaStream_t s) {
+  if (SPMV && A.window) {
+    constexpr int NT = 512;
+    const int lg = ring_log2_for(A.band, 4 * NT, sizeof(float), 64 * 1024);
+    if (lg > 0)
+      return spmv_launch<IdxT, VW, PV, MAXB, SPMV, NT, true>(A, pi, basis, ld, j, lg, partials,
+                                                            st, s);
+  }
+  return spmv_launch<IdxT, VW, PV, MAXB, SPMV, 256, false>(A, pi, basis, ld, j, 0, partials, st,
+                                                          s);
+}
+
+template <typename IdxT, int VW, typename PV, bool SPMV>
+cudaError_t spmv_maxb(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                      int restart, double* partials, DevState* st, cudaStream_t s) {
+  if (restart + 1 <= 32)
+    return spmv_win_or_not<IdxT, VW, PV, 32, SPMV>(A, pi, basis, ld, j, partials, st, s);
+  return spmv_win_or_not<IdxT, VW, PV, kMaxBasis, SPMV>(A, pi, basis, ld, j, partials, st, s);
+}
+
+// Lanes per row are 2, 4, 8 or 32 (the create-time choice is rounded to these).
+template <typename IdxT, typename PV, bool SPMV>
+cudaError_t spmv_vw(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                    int restart, double* partials, DevState* st, cudaStream_t s) {
+  if (!SPMV) return spmv_maxb<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+  switch (A.vw) {
+    case 1:
+    case 2: return spmv_maxb<IdxT, 2, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 4: return spmv_maxb<IdxT, 4, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 8:
+    case 16: return spmv_maxb<IdxT, 8, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    default: return spmv_maxb<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+  }
+}
+
+template <typename PV, bool SPMV>
+cudaError_t spmv_entry(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                       int restart, double* partials, DevState* st, cudaStream_t s) {
+  return A.idx64 ? spmv_vw<int64_t, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s)
+                 : spmv_vw<int32_t, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+}
+
+}  // namespace mdpk

@@ -1,0 +1,17 @@
+// K2 instantiations for f32 probabilities (see k_spmv.cuh).
+#include "k_spmv.cuh"
+
+namespace mdpk {
+
+cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
+                                    int j, int restart, double* partials, DevState* st,
+                                    cudaStream_t s) {
+  return spmv_entry<float, true>(A, pi, basis, ld, j, restart, partials, st, s);
+}
+
+cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, int restart,
+                                double* partials, DevState* st, cudaStream_t s) {
+  return spmv_entry<float, false>(A, nullptr, basis, ld, j, restart, partials, st, s);
+}
+
+}  // namespace mdpk

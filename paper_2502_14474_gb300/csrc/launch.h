@@ -25,6 +25,8 @@ struct Mat {
   int32_t uniform_len = 0;
   int32_t vec4 = 0;
   int32_t vw = 4;           // lanes per row
+  int64_t band = 0;         // max |col - s| (measured at create)
+  int32_t window = 0;       // 1: banded kernels stage V in a shared-memory ring
   double gamma = 0.0;
   int num_sms = 1;
 };
@@ -46,6 +48,19 @@ cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
                                 int64_t ld, int j, int restart, double* partials, DevState* st,
                                 cudaStream_t s);
+
+cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
+                                    int j, int restart, double* partials, DevState* st,
+                                    cudaStream_t s);
+cudaError_t launch_arnoldi_spmv_bf16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
+                                     int j, int restart, double* partials, DevState* st,
+                                     cudaStream_t s);
+cudaError_t launch_arnoldi_spmv_f16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
+                                    int j, int restart, double* partials, DevState* st,
+                                    cudaStream_t s);
+// Dots only (second Gram-Schmidt pass): st->h2[i] = <u_{j+1}, v_i>.
+cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, int restart,
+                                double* partials, DevState* st, cudaStream_t s);
 
 // K3 (+K4 in its last block): w -= sum h_i v_i, ||w||, Givens, convergence.
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,

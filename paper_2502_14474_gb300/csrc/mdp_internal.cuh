@@ -152,6 +152,32 @@ __device__ __forceinline__ double block_max_d(double v, double* scratch) {
   return r;
 }
 
+template <int NT>
+__device__ __forceinline__ double block_sum_nt(double v, double* scratch) {
+  v = warp_sum_d(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) r += scratch[i];
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max_nt(double v, double* scratch) {
+  v = warp_max_d(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) r = fmax(r, scratch[i]);
+  return r;
+}
+
 // "Last block" ticket (threadFenceReduction pattern): every block publishes
 // its partials, fences, then takes a ticket; the block that draws the last
 // ticket sees every partial and reduces them in a fixed order, so results are
