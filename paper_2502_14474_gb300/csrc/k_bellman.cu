@@ -22,6 +22,48 @@
 
 namespace mdpk {
 
+// Fast path of one pass over the rows of a tile when every row holds 4*VW
+// entries (16-byte aligned): the vector owns VW consecutive rows, each lane
+// loads its slice of all of them before any gather, and a reduce-scatter
+// leaves lane l with the sum of row lr0 + l, which it turns into Q(s, a).
+template <bool FF, int VW, typename IdxT, typename GX>
+__device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int64_t r0, int lr0,
+                                                  int64_t rows_here, int lane, int T,
+                                                  float* q_hi, float* q_lo) {
+  int64_t b[VW];
+  bool vd[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    vd[u] = lr0 + u < rows_here;
+    b[u] = (r0 + lr0 + u) * P.uniform_len;
+  }
+  const int lr = lr0 + lane;
+  float hi, lo = 0.f;
+  if constexpr (FF) {
+    float ph[VW], pl[VW];
+    vec_rows_ff<VW>(P.col, P.val, gx, b, vd, lane, ph, pl);
+    reduce_scatter_ff<VW>(ph, pl, lane, hi, lo);
+  } else {
+    float p[VW];
+    vec_rows_f32<VW, float>(P.col, P.val, gx, b, vd, lane, p);
+    hi = reduce_scatter<VW>(p, lane);
+  }
+  if (lr < rows_here) {
+    const int a = lr % P.m;
+    const int sl = lr / P.m;
+    const int64_t r = r0 + lr;
+    if constexpr (FF) {
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+      q_hi[a * T + sl] = q.hi;
+      q_lo[a * T + sl] = q.lo;
+    } else {
+      q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+    }
+  }
+}
+
 template <bool FF, typename IdxT, int VW>
 __global__ void __launch_bounds__(kThreads)
     k_bellman(Csr<IdxT> P, Grid G, const void* __restrict__ Vin, void* __restrict__ Vout,
@@ -40,6 +82,7 @@ __global__ void __launch_bounds__(kThreads)
   const float* Vf = static_cast<const float*>(Vin);
   const float2* Vff = static_cast<const float2*>(Vin);
   const bool vec4 = P.vec4 != 0;
+  const bool fast = VW <= 4 && P.uniform_len == 4 * VW && vec4 && !P.val_lo;
 
   double my_max = 0.0, my_sq = 0.0;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
@@ -48,6 +91,18 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t s0 = tile * T;
     const int64_t r0 = s0 * m;
     const int64_t rows_here = min(static_cast<int64_t>(RT), (P.n - s0) * m);
+    if (fast) {
+      if constexpr (VW <= 4) {
+        for (int base = 0; base < RT; base += kThreads) {
+          if constexpr (FF)
+            bellman_pass_fast<FF, VW>(P, GatherFF{Vff}, r0, base + vec * VW, rows_here, lane, T,
+                                      q_hi, q_lo);
+          else
+            bellman_pass_fast<FF, VW>(P, GatherF32{Vf}, r0, base + vec * VW, rows_here, lane, T,
+                                      q_hi, q_lo);
+        }
+      }
+    } else
     for (int base = 0; base < RT; base += NV) {
       const int lr = base + vec;
       int64_t b = 0, e = 0;
@@ -249,6 +304,7 @@ __global__ void __launch_bounds__(NT)
   const VT* V = static_cast<const VT*>(Vin);
   const typename RingOf<FF>::G gx{ring, mask};
   const bool vec4 = P.vec4 != 0;
+  const bool fast = VW <= 4 && P.uniform_len == 4 * VW && vec4 && !P.val_lo;
 
   double my_max = 0.0, my_sq = 0.0;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
@@ -264,6 +320,12 @@ __global__ void __launch_bounds__(NT)
     if (tile + 1 < t_end)
       ring_fill<VT, NT>(ring, mask, V, s0 + T + band, min(P.n, s0 + 2 * T + band));
     const int64_t rows_here = min(static_cast<int64_t>(RT), (P.n - s0) * m);
+    if (fast) {
+      if constexpr (VW <= 4) {
+        for (int base = 0; base < RT; base += NT)
+          bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, T, q_hi, q_lo);
+      }
+    } else
     for (int base = 0; base < RT; base += NV) {
       const int lr = base + vec;
       int64_t b = 0, e = 0;
@@ -400,9 +462,9 @@ static int64_t n_blocks(const Grid& G) {
   return b < 1 ? 1 : b;
 }
 
-// Bellman tile: about 512 rows, at least one state, at most kThreads states.
+// Bellman tile: about 1024 rows, at least one state, at most kThreads states.
 static int bellman_tile_states(int m) {
-  int T = 512 / m;
+  int T = 1024 / m;
   if (T < 1) T = 1;
   if (T > kThreads) T = kThreads;
   return T;
@@ -445,7 +507,7 @@ static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t*
   if (A.window) {
     // 1024 threads per CTA for the float-float ring (one CTA per SM), 512 for FP32
     constexpr int NT = FF ? 1024 : 512;
-    int T = (NT / VW) * 4 / A.m;  // about four passes of NT/VW rows per tile
+    int T = 4 * NT / A.m;  // about 4*NT rows per tile
     if (T < 1) T = 1;
     if (T > NT) T = NT;
     const int lg = window_log2(A.band, T, FF ? 8 : 4, 128 * 1024);

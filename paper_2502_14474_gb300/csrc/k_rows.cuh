@@ -177,6 +177,143 @@ __device__ __forceinline__ void rows_dot_ff_k4vw(const int32_t* __restrict__ col
   }
 }
 
+// ---- reduce-scatter across the VW lanes of a vector -------------------------
+// On entry lane l holds its partial sums p[u] of the vector's rows u < VW; on
+// exit the return value of lane l is the full sum of row l.  The association
+// is the same for every row ((x0 + x2) + (x1 + x3) for VW = 4), so rows with
+// identical entries give identical sums.
+template <int VW>
+__device__ __forceinline__ float reduce_scatter(const float (&p)[VW], int lane);
+
+template <>
+__device__ __forceinline__ float reduce_scatter<1>(const float (&p)[1], int) {
+  return p[0];
+}
+
+template <>
+__device__ __forceinline__ float reduce_scatter<2>(const float (&p)[2], int lane) {
+  const bool up = lane & 1;
+  const float keep = up ? p[1] : p[0];
+  const float send = up ? p[0] : p[1];
+  return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+}
+
+template <>
+__device__ __forceinline__ float reduce_scatter<4>(const float (&p)[4], int lane) {
+  const bool up2 = lane & 2;
+  float k0 = up2 ? p[2] : p[0], k1 = up2 ? p[3] : p[1];
+  const float s0 = up2 ? p[0] : p[2], s1 = up2 ? p[1] : p[3];
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  const bool up1 = lane & 1;
+  const float keep = up1 ? k1 : k0;
+  const float send = up1 ? k0 : k1;
+  return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+}
+
+// Float-float version: (hi, lo) pairs combined with TwoSum on the high parts.
+__device__ __forceinline__ void ff_merge(float& hi, float& lo, float ohi, float olo) {
+  float s, e;
+  two_sum(hi, ohi, s, e);
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, olo), e);
+}
+
+template <int VW>
+__device__ __forceinline__ void reduce_scatter_ff(const float (&ph)[VW], const float (&pl)[VW],
+                                                  int lane, float& hi, float& lo);
+
+template <>
+__device__ __forceinline__ void reduce_scatter_ff<1>(const float (&ph)[1], const float (&pl)[1],
+                                                     int, float& hi, float& lo) {
+  hi = ph[0];
+  lo = pl[0];
+}
+
+template <>
+__device__ __forceinline__ void reduce_scatter_ff<2>(const float (&ph)[2], const float (&pl)[2],
+                                                     int lane, float& hi, float& lo) {
+  const bool up = lane & 1;
+  hi = up ? ph[1] : ph[0];
+  lo = up ? pl[1] : pl[0];
+  const float sh = up ? ph[0] : ph[1], sl = up ? pl[0] : pl[1];
+  ff_merge(hi, lo, __shfl_xor_sync(0xffffffffu, sh, 1), __shfl_xor_sync(0xffffffffu, sl, 1));
+}
+
+template <>
+__device__ __forceinline__ void reduce_scatter_ff<4>(const float (&ph)[4], const float (&pl)[4],
+                                                     int lane, float& hi, float& lo) {
+  const bool up2 = lane & 2;
+  float k0h = up2 ? ph[2] : ph[0], k0l = up2 ? pl[2] : pl[0];
+  float k1h = up2 ? ph[3] : ph[1], k1l = up2 ? pl[3] : pl[1];
+  const float s0h = up2 ? ph[0] : ph[2], s0l = up2 ? pl[0] : pl[2];
+  const float s1h = up2 ? ph[1] : ph[3], s1l = up2 ? pl[1] : pl[3];
+  ff_merge(k0h, k0l, __shfl_xor_sync(0xffffffffu, s0h, 2), __shfl_xor_sync(0xffffffffu, s0l, 2));
+  ff_merge(k1h, k1l, __shfl_xor_sync(0xffffffffu, s1h, 2), __shfl_xor_sync(0xffffffffu, s1l, 2));
+  const bool up1 = lane & 1;
+  hi = up1 ? k1h : k0h;
+  lo = up1 ? k1l : k0l;
+  const float sh = up1 ? k0h : k1h, sl = up1 ? k0l : k1l;
+  ff_merge(hi, lo, __shfl_xor_sync(0xffffffffu, sh, 1), __shfl_xor_sync(0xffffffffu, sl, 1));
+}
+
+// ---- VW rows per vector, 4*VW entries per row (uniform, 16-byte aligned) ---
+// Lane l loads entries [4l, 4l+4) of each of the vector's VW rows (row u starts
+// at b[u]); the loads of all rows are issued before any gather.  Rows with
+// valid[u] false contribute 0.  Returns lane l's partial sums p[u].
+template <int VW, typename PV, typename GX>
+__device__ __forceinline__ void vec_rows_f32(const int32_t* __restrict__ col,
+                                             const PV* __restrict__ val, GX x,
+                                             const int64_t (&b)[VW], const bool (&valid)[VW],
+                                             int lane, float (&p)[VW]) {
+  int4 c[VW];
+  float4 q[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    if (valid[u]) {
+      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
+      q[u] = Ld<PV>::four(val, b[u] + 4 * lane);
+    } else {
+      c[u] = make_int4(0, 0, 0, 0);
+      q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VW; ++u)
+    p[u] = fmaf(q[u].w, x(c[u].w), fmaf(q[u].z, x(c[u].z), fmaf(q[u].y, x(c[u].y),
+                                                                 q[u].x * x(c[u].x))));
+}
+
+template <int VW, typename GX>
+__device__ __forceinline__ void vec_rows_ff(const int32_t* __restrict__ col,
+                                            const float* __restrict__ val, GX V,
+                                            const int64_t (&b)[VW], const bool (&valid)[VW],
+                                            int lane, float (&ph)[VW], float (&pl)[VW]) {
+  int4 c[VW];
+  float4 q[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    if (valid[u]) {
+      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
+      q[u] = __ldcs(reinterpret_cast<const float4*>(val + b[u] + 4 * lane));
+    } else {
+      c[u] = make_int4(0, 0, 0, 0);
+      q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    float h = 0.f, l = 0.f;
+    const float2 v0 = V(c[u].x), v1 = V(c[u].y), v2 = V(c[u].z), v3 = V(c[u].w);
+    ff_acc(h, l, q[u].x, v0.x, v0.y);
+    ff_acc(h, l, q[u].y, v1.x, v1.y);
+    ff_acc(h, l, q[u].z, v2.x, v2.y);
+    ff_acc(h, l, q[u].w, v3.x, v3.y);
+    ph[u] = h;
+    pl[u] = l;
+  }
+}
+
 // Pointer form (global gathers) kept for the callers that stream a vector.
 template <int VW, typename PV>
 __device__ __forceinline__ float row_dot_f32(const int32_t* __restrict__ col,

@@ -3,14 +3,17 @@
 // CSR (no reassembly of P_pi), fused with the classical Gram-Schmidt dot
 // products h_i = <w, v_i>, i <= j (Saad 2003, Alg. 6.9 with CGS).
 //
-// Tile = 4*NT states.  Phase A: vectors of VW lanes compute w for the tile
-// into shared memory (banded matrices: v_j gathered from a shared-memory ring
-// window, see k_bellman.cu; uniform rows of 4*VW entries: RB rows per vector
-// with all loads issued first).  Phase B: thread t owns states 4t..4t+3 of
-// the tile, stores w as float4 and streams each basis vector once; every warp
-// reduces its partial dot with shuffles and accumulates it per warp in shared
-// memory; the block's FP64 partials are reduced in a fixed order by the last
-// block.  Included by one translation unit per probability type.
+// Tile = 4*NT states.  Phase A writes w for the tile straight to global
+// memory.  Fast path (rows of exactly 4*VW entries, 16-byte aligned): a
+// vector of VW lanes owns VW consecutive states, each lane loads its 16-byte
+// slice of all VW policy rows before any gather (VW rows in flight per lane),
+// and a reduce-scatter leaves every lane with its own state's row sum.
+// Banded matrices gather v_j from a shared-memory ring window (see
+// k_bellman.cu).  Phase B (after a block barrier): thread t owns states
+// 4t..4t+3 of the tile and streams each basis vector once as float4; every
+// warp reduces its partial dot with shuffles and accumulates it per warp in
+// shared memory; the block's FP64 partials are reduced in a fixed order by the
+// last block.  Included by one translation unit per probability type.
 #pragma once
 
 #include "k_rows.cuh"
@@ -46,19 +49,15 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
   for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
 }
 
-constexpr int kSpmvRB = 2;  // rows in flight per vector on the uniform fast path
-
 template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, int NT, bool WIN>
 __global__ void __launch_bounds__(NT)
     k_arnoldi_spmv(Csr<IdxT> P, Grid G, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
                    double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
-  constexpr int TS = 4 * NT;
+  constexpr int TS = 4 * NT;  // states per tile (four passes of NT states)
   constexpr int NV = NT / VW;
-  constexpr int RB = kSpmvRB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) float w_tile[TS];
   __shared__ float wacc[NT / 32][MAXB];
   const int lane = threadIdx.x % VW;
   const int vec = threadIdx.x / VW;
@@ -82,42 +81,50 @@ __global__ void __launch_bounds__(NT)
     ring_fill_f32<NT>(ring, mask, uj, max(int64_t(0), sf - band), min(P.n, sf + TS + band));
   }
   __syncthreads();
-  const bool fast = P.uniform_len == 4 * VW && vec4;
+  // fast path: every row holds 4*VW entries, 16-byte aligned; a vector of VW
+  // lanes owns VW consecutive states and each lane loads its slice of all VW
+  // policy rows before any gather, then a reduce-scatter gives each lane the
+  // row sum of its own state
+  const bool fast = VW <= 4 && P.uniform_len == 4 * VW && vec4;
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
     const int64_t s0 = tile * TS;
     if constexpr (SPMV) {
       if (WIN && tile + 1 < t_end)  // next tile's leading edge; disjoint from live slots
         ring_fill_f32<NT>(ring, mask, uj, s0 + TS + band, min(P.n, s0 + 2 * TS + band));
-      auto body = [&](auto gx, auto xs) {
+      auto phase_a = [&](auto gx, auto xs) {
         if (fast) {
-          for (int base = 0; base < TS; base += NV * RB) {
-            int64_t b[RB], rr[RB];
-            bool valid[RB];
+          if constexpr (VW <= 4) {
+            int32_t act[4];
 #pragma unroll
-            for (int u = 0; u < RB; ++u) {
-              const int64_t s = s0 + base + u * NV + vec;
-              valid[u] = s < P.n;
-              rr[u] = valid[u] ? s * P.m + __ldg(pi + s) : 0;
-              b[u] = rr[u] * P.uniform_len;
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              act[p] = s < P.n ? __ldg(pi + s) : 0;
             }
-            float d[RB];
-            rows_dot_f32_k4vw<VW, RB, PV>(P.col, val, gx, b, valid, lane, d);
 #pragma unroll
-            for (int u = 0; u < RB; ++u) d[u] = group_sum<VW>(d[u]);
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              const bool valid = s < P.n;
+              const int64_t r = s * P.m + act[p];
+              const int64_t rb = r * P.uniform_len;
+              int64_t b[VW];
+              bool vd[VW];
 #pragma unroll
-            for (int u = 0; u < RB; ++u) {
-              const int sl = base + u * NV + vec;
-              if (lane == 0 && valid[u]) {
-                float dd = d[u];
-                if (lp) dd *= __ldcs(P.row_scale + rr[u]);
-                w_tile[sl] = sj * fmaf(-P.gamma, dd, xs(s0 + sl));
+              for (int u = 0; u < VW; ++u) {
+                b[u] = __shfl_sync(0xffffffffu, rb, u, VW);
+                vd[u] = __shfl_sync(0xffffffffu, valid ? 1 : 0, u, VW) != 0;
+              }
+              float part[VW];
+              vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
+              float d = reduce_scatter<VW>(part, lane);
+              if (valid) {
+                if (lp) d *= __ldcs(P.row_scale + r);
+                uw[s] = sj * fmaf(-P.gamma, d, xs(s));
               }
             }
           }
         } else {
           for (int base = 0; base < TS; base += NV) {
-            const int sl = base + vec;
-            const int64_t s = s0 + sl;
+            const int64_t s = s0 + base + vec;
             int64_t b = 0, e = 0, r = 0;
             if (s < P.n) {
               r = s * P.m + __ldg(pi + s);
@@ -127,40 +134,28 @@ __global__ void __launch_bounds__(NT)
             d = group_sum<VW>(d);
             if (lane == 0 && s < P.n) {
               if (lp) d *= __ldcs(P.row_scale + r);
-              w_tile[sl] = sj * fmaf(-P.gamma, d, xs(s));
+              uw[s] = sj * fmaf(-P.gamma, d, xs(s));
             }
           }
         }
       };
       if constexpr (WIN) {
-        body(RingF32{ring, mask}, [&](int64_t s) { return ring[s & mask]; });
+        phase_a(RingF32{ring, mask}, [&](int64_t s) { return ring[s & mask]; });
       } else {
-        body(GatherF32{uj}, [&](int64_t s) { return uj[s]; });
+        phase_a(GatherF32{uj}, [&](int64_t s) { return uj[s]; });
       }
-      __syncthreads();
+      __syncthreads();  // the tile's w (global) visible to the block; ring edge complete
     }
     // phase B: thread t owns states s0 + 4t .. s0 + 4t + 3
     const int64_t sq = s0 + 4 * threadIdx.x;
     float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool full = sq + 3 < P.n;
     if (full) {
-      if constexpr (SPMV) {
-        w = reinterpret_cast<const float4*>(w_tile)[threadIdx.x];
-        *reinterpret_cast<float4*>(uw + sq) = w;
-      } else {
-        w = *reinterpret_cast<const float4*>(uw + sq);
-      }
+      w = *reinterpret_cast<const float4*>(uw + sq);
     } else if (sq < P.n) {
-      float t4[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < 4 && sq + q < P.n; ++q) {
-        if constexpr (SPMV) {
-          t4[q] = w_tile[4 * threadIdx.x + q];
-          uw[sq + q] = t4[q];
-        } else {
-          t4[q] = uw[sq + q];
-        }
-      }
-      w = make_float4(t4[0], t4[1], t4[2], t4[3]);
+      w.x = uw[sq];
+      if (sq + 1 < P.n) w.y = uw[sq + 1];
+      if (sq + 2 < P.n) w.z = uw[sq + 2];
     }
 #pragma unroll 4
     for (int i = 0; i <= j; ++i) {
@@ -177,7 +172,6 @@ __global__ void __launch_bounds__(NT)
       p = warp_sum(p);
       if (wl == 0) wacc[warp][i] += p;
     }
-    if constexpr (SPMV) __syncthreads();
   }
   publish_dots_nt<MAXB, NT>(j, partials, wacc);
   if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
