@@ -222,12 +222,13 @@ enum {
   MDP_PROF_BELLMAN_F32 = 0,  /* K1: FP32 Bellman backup */
   MDP_PROF_BELLMAN_FF = 1,   /* K6: float-float Bellman backup + residual */
   MDP_PROF_POLICY_RESID = 2, /* float-float policy residual (refinement) */
-  MDP_PROF_ARNOLDI_SPMV = 3, /* K2: policy-row SpMV + Gram-Schmidt dots */
+  MDP_PROF_ARNOLDI_SPMV = 3, /* K2: policy-row SpMV w = v_j - gamma P_pi v_j */
   MDP_PROF_ARNOLDI_ORTHO = 4,/* K3 + K4: orthogonalisation, norm, Givens */
   MDP_PROF_GMRES_UPDATE = 5, /* K5: V += sum y_i v_i */
   MDP_PROF_RICHARDSON = 6,   /* modified-PI sweep */
   MDP_PROF_OTHER = 7,        /* conversions, set-up kernels */
-  MDP_PROF_KINDS = 8
+  MDP_PROF_ARNOLDI_DOTS = 8, /* Gram-Schmidt dots <w, v_i> */
+  MDP_PROF_KINDS = 12
 };
 
 typedef struct {

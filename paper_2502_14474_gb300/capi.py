@@ -29,7 +29,8 @@ EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval"
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
-              "gmres_update", "richardson", "other"]
+              "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
+              "unused11"]
 
 
 class MDPError(RuntimeError):
@@ -87,13 +88,15 @@ class mdp_info_t(ctypes.Structure):
 
 
 class mdp_profile_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 8), ("skipped", ctypes.c_int64 * 8),
-                ("ms", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8),
+    _fields_ = [("launches", ctypes.c_int64 * 12), ("skipped", ctypes.c_int64 * 12),
+                ("ms", ctypes.c_double * 12), ("bytes", ctypes.c_double * 12),
                 ("total_launches", ctypes.c_int64)]
 
     def as_dict(self):
         kinds = {}
         for i, name in enumerate(PROF_KINDS):
+            if name.startswith("unused"):
+                continue
             kinds[name] = dict(launches=self.launches[i], skipped=self.skipped[i],
                                ms=self.ms[i], bytes=self.bytes[i])
         return dict(kinds=kinds, total_launches=self.total_launches)

@@ -207,11 +207,12 @@ double bytes_policy_resid(const Mat& A) {
   return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (8.0 + (A.val_lo ? 4.0 : 0.0)) + 4.0 +
               (A.g_lo ? 4.0 : 0.0) + 8.0 + 4.0);
 }
-double bytes_spmv(const Mat& A, bool lp, int j) {
+double bytes_spmv(const Mat& A, bool lp) {
   const double n = A.n;
   return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
-              (lp ? 4.0 : 0.0) + 4.0 + 4.0 + 4.0 * (j + 1));
+              (lp ? 4.0 : 0.0) + 4.0 + 4.0);
 }
+double bytes_dots(const Mat& A, int j) { return 4.0 * A.n * (j + 2); }
 double bytes_ortho(const Mat& A, int j, int cgs2) {
   const double n = A.n;
   const double one = 4.0 * (j + 1) * n + 8.0 * n;
@@ -322,8 +323,11 @@ mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2
                        cudaStream_t s, int* jdone, int* converged) {
   const size_t first = h->prof.pending.size();
   for (int j = 0; j < steps; ++j) {
-    CK(h, run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp, j), j, [&] {
+    CK(h, run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), j, [&] {
          return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
+       }));
+    CK(h, run(h, s, MDP_PROF_ARNOLDI_DOTS, 1, bytes_dots(h->A, j), j, [&] {
+         return launch_arnoldi_dots(h->A, h->basis, h->ld, j, steps, 0, h->partials, h->st, s);
        }));
     CK(h, run(h, s, MDP_PROF_ARNOLDI_ORTHO, cgs2 ? 3 : 1, bytes_ortho(h->A, j, cgs2), j, [&] {
          return launch_arnoldi_ortho(h->A, h->basis, h->ld, j, steps, cgs2, h->partials, h->st, s);

@@ -126,15 +126,19 @@ __global__ void __launch_bounds__(kThreads)
     if (s + 3 < n) {
       float4 w = *reinterpret_cast<const float4*>(uw + s);
       int i = 0;
-      for (; i + 1 <= j; i += 2) {
+      for (; i + 3 <= j; i += 4) {
         const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
         const float4 b1 =
             *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 1) * ld + s);
-        const float c0 = coef[i], c1 = coef[i + 1];
-        w.x = fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x));
-        w.y = fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y));
-        w.z = fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z));
-        w.w = fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w));
+        const float4 b2 =
+            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 2) * ld + s);
+        const float4 b3 =
+            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 3) * ld + s);
+        const float c0 = coef[i], c1 = coef[i + 1], c2 = coef[i + 2], c3 = coef[i + 3];
+        w.x = fmaf(-c3, b3.x, fmaf(-c2, b2.x, fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x))));
+        w.y = fmaf(-c3, b3.y, fmaf(-c2, b2.y, fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y))));
+        w.z = fmaf(-c3, b3.z, fmaf(-c2, b2.z, fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z))));
+        w.w = fmaf(-c3, b3.w, fmaf(-c2, b2.w, fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w))));
       }
       for (; i <= j; ++i) {
         const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
@@ -351,7 +355,7 @@ cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, 
   k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 1, partials, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_arnoldi_dots(A, basis, ld, j, restart, partials, st, s);
+  e = launch_arnoldi_dots(A, basis, ld, j, restart, 1, partials, st, s);
   if (e != cudaSuccess) return e;
   k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 2, partials, st);
   return cudaGetLastError();

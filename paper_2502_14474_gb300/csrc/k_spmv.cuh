@@ -49,11 +49,13 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
   for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
 }
 
-template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, int NT, bool WIN>
+// SPMV && DOTS: fused step; SPMV only: w into u_{j+1}; DOTS only: h_i = <u_{j+1}, v_i>
+// into H(:, j) (out_h2 == 0) or into st->h2 (second Gram-Schmidt pass).
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, bool DOTS, int NT, bool WIN>
 __global__ void __launch_bounds__(NT)
     k_arnoldi_spmv(Csr<IdxT> P, Grid G, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
-                   double* __restrict__ partials, DevState* __restrict__ st) {
+                   int out_h2, double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int TS = 4 * NT;  // states per tile (four passes of NT states)
   constexpr int NV = NT / VW;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(NT)
       }
       __syncthreads();  // the tile's w (global) visible to the block; ring edge complete
     }
+    if constexpr (!DOTS) continue;
     // phase B: thread t owns states s0 + 4t .. s0 + 4t + 3
     const int64_t sq = s0 + 4 * threadIdx.x;
     float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -173,11 +176,14 @@ __global__ void __launch_bounds__(NT)
       if (wl == 0) wacc[warp][i] += p;
     }
   }
-  publish_dots_nt<MAXB, NT>(j, partials, wacc);
-  if (last_block(&st->counter[SPMV ? kCntDots : kCntDots2])) {
-    double* out = SPMV ? st->H + static_cast<int64_t>(j) * kMaxBasis : st->h2;
-    reduce_dots_nt<MAXB, NT>(partials, j, out, st->scale);
-    if (threadIdx.x == 0) st->counter[SPMV ? kCntDots : kCntDots2] = 0;
+  if constexpr (DOTS) {
+    publish_dots_nt<MAXB, NT>(j, partials, wacc);
+    const unsigned cnt = out_h2 ? kCntDots2 : kCntDots;
+    if (last_block(&st->counter[cnt])) {
+      double* out = out_h2 ? st->h2 : st->H + static_cast<int64_t>(j) * kMaxBasis;
+      reduce_dots_nt<MAXB, NT>(partials, j, out, st->scale);
+      if (threadIdx.x == 0) st->counter[cnt] = 0;
+    }
   }
 }
 
@@ -230,10 +236,10 @@ inline int ring_log2_for(int64_t band, int64_t tile, size_t entry, size_t budget
   return lg;
 }
 
-template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, int NT, bool WIN>
+template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, bool DOTS, int NT, bool WIN>
 cudaError_t spmv_launch(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                        int lg, double* partials, DevState* st, cudaStream_t s) {
-  auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV, NT, WIN>;
+                        int out_h2, int lg, double* partials, DevState* st, cudaStream_t s) {
+  auto kern = k_arnoldi_spmv<IdxT, VW, PV, MAXB, SPMV, DOTS, NT, WIN>;
   const size_t smem = WIN ? (size_t(1) << lg) * sizeof(float) : 0;
   if (smem > 0)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -244,53 +250,55 @@ cudaError_t spmv_launch(const Mat& A, const int32_t* pi, float* basis, int64_t l
     occ = 1;
   constexpr int TS = 4 * NT;
   const Grid G = tiles_grid((A.n + TS - 1) / TS, A.num_sms * occ, TS);
-  kern<<<static_cast<unsigned>(tiles_blocks(G)), NT, smem, s>>>(csr_view<IdxT>(A), G, A.band, lg,
-                                                                pi, basis, ld, j, partials, st);
+  kern<<<static_cast<unsigned>(tiles_blocks(G)), NT, smem, s>>>(
+      csr_view<IdxT>(A), G, A.band, lg, pi, basis, ld, j, out_h2, partials, st);
   return cudaGetLastError();
 }
 
-template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV>
-cudaError_t spmv_win_or_not(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                            double* partials, DevState* st, cudaStream_t s) {
-  if (SPMV && A.window) {
+// SpMV only (w into u_{j+1}); the ring window for banded matrices.
+template <typename IdxT, int VW, typename PV>
+cudaError_t spmv_only(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                      double* partials, DevState* st, cudaStream_t s) {
+  if (A.window) {
     constexpr int NT = 512;
     const int lg = ring_log2_for(A.band, 4 * NT, sizeof(float), 64 * 1024);
     if (lg > 0)
-      return spmv_launch<IdxT, VW, PV, MAXB, SPMV, NT, true>(A, pi, basis, ld, j, lg, partials,
-                                                            st, s);
+      return spmv_launch<IdxT, VW, PV, 2, true, false, NT, true>(A, pi, basis, ld, j, 0, lg,
+                                                                  partials, st, s);
   }
-  return spmv_launch<IdxT, VW, PV, MAXB, SPMV, 256, false>(A, pi, basis, ld, j, 0, partials, st,
-                                                          s);
-}
-
-template <typename IdxT, int VW, typename PV, bool SPMV>
-cudaError_t spmv_maxb(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                      int restart, double* partials, DevState* st, cudaStream_t s) {
-  if (restart + 1 <= 32)
-    return spmv_win_or_not<IdxT, VW, PV, 32, SPMV>(A, pi, basis, ld, j, partials, st, s);
-  return spmv_win_or_not<IdxT, VW, PV, kMaxBasis, SPMV>(A, pi, basis, ld, j, partials, st, s);
+  return spmv_launch<IdxT, VW, PV, 2, true, false, 256, false>(A, pi, basis, ld, j, 0, 0,
+                                                                partials, st, s);
 }
 
 // Lanes per row are 2, 4, 8 or 32 (the create-time choice is rounded to these).
-template <typename IdxT, typename PV, bool SPMV>
+template <typename IdxT, typename PV>
 cudaError_t spmv_vw(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                    int restart, double* partials, DevState* st, cudaStream_t s) {
-  if (!SPMV) return spmv_maxb<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+                    double* partials, DevState* st, cudaStream_t s) {
   switch (A.vw) {
     case 1:
-    case 2: return spmv_maxb<IdxT, 2, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    case 4: return spmv_maxb<IdxT, 4, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 2: return spmv_only<IdxT, 2, PV>(A, pi, basis, ld, j, partials, st, s);
+    case 4: return spmv_only<IdxT, 4, PV>(A, pi, basis, ld, j, partials, st, s);
     case 8:
-    case 16: return spmv_maxb<IdxT, 8, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
-    default: return spmv_maxb<IdxT, 32, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+    case 16: return spmv_only<IdxT, 8, PV>(A, pi, basis, ld, j, partials, st, s);
+    default: return spmv_only<IdxT, 32, PV>(A, pi, basis, ld, j, partials, st, s);
   }
 }
 
-template <typename PV, bool SPMV>
+template <typename PV>
 cudaError_t spmv_entry(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                       int restart, double* partials, DevState* st, cudaStream_t s) {
-  return A.idx64 ? spmv_vw<int64_t, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s)
-                 : spmv_vw<int32_t, PV, SPMV>(A, pi, basis, ld, j, restart, partials, st, s);
+                       double* partials, DevState* st, cudaStream_t s) {
+  return A.idx64 ? spmv_vw<int64_t, PV>(A, pi, basis, ld, j, partials, st, s)
+                 : spmv_vw<int32_t, PV>(A, pi, basis, ld, j, partials, st, s);
+}
+
+// Gram-Schmidt dots of the stored u_{j+1} against v_0..v_j.
+inline cudaError_t dots_entry(const Mat& A, float* basis, int64_t ld, int j, int restart,
+                              int out_h2, double* partials, DevState* st, cudaStream_t s) {
+  if (restart + 1 <= 32)
+    return spmv_launch<int32_t, 32, float, 32, false, true, 256, false>(
+        A, nullptr, basis, ld, j, out_h2, 0, partials, st, s);
+  return spmv_launch<int32_t, 32, float, kMaxBasis, false, true, 256, false>(
+      A, nullptr, basis, ld, j, out_h2, 0, partials, st, s);
 }
 
 }  // namespace mdpk

@@ -6,7 +6,8 @@ namespace mdpk {
 cudaError_t launch_arnoldi_spmv_f16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s) {
-  return spmv_entry<__half, true>(A, pi, basis, ld, j, restart, partials, st, s);
+  (void)restart;
+  return spmv_entry<__half>(A, pi, basis, ld, j, partials, st, s);
 }
 
 }  // namespace mdpk

@@ -6,12 +6,13 @@ namespace mdpk {
 cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s) {
-  return spmv_entry<float, true>(A, pi, basis, ld, j, restart, partials, st, s);
+  (void)restart;
+  return spmv_entry<float>(A, pi, basis, ld, j, partials, st, s);
 }
 
 cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, int restart,
-                                double* partials, DevState* st, cudaStream_t s) {
-  return spmv_entry<float, false>(A, nullptr, basis, ld, j, restart, partials, st, s);
+                                int out_h2, double* partials, DevState* st, cudaStream_t s) {
+  return dots_entry(A, basis, ld, j, restart, out_h2, partials, st, s);
 }
 
 }  // namespace mdpk

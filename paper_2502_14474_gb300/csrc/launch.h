@@ -43,7 +43,7 @@ cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, in
 cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2* V, float* r,
                                    double* partials, DevState* st, cudaStream_t s);
 
-// Arnoldi step j (K2): w = v_j - gamma P_pi v_j into u_{j+1}, dots <w, v_i>.
+// Arnoldi step j, SpMV half (K2): w = v_j - gamma P_pi v_j into u_{j+1}.
 // lp: use the 16-bit probabilities with row renormalisation.
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
                                 int64_t ld, int j, int restart, double* partials, DevState* st,
@@ -58,9 +58,10 @@ cudaError_t launch_arnoldi_spmv_bf16(const Mat& A, const int32_t* pi, float* bas
 cudaError_t launch_arnoldi_spmv_f16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s);
-// Dots only (second Gram-Schmidt pass): st->h2[i] = <u_{j+1}, v_i>.
+// Gram-Schmidt dots of u_{j+1} against v_0..v_j: into H(:, j) (out_h2 == 0)
+// or st->h2 (second pass of CGS2).
 cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, int restart,
-                                double* partials, DevState* st, cudaStream_t s);
+                                int out_h2, double* partials, DevState* st, cudaStream_t s);
 
 // K3 (+K4 in its last block): w -= sum h_i v_i, ||w||, Givens, convergence.
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
