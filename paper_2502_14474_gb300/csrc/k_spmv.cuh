@@ -32,14 +32,19 @@ __device__ __forceinline__ void publish_dots_nt(int j, double* partials,
   }
 }
 
+// Last block: h_i = scale_i * sum over blocks of partial i, for i <= j.  Warp w
+// reduces dots i = w, w + NT/32, ...: its lanes stride over the blocks and a
+// fixed shuffle tree combines them (deterministic, no serial chain of loads).
 template <int MAXB, int NT>
 __device__ __forceinline__ void reduce_dots_nt(const double* partials, int j, double* out,
                                                const double* scale) {
-  for (int i = threadIdx.x; i <= j; i += NT) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = static_cast<int>(gridDim.x);
+  for (int i = warp; i <= j; i += NT / 32) {
     double s = 0.0;
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b)
-      s += __ldcg(partials + static_cast<int64_t>(b) * MAXB + i);
-    out[i] = s * scale[i];
+    for (int b = lane; b < nb; b += 32) s += __ldcg(partials + static_cast<int64_t>(b) * MAXB + i);
+    s = warp_sum_d(s);
+    if (lane == 0) out[i] = s * scale[i];
   }
 }
 
@@ -52,7 +57,7 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
 // SPMV && DOTS: fused step; SPMV only: w into u_{j+1}; DOTS only: h_i = <u_{j+1}, v_i>
 // into H(:, j) (out_h2 == 0) or into st->h2 (second Gram-Schmidt pass).
 template <typename IdxT, int VW, typename PV, int MAXB, bool SPMV, bool DOTS, int NT, bool WIN>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
     k_arnoldi_spmv(Csr<IdxT> P, Grid G, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
                    int out_h2, double* __restrict__ partials, DevState* __restrict__ st) {
