@@ -74,8 +74,7 @@ struct mdp_s {
   std::atomic<int> cancel{0};
   // owned device memory
   void* rp = nullptr;
-  int32_t* col = nullptr;
-  float* val = nullptr;
+  uint32_t* pk = nullptr;   // packed col/val (groups of 4 entries, 32 bytes)
   float* val_lo = nullptr;
   float* g = nullptr;
   float* g_lo = nullptr;
@@ -226,7 +225,7 @@ double bytes_richardson(const Mat& A, bool lp) {
 }
 
 void free_all(mdp_s* h) {
-  void* ptrs[] = {h->rp, h->col, h->val, h->val_lo, h->g, h->g_lo, h->val16, h->row_scale,
+  void* ptrs[] = {h->rp, h->pk, h->val_lo, h->g, h->g_lo, h->val16, h->row_scale,
                   h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -500,8 +499,8 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   } while (0)
 
   CALLOC(h->rp, static_cast<size_t>(rows + 1) * (idx64 ? 8 : 4));
-  CALLOC(h->col, static_cast<size_t>(nnz) * 4);
-  CALLOC(h->val, static_cast<size_t>(nnz) * 4);
+  const int64_t padded = (nnz + 3) & ~int64_t(3);
+  CALLOC(h->pk, static_cast<size_t>(padded) * 8);
   if (val_t == MDP_F64) CALLOC(h->val_lo, static_cast<size_t>(nnz) * 4);
   CALLOC(h->g, static_cast<size_t>(rows) * 4);
   if (cost_t == MDP_F64) CALLOC(h->g_lo, static_cast<size_t>(rows) * 4);
@@ -511,11 +510,10 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   memset(&init, 0, sizeof(init));
   init.min_len = 0x7fffffff;
   CCK(cudaMemcpyAsync(dflags, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  CCK(cudaMemcpyAsync(h->col, col_in, static_cast<size_t>(nnz) * 4, cudaMemcpyDeviceToDevice, s));
   const double tol = (flags & MDP_FLAG_NO_VALIDATE) ? INFINITY : 1e-5;
-  CCK(launch_prep_rows(n, m, rp_in, h->col, val_in, val_t == MDP_F64, g_in, cost_t == MDP_F64,
+  CCK(launch_prep_rows(n, m, rp_in, col_in, val_in, val_t == MDP_F64, g_in, cost_t == MDP_F64,
                        tol, h->rp, idx64, h->g, h->g_lo, dflags, num_sms, s));
-  CCK(launch_prep_vals(nnz, val_in, val_t == MDP_F64, h->val, h->val_lo, num_sms, s));
+  CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
   PrepFlags fl;
   CCK(cudaMemcpyAsync(&fl, dflags, sizeof(fl), cudaMemcpyDeviceToHost, s));
   CCK(cudaStreamSynchronize(s));
@@ -538,8 +536,8 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   A.m = m;
   A.idx64 = idx64;
   A.rp = h->rp;
-  A.col = h->col;
-  A.val = h->val;
+  A.col = reinterpret_cast<const int32_t*>(h->pk);
+  A.val = reinterpret_cast<const float*>(h->pk);
   A.val_lo = h->val_lo;
   A.g = h->g;
   A.g_lo = h->g_lo;

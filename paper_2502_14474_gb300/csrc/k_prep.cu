@@ -88,17 +88,29 @@ __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __
   if (max_err > 0.0) atomic_max_double_pos(&flags->max_sum_err, max_err);
 }
 
-__global__ void k_prep_vals(int64_t nnz, const void* __restrict__ val, int f64,
-                            float* __restrict__ out, float* __restrict__ out_lo) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nnz;
+// Pack col/val into groups of four entries, 32 bytes each:
+// pk[8g .. 8g+3] = col(4g .. 4g+3), pk[8g+4 .. 8g+7] = val(4g .. 4g+3) as FP32
+// bits; the tail of the last group is zero.  FP64 inputs also store the FP32
+// remainder val - (float)val in val_lo (plain entry order).
+__global__ void k_pack(int64_t nnz, const int32_t* __restrict__ col, const void* __restrict__ val,
+                       int f64, uint32_t* __restrict__ pk, float* __restrict__ val_lo) {
+  const int64_t padded = (nnz + 3) & ~int64_t(3);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < padded;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t slot = ((i >> 2) << 3) + (i & 3);
+    if (i >= nnz) {
+      pk[slot] = 0u;
+      pk[slot + 4] = 0u;
+      continue;
+    }
+    pk[slot] = static_cast<uint32_t>(col[i]);
     if (f64) {
       const double p = static_cast<const double*>(val)[i];
       const float hi = static_cast<float>(p);
-      out[i] = hi;
-      out_lo[i] = static_cast<float>(p - static_cast<double>(hi));
+      pk[slot + 4] = __float_as_uint(hi);
+      val_lo[i] = static_cast<float>(p - static_cast<double>(hi));
     } else {
-      out[i] = static_cast<const float*>(val)[i];
+      pk[slot + 4] = __float_as_uint(static_cast<const float*>(val)[i]);
     }
   }
 }
@@ -120,7 +132,7 @@ struct Round16<__half> {
 // the inner operator c_r * q is stochastic to FP32 rounding.
 template <typename IdxT, typename Q>
 __global__ void k_prep_lowp(int64_t rows, const IdxT* __restrict__ rp, int32_t uniform_len,
-                            const float* __restrict__ val, Q* __restrict__ q,
+                            const float* __restrict__ pk, Q* __restrict__ q,
                             float* __restrict__ scale) {
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -128,7 +140,7 @@ __global__ void k_prep_lowp(int64_t rows, const IdxT* __restrict__ rp, int32_t u
     const int64_t e = uniform_len > 0 ? b + uniform_len : static_cast<int64_t>(rp[r + 1]);
     double sum = 0.0;
     for (int64_t i = b; i < e; ++i) {
-      const Q v = Round16<Q>::q(val[i]);
+      const Q v = Round16<Q>::q(pk[((i >> 2) << 3) + 4 + (i & 3)]);
       q[i] = v;
       sum += static_cast<double>(Round16<Q>::f(v));
     }
@@ -159,9 +171,9 @@ cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const i
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_vals(int64_t nnz, const void* val_in, int val_f64, float* val_out,
-                             float* val_lo_out, int num_sms, cudaStream_t s) {
-  k_prep_vals<<<grid_of(nnz, num_sms), 256, 0, s>>>(nnz, val_in, val_f64, val_out, val_lo_out);
+cudaError_t launch_pack(int64_t nnz, const int32_t* col_in, const void* val_in, int val_f64,
+                        uint32_t* pk, float* val_lo_out, int num_sms, cudaStream_t s) {
+  k_pack<<<grid_of(nnz + 3, num_sms), 256, 0, s>>>(nnz, col_in, val_in, val_f64, pk, val_lo_out);
   return cudaGetLastError();
 }
 

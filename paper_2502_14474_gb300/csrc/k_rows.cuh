@@ -13,15 +13,33 @@
 
 namespace mdpk {
 
+// ---- packed matrix layout ----------------------------------------------------
+// The nonzeros are stored in groups of four, each group 32 bytes:
+//   [col(4e) col(4e+1) col(4e+2) col(4e+3) | val(4e) .. val(4e+3)]
+// over the global entry order (rows are not padded; the last group is).  A row
+// of 16 aligned entries is one contiguous 128-byte line, so gathering the rows
+// of a policy touches whole lines instead of two half-used ones.  `col` and the
+// FP32 `val` below both point at the packed array; these helpers map an entry
+// index to its slot.
+__device__ __forceinline__ int32_t ldcol(const int32_t* pk, int64_t i) {
+  return __ldcs(pk + ((i >> 2) << 3) + (i & 3));
+}
+// Four columns starting at entry i (i a multiple of 4).
+__device__ __forceinline__ int4 ldcol4(const int32_t* pk, int64_t i) {
+  return __ldcs(reinterpret_cast<const int4*>(pk + 2 * i));
+}
+
 // ---- value loads for the three probability storage types ------------------
 template <typename PV>
 struct Ld;
 
 template <>
-struct Ld<float> {
-  static __device__ __forceinline__ float one(const float* p, int64_t i) { return __ldcs(p + i); }
-  static __device__ __forceinline__ float4 four(const float* p, int64_t i) {
-    return __ldcs(reinterpret_cast<const float4*>(p + i));
+struct Ld<float> {  // FP32 values live in the packed array
+  static __device__ __forceinline__ float one(const float* pk, int64_t i) {
+    return __ldcs(pk + ((i >> 2) << 3) + 4 + (i & 3));
+  }
+  static __device__ __forceinline__ float4 four(const float* pk, int64_t i) {
+    return __ldcs(reinterpret_cast<const float4*>(pk + 2 * i + 4));
   }
 };
 
@@ -98,10 +116,10 @@ __device__ __forceinline__ float row_dot_f32(const int32_t* __restrict__ col,
     const int64_t e4 = e & ~int64_t(3);
     const int64_t hend = b4 < e ? b4 : e;
     for (int64_t i = b + lane; i < hend; i += VW)
-      acc = fmaf(Ld<PV>::one(val, i), x(__ldcs(col + i)), acc);
+      acc = fmaf(Ld<PV>::one(val, i), x(ldcol(col, i)), acc);
 #pragma unroll 2
     for (int64_t i = b4 + 4 * lane; i < e4; i += 4 * VW) {
-      const int4 c = __ldcs(reinterpret_cast<const int4*>(col + i));
+      const int4 c = ldcol4(col, i);
       const float4 p = Ld<PV>::four(val, i);
       acc = fmaf(p.x, x(c.x), acc);
       acc = fmaf(p.y, x(c.y), acc);
@@ -110,11 +128,11 @@ __device__ __forceinline__ float row_dot_f32(const int32_t* __restrict__ col,
     }
     const int64_t tb = e4 > b4 ? e4 : b4;
     for (int64_t i = tb + lane; i < e; i += VW)
-      acc = fmaf(Ld<PV>::one(val, i), x(__ldcs(col + i)), acc);
+      acc = fmaf(Ld<PV>::one(val, i), x(ldcol(col, i)), acc);
   } else {
 #pragma unroll 4
     for (int64_t i = b + lane; i < e; i += VW)
-      acc = fmaf(Ld<PV>::one(val, i), x(__ldcs(col + i)), acc);
+      acc = fmaf(Ld<PV>::one(val, i), x(ldcol(col, i)), acc);
   }
   return acc;
 }
@@ -134,7 +152,7 @@ __device__ __forceinline__ void rows_dot_f32_k4vw(const int32_t* __restrict__ co
 #pragma unroll
   for (int u = 0; u < RB; ++u) {
     if (valid[u]) {
-      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
+      c[u] = ldcol4(col, b[u] + 4 * lane);
       p[u] = Ld<PV>::four(val, b[u] + 4 * lane);
     } else {
       c[u] = make_int4(0, 0, 0, 0);
@@ -157,8 +175,8 @@ __device__ __forceinline__ void rows_dot_ff_k4vw(const int32_t* __restrict__ col
 #pragma unroll
   for (int u = 0; u < RB; ++u) {
     if (valid[u]) {
-      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
-      p[u] = __ldcs(reinterpret_cast<const float4*>(val + b[u] + 4 * lane));
+      c[u] = ldcol4(col, b[u] + 4 * lane);
+      p[u] = Ld<float>::four(val, b[u] + 4 * lane);
     } else {
       c[u] = make_int4(0, 0, 0, 0);
       p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -271,7 +289,7 @@ __device__ __forceinline__ void vec_rows_f32(const int32_t* __restrict__ col,
 #pragma unroll
   for (int u = 0; u < VW; ++u) {
     if (valid[u]) {
-      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
+      c[u] = ldcol4(col, b[u] + 4 * lane);
       q[u] = Ld<PV>::four(val, b[u] + 4 * lane);
     } else {
       c[u] = make_int4(0, 0, 0, 0);
@@ -294,8 +312,8 @@ __device__ __forceinline__ void vec_rows_ff(const int32_t* __restrict__ col,
 #pragma unroll
   for (int u = 0; u < VW; ++u) {
     if (valid[u]) {
-      c[u] = __ldcs(reinterpret_cast<const int4*>(col + b[u] + 4 * lane));
-      q[u] = __ldcs(reinterpret_cast<const float4*>(val + b[u] + 4 * lane));
+      c[u] = ldcol4(col, b[u] + 4 * lane);
+      q[u] = Ld<float>::four(val, b[u] + 4 * lane);
     } else {
       c[u] = make_int4(0, 0, 0, 0);
       q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -329,8 +347,8 @@ __device__ __forceinline__ void ff_elem(const int32_t* __restrict__ col,
                                         const float* __restrict__ val,
                                         const float* __restrict__ val_lo, GX V, int64_t i,
                                         float& hi, float& lo) {
-  const float2 v = V(__ldcs(col + i));
-  const float p = __ldcs(val + i);
+  const float2 v = V(ldcol(col, i));
+  const float p = Ld<float>::one(val, i);
   ff_acc(hi, lo, p, v.x, v.y);
   if (val_lo) lo = __fmaf_rn(__ldcs(val_lo + i), v.x, lo);
 }
@@ -349,8 +367,8 @@ __device__ __forceinline__ void row_dot_ff(const int32_t* __restrict__ col,
     for (int64_t i = b + lane; i < hend; i += VW) ff_elem(col, val, val_lo, V, i, hi, lo);
 #pragma unroll 2
     for (int64_t i = b4 + 4 * lane; i < e4; i += 4 * VW) {
-      const int4 c = __ldcs(reinterpret_cast<const int4*>(col + i));
-      const float4 p = __ldcs(reinterpret_cast<const float4*>(val + i));
+      const int4 c = ldcol4(col, i);
+      const float4 p = Ld<float>::four(val, i);
       const float2 v0 = V(c.x), v1 = V(c.y), v2 = V(c.z), v3 = V(c.w);
       ff_acc(hi, lo, p.x, v0.x, v0.y);
       ff_acc(hi, lo, p.y, v1.x, v1.y);

@@ -14,8 +14,8 @@ struct Mat {
   int32_t m = 0;
   int32_t idx64 = 0;        // row pointers are int64
   const void* rp = nullptr;
-  const int32_t* col = nullptr;
-  const float* val = nullptr;
+  const int32_t* col = nullptr;  // packed layout (see k_rows.cuh), viewed as int32
+  const float* val = nullptr;    // the same packed array, viewed as FP32
   const float* val_lo = nullptr;
   const float* g = nullptr;
   const float* g_lo = nullptr;
@@ -102,8 +102,9 @@ cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const i
                              const void* val_in, int val_f64, const void* g_in, int g_f64,
                              double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
                              PrepFlags* flags, int num_sms, cudaStream_t s);
-cudaError_t launch_prep_vals(int64_t nnz, const void* val_in, int val_f64, float* val_out,
-                             float* val_lo_out, int num_sms, cudaStream_t s);
+// Interleave col/val into the packed layout (groups of 4 entries, 32 bytes).
+cudaError_t launch_pack(int64_t nnz, const int32_t* col_in, const void* val_in, int val_f64,
+                        uint32_t* pk, float* val_lo_out, int num_sms, cudaStream_t s);
 cudaError_t launch_prep_lowp(const Mat& A, void* val16, float* row_scale, int store_t,
                              cudaStream_t s);
 
