@@ -103,6 +103,34 @@ __device__ void givens_step(DevState* st, int j, double nrm) {
 // mode 0: CGS with H(:, j), then Givens.  mode 1: first pass of CGS2 (no norm).
 // mode 2: second pass of CGS2 with st->h2 (added into H), then Givens.
 // ---------------------------------------------------------------------------
+// Subtract sum_i c_i u_i from one float4 quad of u_{j+1} (c_i = coef[i]).
+__device__ __forceinline__ float4 ortho_quad(const float* __restrict__ basis, int64_t ld, int j,
+                                             const float* coef, int64_t s, float4 w) {
+  int i = 0;
+  for (; i + 3 <= j; i += 4) {
+    const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
+    const float4 b1 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 1) * ld + s);
+    const float4 b2 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 2) * ld + s);
+    const float4 b3 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 3) * ld + s);
+    const float c0 = coef[i], c1 = coef[i + 1], c2 = coef[i + 2], c3 = coef[i + 3];
+    w.x = fmaf(-c3, b3.x, fmaf(-c2, b2.x, fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x))));
+    w.y = fmaf(-c3, b3.y, fmaf(-c2, b2.y, fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y))));
+    w.z = fmaf(-c3, b3.z, fmaf(-c2, b2.z, fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z))));
+    w.w = fmaf(-c3, b3.w, fmaf(-c2, b2.w, fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w))));
+  }
+  for (; i <= j; ++i) {
+    const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
+    const float c0 = coef[i];
+    w.x = fmaf(-c0, b0.x, w.x);
+    w.y = fmaf(-c0, b0.y, w.y);
+    w.z = fmaf(-c0, b0.z, w.z);
+    w.w = fmaf(-c0, b0.w, w.w);
+  }
+  return w;
+}
+
+// Tile = 8*kThreads states: thread t owns quads t and t + kThreads of the tile
+// (two independent chains of basis loads in flight).
 __global__ void __launch_bounds__(kThreads)
     k_arnoldi_ortho(int64_t n, Grid G, float* __restrict__ basis, int64_t ld, int j, int mode,
                     double* __restrict__ partials, DevState* __restrict__ st) {
@@ -115,47 +143,37 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   float* uw = basis + static_cast<int64_t>(j + 1) * ld;
   float acc = 0.f;
-  // thread-quad q owns states 4q .. 4q+3 (the last quad may be partial)
-  const int64_t nq = (n + 3) / 4;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t q = tile * kThreads + threadIdx.x;
-    if (q >= nq) continue;
-    const int64_t s = 4 * q;
-    if (s + 3 < n) {
-      float4 w = *reinterpret_cast<const float4*>(uw + s);
-      int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
-        const float4 b1 =
-            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 1) * ld + s);
-        const float4 b2 =
-            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 2) * ld + s);
-        const float4 b3 =
-            *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 3) * ld + s);
-        const float c0 = coef[i], c1 = coef[i + 1], c2 = coef[i + 2], c3 = coef[i + 3];
-        w.x = fmaf(-c3, b3.x, fmaf(-c2, b2.x, fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x))));
-        w.y = fmaf(-c3, b3.y, fmaf(-c2, b2.y, fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y))));
-        w.z = fmaf(-c3, b3.z, fmaf(-c2, b2.z, fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z))));
-        w.w = fmaf(-c3, b3.w, fmaf(-c2, b2.w, fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w))));
-      }
-      for (; i <= j; ++i) {
-        const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
-        const float c0 = coef[i];
-        w.x = fmaf(-c0, b0.x, w.x);
-        w.y = fmaf(-c0, b0.y, w.y);
-        w.z = fmaf(-c0, b0.z, w.z);
-        w.w = fmaf(-c0, b0.w, w.w);
-      }
-      *reinterpret_cast<float4*>(uw + s) = w;
-      acc = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, acc))));
+    const int64_t s_a = tile * (8 * kThreads) + 4 * threadIdx.x;
+    const int64_t s_b = s_a + 4 * kThreads;
+    if (s_b + 3 < n) {
+      float4 wa = *reinterpret_cast<const float4*>(uw + s_a);
+      float4 wb = *reinterpret_cast<const float4*>(uw + s_b);
+      wa = ortho_quad(basis, ld, j, coef, s_a, wa);
+      wb = ortho_quad(basis, ld, j, coef, s_b, wb);
+      *reinterpret_cast<float4*>(uw + s_a) = wa;
+      *reinterpret_cast<float4*>(uw + s_b) = wb;
+      acc = fmaf(wa.x, wa.x, fmaf(wa.y, wa.y, fmaf(wa.z, wa.z, fmaf(wa.w, wa.w, acc))));
+      acc = fmaf(wb.x, wb.x, fmaf(wb.y, wb.y, fmaf(wb.z, wb.z, fmaf(wb.w, wb.w, acc))));
     } else {
-      for (int64_t t = s; t < n; ++t) {
-        float w = uw[t];
-        for (int i = 0; i <= j; ++i) w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + t], w);
-        uw[t] = w;
-        acc = fmaf(w, w, acc);
+      // ragged end of the vector: each quad on its own, scalar past the last full quad
+      for (int64_t sq : {s_a, s_b}) {
+        if (sq + 3 < n) {
+          float4 w = *reinterpret_cast<const float4*>(uw + sq);
+          w = ortho_quad(basis, ld, j, coef, sq, w);
+          *reinterpret_cast<float4*>(uw + sq) = w;
+          acc = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, acc))));
+        } else {
+          for (int64_t t = sq; t < n && t < sq + 4; ++t) {
+            float w = uw[t];
+            for (int i = 0; i <= j; ++i)
+              w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + t], w);
+            uw[t] = w;
+            acc = fmaf(w, w, acc);
+          }
+        }
       }
     }
   }
@@ -346,7 +364,8 @@ static Grid stream_grid(int64_t n, int num_sms, int occ) {
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
                                  int cgs2, double* partials, DevState* st, cudaStream_t s) {
   static int occ = occ_of(k_arnoldi_ortho);
-  const Grid G = stream_grid(A.n, A.num_sms, occ);
+  const Grid G = grid_for((A.n + 8 * kThreads - 1) / (8 * kThreads), A.num_sms * occ,
+                          8 * kThreads);
   const unsigned nb = static_cast<unsigned>(grid_blocks(G));
   if (!cgs2) {
     k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 0, partials, st);
