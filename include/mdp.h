@@ -248,6 +248,33 @@ mdp_status mdp_profile_enable(mdp_t h, int on);
 /* Aggregate the counters since the last enable (synchronises pending events). */
 mdp_status mdp_profile_read(mdp_t h, mdp_profile_t* out);
 
+/*
+ * mdp_bellman_noalloc -- one FP32 Bellman backup (as mdp_bellman with v_t =
+ * MDP_F32) computed directly on a caller's CSR, allocating no memory at all.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code whose device memory belongs to
+ * another allocator or a fixed budget (a framework's caching allocator, a
+ * request loop's admission budget), or a latency-critical thread that may not
+ * call cudaMalloc/cudaFree because they can synchronise the whole device.
+ *   n_states, n_actions, row_ptr (int64[n*m+1]), col (int32[nnz]), val
+ *   (float[nnz]), cost (float[n*m]): the CSR as mdp_create takes it, device
+ *   pointers, read in place (not validated for stochasticity; out-of-range row
+ *   pointers or columns are skipped and reported as MDP_ERR_BAD_CSR).
+ *   gamma in [0, 1).  V_in float[n]; V_out float[n] (not aliasing V_in),
+ *   pi_out int32[n] and r_out float[n] may be NULL; res_inf, res_2 host
+ *   doubles or NULL (FP64 fixed-order reduction).  Synchronises the stream.
+ * Scratch: a file-scope device array of 262,400 bytes per device that loads
+ * the library (held until exit), enough for n_states <= 4,194,304; larger
+ * problems are rejected with MDP_ERR_ARG.  The first call on a device looks
+ * the array up with cudaGetSymbolAddress, so it should come before any stream
+ * capture.  All calls on a device share the array: calls whose kernels overlap
+ * on the GPU race and must be serialised by the caller.
+ */
+mdp_status mdp_bellman_noalloc(int64_t n_states, int32_t n_actions, const int64_t* row_ptr,
+                               const int32_t* col, const float* val, const float* cost,
+                               double gamma, const float* V_in, float* V_out, int32_t* pi_out,
+                               float* r_out, double* res_inf, double* res_2, void* stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* mdp_last_error(void);
 

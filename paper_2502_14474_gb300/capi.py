@@ -26,7 +26,8 @@ MDP_HISTORY = 128
 # Every symbol include/mdp.h declares (checked by the tests).
 EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
-                   "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read"])
+                   "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
+                   "mdp_bellman_noalloc"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
               "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
@@ -154,6 +155,9 @@ def load(build_if_missing: bool = True):
         lib.mdp_profile_enable.restype = ctypes.c_int
         lib.mdp_profile_read.argtypes = [P, ctypes.POINTER(mdp_profile_t)]
         lib.mdp_profile_read.restype = ctypes.c_int
+        lib.mdp_bellman_noalloc.argtypes = [I64, I32, P, P, P, P, D, P, P, P, P,
+                                            ctypes.POINTER(D), ctypes.POINTER(D), P]
+        lib.mdp_bellman_noalloc.restype = ctypes.c_int
         lib.mdp_last_error.argtypes = []
         lib.mdp_last_error.restype = ctypes.c_char_p
         lib.mdp_version.argtypes = []
@@ -278,3 +282,16 @@ def mdp_profile_read(h) -> dict:
     p = mdp_profile_t()
     _check(load().mdp_profile_read(h, ctypes.byref(p)))
     return p.as_dict()
+
+
+def mdp_bellman_noalloc(n_states, n_actions, row_ptr, col, val, cost, gamma, V_in, V_out=None,
+                        pi_out=None, r_out=None, stream=None):
+    """FP32 Bellman backup on a caller's CSR without any allocation; returns
+    (res_inf, res_2).  See include/mdp.h for the scratch limit and sharing."""
+    ri, r2 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().mdp_bellman_noalloc(int(n_states), int(n_actions), _ptr(row_ptr), _ptr(col),
+                                    _ptr(val), _ptr(cost), float(gamma), _ptr(V_in), _ptr(V_out),
+                                    _ptr(pi_out), _ptr(r_out), ctypes.byref(ri),
+                                    ctypes.byref(r2), _stream(stream))
+    _check(rc)
+    return ri.value, r2.value

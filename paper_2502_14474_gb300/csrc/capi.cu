@@ -67,6 +67,9 @@ struct Prof {
 
 }  // namespace
 
+// Message hook for entry points defined in other translation units.
+void mdpk_set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct mdp_s {
   int device = 0;
   Mat A;
