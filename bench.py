@@ -51,6 +51,8 @@ def _args():
                    help="only run N float-float Bellman backups (for ncu captures)")
     p.add_argument("--profile-solve", action="store_true",
                    help="one solve, nothing else (for ncu launch lists)")
+    p.add_argument("--no-profile", action="store_true",
+                   help="no per-kernel events in the timed region (roofline omitted)")
     return p.parse_args()
 
 
@@ -125,6 +127,31 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def _traffic_record(kernel, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None when
+    the record is for another kernel or size, or the kernel's sources changed."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    try:
+        rec = {}
+        for line in open(path):
+            line = line.strip()
+            if line and not line.startswith("#") and "=" in line:
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("kernel") != kernel or int(rec.get("scaled_n", -1)) != n:
+            return None
+        h = hashlib.sha256()
+        for f in rec["sources"].split():
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != rec.get("sources_sha256"):
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _workload(n=None, s0=0, s1=None):
@@ -229,7 +256,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
                            if ws == 1 else local)
-    h.profile(True)
+    h.profile(not args.no_profile)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -263,12 +290,13 @@ def main():
     peak, peak_src = _peaks()
     achieved = (dk["bytes"] / dk["launches"]) / (dk["ms"] / dk["launches"] / 1e3) / 1e9 \
         if dk["launches"] else 0.0
+    traffic = _traffic_record(dom, host.n)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic,
                 "bytes_per_launch": dk["bytes"] / max(1, dk["launches"]),
                 "ms_per_launch": dk["ms"] / max(1, dk["launches"]),
-                "launches": dk["launches"]}
+                "launches": dk["launches"]} if not args.no_profile else None
     per_kernel = {k: {"launches": v["launches"], "skipped": v["skipped"],
                       "ms_total": round(v["ms"], 3),
                       "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"]
