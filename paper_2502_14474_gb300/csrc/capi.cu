@@ -557,10 +557,17 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   // (With aligned starts every row splits the same way, so a row's summation
   // order depends only on its entries: identical rows give identical sums and
   // exact ties resolve to the lowest action.)
+  // Rows of uniform length 4*VW (VW <= 4) with aligned starts take the
+  // VW-rows-per-vector fast path; other rows of fewer than 24 entries on
+  // average are read by one thread each in whole packed groups; longer rows
+  // are split over lanes.
   const double mean = static_cast<double>(nnz) / static_cast<double>(rows);
   A.vec4 = (mean >= 12.0 && h->aligned) ? 1 : 0;
   int vw = pow2_floor(std::max(1, static_cast<int>(std::lround(A.vec4 ? mean / 4.0 : mean))));
   A.vw = std::min(32, std::max(1, vw));
+  const bool fast = A.vec4 && fl.min_len == fl.max_len && (fl.min_len == 8 || fl.min_len == 16);
+  if (!fast && mean < 24.0) A.vw = 1;
+  if (fast) A.vw = fl.min_len / 4;
   A.band = h->band;
   // stage V in shared memory when the band window fits (2*band + 2*tile <= 16384
   // float-float slots) and the matrix is large enough to amortise the fills
@@ -570,7 +577,8 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   h->store_t = store_t;
   A.store_t = store_t;
   if (store_t == MDP_BF16 || store_t == MDP_F16) {
-    CALLOC(h->val16, static_cast<size_t>(nnz) * 2);
+    CALLOC(h->val16, static_cast<size_t>(padded) * 2);  // group loads read whole quads
+    CCK(cudaMemsetAsync(h->val16, 0, static_cast<size_t>(padded) * 2, s));
     CALLOC(h->row_scale, static_cast<size_t>(rows) * 4);
     CCK(launch_prep_lowp(A, h->val16, h->row_scale, store_t, s));
     A.val16 = h->val16;

@@ -105,11 +105,64 @@ struct RingFF {
   __device__ __forceinline__ float2 operator()(int32_t c) const { return buf[c & mask]; }
 };
 
+// ---- one thread per row, whole packed groups --------------------------------
+// For short or unaligned rows: the thread loads every 4-entry group that
+// overlaps [b, e) with one int4 of columns and one 4-value load, and adds the
+// entries inside the row strictly in entry order (so identical rows give
+// identical sums whatever their alignment).  Entries outside the row are not
+// gathered.  The value array must be padded to a multiple of 4 entries.
+template <typename PV, typename GX>
+__device__ __forceinline__ float row_dot_f32_g1(const int32_t* __restrict__ col,
+                                                const PV* __restrict__ val, GX x, int64_t b,
+                                                int64_t e) {
+  float acc = 0.f;
+  const int64_t g1 = (e + 3) >> 2;
+#pragma unroll 2
+  for (int64_t g = b >> 2; g < g1; ++g) {
+    const int64_t i0 = g << 2;
+    const int4 c = ldcol4(col, i0);
+    const float4 p = Ld<PV>::four(val, i0);
+    if (i0 >= b) acc = fmaf(p.x, x(c.x), acc);
+    if (i0 + 1 >= b && i0 + 1 < e) acc = fmaf(p.y, x(c.y), acc);
+    if (i0 + 2 >= b && i0 + 2 < e) acc = fmaf(p.z, x(c.z), acc);
+    if (i0 + 3 >= b && i0 + 3 < e) acc = fmaf(p.w, x(c.w), acc);
+  }
+  return acc;
+}
+
+template <typename GX>
+__device__ __forceinline__ void row_dot_ff_g1(const int32_t* __restrict__ col,
+                                              const float* __restrict__ val,
+                                              const float* __restrict__ val_lo, GX V, int64_t b,
+                                              int64_t e, float& hi, float& lo) {
+  hi = 0.f;
+  lo = 0.f;
+  const int64_t g1 = (e + 3) >> 2;
+#pragma unroll 2
+  for (int64_t g = b >> 2; g < g1; ++g) {
+    const int64_t i0 = g << 2;
+    const int4 c = ldcol4(col, i0);
+    const float4 p = Ld<float>::four(val, i0);
+    const int cc[4] = {c.x, c.y, c.z, c.w};
+    const float pp[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + q;
+      if (i >= b && i < e) {
+        const float2 v = V(cc[q]);
+        ff_acc(hi, lo, pp[q], v.x, v.y);
+        if (val_lo) lo = __fmaf_rn(__ldcs(val_lo + i), v.x, lo);
+      }
+    }
+  }
+}
+
 // ---- FP32 dot: sum val[e] * x[col[e]] over this lane's share of [b, e) -----
 template <int VW, typename PV, typename GX>
 __device__ __forceinline__ float row_dot_f32(const int32_t* __restrict__ col,
                                              const PV* __restrict__ val, GX x, int64_t b,
                                              int64_t e, int lane, bool vec4) {
+  if constexpr (VW == 1) return row_dot_f32_g1<PV, GX>(col, val, x, b, e);
   float acc = 0.f;
   if (vec4) {
     const int64_t b4 = (b + 3) & ~int64_t(3);
@@ -358,6 +411,10 @@ __device__ __forceinline__ void row_dot_ff(const int32_t* __restrict__ col,
                                            const float* __restrict__ val,
                                            const float* __restrict__ val_lo, GX V, int64_t b,
                                            int64_t e, int lane, bool vec4, float& hi, float& lo) {
+  if constexpr (VW == 1) {
+    row_dot_ff_g1<GX>(col, val, val_lo, V, b, e, hi, lo);
+    return;
+  }
   hi = 0.f;
   lo = 0.f;
   if (vec4 && !val_lo) {

@@ -346,7 +346,7 @@ template <typename IdxT, typename PV>
 cudaError_t spmv_vw(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
                     double* partials, DevState* st, cudaStream_t s) {
   switch (A.vw) {
-    case 1:
+    case 1: return spmv_only<IdxT, 1, PV>(A, pi, basis, ld, j, partials, st, s);
     case 2: return spmv_only<IdxT, 2, PV>(A, pi, basis, ld, j, partials, st, s);
     case 4: return spmv_only<IdxT, 4, PV>(A, pi, basis, ld, j, partials, st, s);
     case 8:
