@@ -53,6 +53,13 @@ def _args():
                    help="one solve, nothing else (for ncu launch lists)")
     p.add_argument("--no-profile", action="store_true",
                    help="no per-kernel events in the timed region (roofline omitted)")
+    p.add_argument("--workload", choices=["banded4m", "grid4096"], default="banded4m",
+                   help="banded4m: the headline MDP; grid4096: the 4096^2 grid world of the "
+                        "precision path (gamma = 0.999)")
+    p.add_argument("--store", choices=["f32", "bf16", "f16"], default="f32",
+                   help="probabilities of the inner GMRES SpMV")
+    p.add_argument("--inner-norm", choices=["2", "inf"], default="2")
+    p.add_argument("--max-inner", type=int, default=10000)
     return p.parse_args()
 
 
@@ -154,8 +161,14 @@ def _traffic_record(kernel, n):
         return None
 
 
+WORKLOAD = "banded4m"
+
+
 def _workload(n=None, s0=0, s1=None):
     import synth
+    if WORKLOAD == "grid4096":
+        side = int(round(n ** 0.5)) if n else None
+        return synth.grid_4096(s0=s0, s1=s1, side=side)
     return synth.banded_4m(n=n, s0=s0, s1=s1)
 
 
@@ -215,7 +228,9 @@ def run_reference(args):
 
 
 def main():
+    global WORKLOAD
     args = _args()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -229,9 +244,10 @@ def main():
 
     host = _workload(n=args.n)
     nnz = host.nnz
-    h = MDP.from_csr(host)
+    h = MDP.from_csr(host, store=args.store)
     dev = torch.device("cuda", local)
-    opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart)
+    opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart, inner_norm=args.inner_norm,
+                max_inner=args.max_inner)
 
     if args.profile_bellman:
         V = torch.zeros(host.n, dtype=torch.float64, device=dev)
@@ -331,7 +347,7 @@ def main():
 
         def one():
             m = MDP(host.n, host.m, hp["row_ptr"].numpy(), hp["col"].numpy(), hp["val"].numpy(),
-                    hp["g"].numpy(), host.gamma)
+                    hp["g"].numpy(), host.gamma, store=args.store)
             Vd, pid, s = m.solve(**opts)
             Vh.copy_(Vd, non_blocking=True)
             pih.copy_(pid, non_blocking=True)
@@ -367,8 +383,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": host.name, "n_states": host.n, "m": host.m, "nnz": nnz,
-                       "successors": 16, "band": 4096, "gamma": host.gamma, "seed": 2,
+                       "gamma": host.gamma, "seed": 2 if args.workload == "banded4m" else 3,
                        "tol": args.tol, "inner": f"gmres({args.restart})", "eta": 0.1,
+                       "inner_norm": args.inner_norm, "max_inner": args.max_inner,
+                       "inner_probabilities": args.store,
                        "outer_iterate": "float-float (hi+lo FP32)", "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{ws}"},
             "time_to_tol_s": ms_max / args.steps / 1e3,

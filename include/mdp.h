@@ -90,6 +90,10 @@ typedef struct {
   int32_t inner;        /* mdp_inner, default MDP_INNER_GMRES */
   int32_t cgs2;         /* 1 = re-orthogonalise once (classical Gram-Schmidt twice) */
   int32_t low_precision_inner; /* 1 = inner SpMV on the BF16/FP16 copy (needs store_t) */
+  int32_t inner_norm;   /* 0: stop the inner GMRES on its 2-norm residual estimate
+                           <= eta * ||T V - V||_inf (default, conservative);
+                           1: additionally stop after any restart cycle whose explicit
+                           policy residual has ||.||_inf <= eta * ||T V - V||_inf */
 } mdp_solve_opts;
 
 #define MDP_HISTORY 128

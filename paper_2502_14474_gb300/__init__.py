@@ -144,7 +144,7 @@ class MDP:
 
     def solve(self, tol=1e-9, inner_rtol=0.1, restart=30, max_outer=1000, max_inner=10000,
               inner="gmres", cgs2=False, low_precision_inner=None, V_init=None,
-              raise_on_not_converged=True):
+              raise_on_not_converged=True, inner_norm="2"):
         """Inexact policy iteration; returns (V float64, pi int32, stats dict)."""
         torch = _torch()
         o = mdp_default_opts()
@@ -155,6 +155,7 @@ class MDP:
         if low_precision_inner is None:
             low_precision_inner = self.store != "f32"
         o.low_precision_inner = 1 if low_precision_inner else 0
+        o.inner_norm = 1 if str(inner_norm) in ("inf", "1") else 0
         V = torch.empty(self.n, dtype=torch.float64, device=self.device)
         pi = torch.empty(self.n, dtype=torch.int32, device=self.device)
         vt = _dtype_code(V_init) if V_init is not None else MDP_F64

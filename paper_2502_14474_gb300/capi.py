@@ -45,7 +45,8 @@ class mdp_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("restart", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_inner", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("cgs2", ctypes.c_int32), ("low_precision_inner", ctypes.c_int32)]
+                ("cgs2", ctypes.c_int32), ("low_precision_inner", ctypes.c_int32),
+                ("inner_norm", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):

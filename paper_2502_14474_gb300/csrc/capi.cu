@@ -383,6 +383,7 @@ void mdp_default_opts(mdp_solve_opts* o) {
   o->inner = MDP_INNER_GMRES;
   o->cgs2 = 0;
   o->low_precision_inner = 0;
+  o->inner_norm = 0;
 }
 
 size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, mdp_dtype store_t,
@@ -761,6 +762,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_ERR_ARG, "bad iteration limits");
   if (o.inner != MDP_INNER_GMRES && o.inner != MDP_INNER_RICHARDSON)
     return fail(MDP_ERR_ARG, "unknown inner solver");
+  if (o.inner_norm != 0 && o.inner_norm != 1) return fail(MDP_ERR_ARG, "inner_norm is 0 or 1");
   const bool lp = o.low_precision_inner != 0;
   if (lp && !h->val16) return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
   DeviceGuard dg(h->device);
@@ -844,6 +846,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
         rc = read_head(h, s);
         if (rc != MDP_OK) return rc;
         if (!h->head->active) break;  // already below the target
+        if (o.inner_norm == 1 && h->head->res_inf <= target) break;
       }
       if (o.restart != std::min(o.restart, o.max_inner)) {
         rc = set_cycle(h, o.restart, 1, o.inner_rtol, 0.0, 0, s);
