@@ -72,6 +72,9 @@ typedef enum {
 /* mdp_create flags */
 #define MDP_FLAG_HOST_INPUT 0x1ull   /* row_ptr, col, val, cost are host pointers */
 #define MDP_FLAG_NO_VALIDATE 0x2ull  /* skip the stochasticity check (CSR checks stay) */
+#define MDP_FLAG_AUTOTUNE 0x4ull     /* time the candidate lanes-per-row / shared-memory window
+                                        schedules of the Bellman kernel at create and keep the
+                                        fastest (cached per process by matrix shape) */
 
 /* Inner solver of the policy-evaluation step (madupite: "selecting among a wide
  * range of inner solvers for the approximate policy evaluation step"). */
@@ -206,6 +209,26 @@ void mdp_default_opts(mdp_solve_opts* opts);
  */
 mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts, const void* V_init, mdp_dtype vinit_t,
                      double* V_out, int32_t* pi_out, mdp_solve_stats* st, void* stream);
+
+/*
+ * mdp_batch_solve -- solve `count` independent MDPs (one handle each) with the
+ * inexact policy iteration of mdp_solve, concurrently: `n_streams` host
+ * workers each own a CUDA stream and take the next MDP from a shared counter,
+ * so the kernels of different (often small, uneven) MDPs overlap on the GPU.
+ *   hs[count]      distinct handles (each solved once; not shared across calls).
+ *   opts           NULL = defaults, used for every MDP.
+ *   V_out[i]       double[n_i] device;  pi_out[i] int32[n_i] device or NULL
+ *                  (pi_out itself may be NULL);  stats[count] host or NULL.
+ *   n_streams      1..64 concurrent workers (0 = 8).
+ * Every per-MDP result equals what mdp_solve returns for that MDP alone: the
+ * handles share no state and every reduction has a fixed order.  Returns
+ * MDP_OK when all converged, else the first non-OK status in index order
+ * (per-MDP statuses in status_out[count] when it is not NULL).  Returns after
+ * all work is complete.
+ */
+mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts* opts,
+                           double* const* V_out, int32_t* const* pi_out, mdp_solve_stats* stats,
+                           mdp_status* status_out, int32_t n_streams);
 
 /* Handle properties (layout chosen at create, memory held). */
 mdp_status mdp_info(mdp_t h, mdp_info_t* info);

@@ -59,7 +59,7 @@ class MDP:
     """
 
     def __init__(self, n, m, row_ptr, col, val, cost, gamma, store="f32", stream=None,
-                 validate=True, device=None):
+                 validate=True, device=None, autotune=False):
         torch = _torch()
         self.n, self.m, self.gamma = int(n), int(m), float(gamma)
         host = isinstance(row_ptr, np.ndarray)
@@ -77,6 +77,7 @@ class MDP:
         self.device = torch.device(device) if device is not None else (
             torch.device("cuda", torch.cuda.current_device()) if host else row_ptr.device)
         flags = (MDP_FLAG_HOST_INPUT if host else 0) | (0 if validate else MDP_FLAG_NO_VALIDATE)
+        flags |= capi.MDP_FLAG_AUTOTUNE if autotune else 0
         self.stream = stream
         with torch.cuda.device(self.device):
             self.h = mdp_create(n, m, row_ptr, col, val, _dtype_code(val), cost, _dtype_code(cost),
@@ -84,16 +85,17 @@ class MDP:
         self.store = store
 
     @classmethod
-    def from_csr(cls, mdp, store="f32", device="cuda", host_input=False, validate=True):
+    def from_csr(cls, mdp, store="f32", device="cuda", host_input=False, validate=True,
+                 autotune=False, stream=None):
         """Build from an object with n, m, gamma, row_ptr, col, val, g (numpy)."""
         torch = _torch()
         if host_input:
             return cls(mdp.n, mdp.m, mdp.row_ptr, mdp.col, mdp.val, mdp.g, mdp.gamma, store=store,
-                       validate=validate, device=device)
+                       validate=validate, device=device, autotune=autotune, stream=stream)
         dev = torch.device(device)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         return cls(mdp.n, mdp.m, t(mdp.row_ptr), t(mdp.col), t(mdp.val), t(mdp.g), mdp.gamma,
-                   store=store, validate=validate)
+                   store=store, validate=validate, autotune=autotune, stream=stream)
 
     def _s(self):
         torch = _torch()

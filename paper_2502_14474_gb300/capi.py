@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_ARG", 2: "MDP_ERR_NOT_STOCHASTIC", 3: "
                 7: "MDP_ERR_CANCELLED", 8: "MDP_ERR_BAD_CSR", 9: "MDP_ERR_NONFINITE"}
 MDP_FLAG_HOST_INPUT = 0x1
 MDP_FLAG_NO_VALIDATE = 0x2
+MDP_FLAG_AUTOTUNE = 0x4
 MDP_INNER_GMRES, MDP_INNER_RICHARDSON = 0, 1
 MDP_HISTORY = 128
 
@@ -27,7 +28,7 @@ MDP_HISTORY = 128
 EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
-                   "mdp_bellman_noalloc"])
+                   "mdp_bellman_noalloc", "mdp_batch_solve"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
               "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
@@ -159,6 +160,9 @@ def load(build_if_missing: bool = True):
         lib.mdp_bellman_noalloc.argtypes = [I64, I32, P, P, P, P, D, P, P, P, P,
                                             ctypes.POINTER(D), ctypes.POINTER(D), P]
         lib.mdp_bellman_noalloc.restype = ctypes.c_int
+        lib.mdp_batch_solve.argtypes = [P, I32, ctypes.POINTER(mdp_solve_opts), P, P,
+                                        ctypes.POINTER(mdp_solve_stats), P, I32]
+        lib.mdp_batch_solve.restype = ctypes.c_int
         lib.mdp_last_error.argtypes = []
         lib.mdp_last_error.restype = ctypes.c_char_p
         lib.mdp_version.argtypes = []
@@ -296,3 +300,20 @@ def mdp_bellman_noalloc(n_states, n_actions, row_ptr, col, val, cost, gamma, V_i
                                     ctypes.byref(r2), _stream(stream))
     _check(rc)
     return ri.value, r2.value
+
+
+def mdp_batch_solve(handles, V_outs, pi_outs=None, opts=None, n_streams=8,
+                    raise_on_error=True):
+    """Solve independent MDPs concurrently; returns (per-MDP stats dicts, statuses)."""
+    count = len(handles)
+    H = (ctypes.c_void_p * max(count, 1))(*handles)
+    Vp = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in V_outs])
+    Pp = (ctypes.c_void_p * max(count, 1))(*[_ptr(p) for p in pi_outs]) if pi_outs else None
+    st = (mdp_solve_stats * max(count, 1))()
+    status = (ctypes.c_int * max(count, 1))()
+    rc = load().mdp_batch_solve(H, count, ctypes.byref(opts) if opts is not None else None, Vp,
+                                Pp, st, status, int(n_streams))
+    if rc != MDP_OK and raise_on_error:
+        _check(rc)
+    return [st[i].as_dict() for i in range(count)], [STATUS_NAMES.get(status[i], status[i])
+                                                     for i in range(count)]

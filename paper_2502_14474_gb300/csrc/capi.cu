@@ -14,7 +14,11 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mdp.h"
@@ -250,6 +254,31 @@ void free_all(mdp_s* h) {
     }                                                                                           \
   } while (0)
 
+// ---- autotuner -----------------------------------------------------------------
+// Schedules of the CSR kernels: lanes per row (vw) and the shared-memory window
+// for banded matrices.  Candidates are timed on the float-float Bellman kernel
+// (CUDA events, best of 3 after 2 warm-up launches); the winner is cached per
+// process by matrix shape so that similar matrices are not re-tuned.
+struct TuneKey {
+  int64_t n_bucket, mean_x4, band_bucket;
+  int32_t m, uniform_len, vec4, idx64;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n_bucket, mean_x4, band_bucket, m, uniform_len, vec4, idx64) <
+           std::tie(o.n_bucket, o.mean_x4, o.band_bucket, o.m, o.uniform_len, o.vec4, o.idx64);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+int64_t log2_bucket(int64_t x) {
+  int64_t b = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++b;
+  }
+  return b;
+}
+
 size_t partials_len(int num_sms) { return static_cast<size_t>(num_sms) * 8 * (kMaxBasis + 1); }
 
 mdp_status ensure_basis(mdp_s* h, int restart) {
@@ -262,6 +291,63 @@ mdp_status ensure_basis(mdp_s* h, int restart) {
   ALLOC(h, h->basis, static_cast<size_t>(restart + 1) * h->ld * sizeof(float));
   h->restart_cap = restart;
   return MDP_OK;
+}
+
+cudaError_t autotune(mdp_s* h, float* scratch_r, cudaStream_t s) {
+  Mat& A = h->A;
+  TuneKey key{log2_bucket(A.n), static_cast<int64_t>(4.0 * A.nnz / A.rows), log2_bucket(A.band + 1),
+              A.m, A.uniform_len, A.vec4, A.idx64};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      A.vw = it->second.first;
+      A.window = it->second.second;
+      return cudaSuccess;
+    }
+  }
+  std::vector<std::pair<int, int>> cand;
+  const int window0 = A.window;
+  for (int vw : {1, 2, 4, 8, 32}) {
+    // the uniform fast path needs rows of exactly 4*vw aligned entries
+    if (A.vec4 && A.uniform_len > 0 && vw <= 4 && A.uniform_len != 4 * vw && vw != 1) continue;
+    cand.push_back({vw, window0});
+    if (window0) cand.push_back({vw, 0});
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t err = cudaMemsetAsync(h->V, 0, static_cast<size_t>(A.n) * sizeof(float2), s);
+  float best = 1e30f;
+  std::pair<int, int> pick{A.vw, A.window};
+  for (auto c : cand) {
+    A.vw = c.first;
+    A.window = c.second;
+    float t_best = 1e30f;
+    for (int it = 0; it < 5 && err == cudaSuccess; ++it) {
+      cudaEventRecord(e0, s);
+      err = launch_bellman(A, true, h->V, nullptr, h->pi, scratch_r, h->partials, h->st, 0, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (it >= 2) t_best = std::min(t_best, ms);
+    }
+    if (err != cudaSuccess) break;
+    if (t_best < best) {
+      best = t_best;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  A.vw = pick.first;
+  A.window = pick.second;
+  if (err == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = pick;
+  }
+  return err;
 }
 
 mdp_status ensure_richardson(mdp_s* h) {
@@ -601,6 +687,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
     return bail(fail(MDP_ERR_OOM, "pinned host allocation failed"));
   }
   if (ensure_basis(h, 30) != MDP_OK) return bail(MDP_ERR_OOM);
+  if (flags & MDP_FLAG_AUTOTUNE) CCK(autotune(h, h->basis, s));
   CCK(cudaStreamSynchronize(s));
 #undef CALLOC
 #undef CCK
@@ -889,6 +976,62 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   ss.transitions = transitions;
   if (stats) *stats = ss;
   return result;
+}
+
+mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts* opts,
+                           double* const* V_out, int32_t* const* pi_out, mdp_solve_stats* stats,
+                           mdp_status* status_out, int32_t n_streams) {
+  if (count < 0 || (count > 0 && (!hs || !V_out)))
+    return fail(MDP_ERR_ARG, "mdp_batch_solve: bad arguments");
+  if (n_streams == 0) n_streams = 8;
+  if (n_streams < 1 || n_streams > 64)
+    return fail(MDP_ERR_ARG, "mdp_batch_solve: n_streams must be in [1, 64]");
+  for (int32_t i = 0; i < count; ++i)
+    if (!hs[i] || !V_out[i]) return fail(MDP_ERR_ARG, "mdp_batch_solve: NULL handle or output");
+  for (int32_t i = 0; i < count; ++i)
+    for (int32_t k = i + 1; k < count && k < i + 1 + 4096; ++k)
+      if (hs[i] == hs[k]) return fail(MDP_ERR_ARG, "mdp_batch_solve: a handle appears twice");
+  std::vector<mdp_status> st(static_cast<size_t>(count), MDP_OK);
+  std::vector<std::string> msg(static_cast<size_t>(count));
+  std::atomic<int32_t> next{0};
+  const int workers = std::min<int>(n_streams, std::max<int32_t>(count, 1));
+  std::vector<std::thread> pool;
+  std::vector<int> dev_err(static_cast<size_t>(workers), 0);
+  int device = 0;
+  cudaGetDevice(&device);
+  for (int w = 0; w < workers; ++w) {
+    pool.emplace_back([&, w]() {
+      cudaSetDevice(device);
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        dev_err[w] = 1;
+        return;
+      }
+      for (;;) {
+        const int32_t i = next.fetch_add(1);
+        if (i >= count) break;
+        mdp_solve_stats one;
+        st[i] = mdp_solve(hs[i], opts, nullptr, MDP_F64, V_out[i], pi_out ? pi_out[i] : nullptr,
+                          &one, s);
+        if (st[i] != MDP_OK) msg[i] = g_err;
+        if (stats) stats[i] = one;
+      }
+      cudaStreamDestroy(s);
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int w = 0; w < workers; ++w)
+    if (dev_err[w]) return fail(MDP_ERR_CUDA, "mdp_batch_solve: stream creation failed");
+  mdp_status first = MDP_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    if (status_out) status_out[i] = st[i];
+    if (first == MDP_OK && st[i] != MDP_OK) {
+      first = st[i];
+      g_err = "mdp_batch_solve: MDP " + std::to_string(i) + ": " + msg[i];
+    }
+  }
+  return first;
 }
 
 mdp_status mdp_profile_enable(mdp_t h, int on) {

@@ -64,6 +64,47 @@ __device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int
   }
 }
 
+// One thread per row, two rows per thread in flight (short rows, VW == 1).
+template <bool FF, typename IdxT, typename GX>
+__device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int64_t r0, int lr_a,
+                                                  int lr_b, int64_t rows_here, int T, float* q_hi,
+                                                  float* q_lo) {
+  int64_t b[2] = {0, 0}, e[2] = {0, 0};
+  const int lr[2] = {lr_a, lr_b};
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (lr[u] < rows_here) row_bounds<IdxT>(P.rp, P.uniform_len, r0 + lr[u], b[u], e[u]);
+  if constexpr (FF) {
+    float hi[2], lo[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) row_dot_ff_g1(P.col, P.val, P.val_lo, gx, b[u], e[u], hi[u], lo[u]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (lr[u] < rows_here) {
+        const int a = lr[u] % P.m, sl = lr[u] / P.m;
+        const int64_t r = r0 + lr[u];
+        const ff sum = ff_norm(hi[u], lo[u]);
+        const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+        const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+        q_hi[a * T + sl] = q.hi;
+        q_lo[a * T + sl] = q.lo;
+      }
+    }
+  } else {
+    RowPre<float> R[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) row_pre<float>(P.col, P.val, b[u], e[u], R[u]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (lr[u] < rows_here) {
+        const int a = lr[u] % P.m, sl = lr[u] / P.m;
+        const float d = row_pre_dot<float>(P.col, P.val, gx, R[u]);
+        q_hi[a * T + sl] = fmaf(P.gamma, d, __ldcs(P.g + r0 + lr[u]));
+      }
+    }
+  }
+}
+
 template <bool FF, typename IdxT, int VW>
 __global__ void __launch_bounds__(kThreads)
     k_bellman(Csr<IdxT> P, Grid G, const void* __restrict__ Vin, void* __restrict__ Vout,
@@ -101,6 +142,15 @@ __global__ void __launch_bounds__(kThreads)
             bellman_pass_fast<FF, VW>(P, GatherF32{Vf}, r0, base + vec * VW, rows_here, lane, T,
                                       q_hi, q_lo);
         }
+      }
+    } else if (VW == 1) {
+      for (int base = 0; base < RT; base += 2 * kThreads) {
+        if constexpr (FF)
+          bellman_pass_g1x2<FF>(P, GatherFF{Vff}, r0, base + threadIdx.x,
+                                base + kThreads + threadIdx.x, rows_here, T, q_hi, q_lo);
+        else
+          bellman_pass_g1x2<FF>(P, GatherF32{Vf}, r0, base + threadIdx.x,
+                                base + kThreads + threadIdx.x, rows_here, T, q_hi, q_lo);
       }
     } else
     for (int base = 0; base < RT; base += NV) {
@@ -325,6 +375,10 @@ __global__ void __launch_bounds__(NT)
         for (int base = 0; base < RT; base += NT)
           bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, T, q_hi, q_lo);
       }
+    } else if (VW == 1) {
+      for (int base = 0; base < RT; base += 2 * NT)
+        bellman_pass_g1x2<FF>(P, gx, r0, base + threadIdx.x, base + NT + threadIdx.x, rows_here,
+                              T, q_hi, q_lo);
     } else
     for (int base = 0; base < RT; base += NV) {
       const int lr = base + vec;

@@ -130,6 +130,62 @@ __device__ __forceinline__ float row_dot_f32_g1(const int32_t* __restrict__ col,
   return acc;
 }
 
+// Short row with its first two packed groups loaded ahead: `row_pre` issues
+// the loads, `row_pre_dot` adds the entries of [b, e) in entry order (the
+// prefetched groups first, then any further groups), so several rows of one
+// thread can have their loads in flight together.
+template <typename PV>
+struct RowPre {
+  int4 c0, c1;
+  float4 v0, v1;
+  int64_t b, e;
+};
+
+template <typename PV>
+__device__ __forceinline__ void row_pre(const int32_t* __restrict__ col, const PV* __restrict__ val,
+                                        int64_t b, int64_t e, RowPre<PV>& R) {
+  R.b = b;
+  R.e = e;
+  const int64_t i0 = (b >> 2) << 2;
+  R.c0 = make_int4(0, 0, 0, 0);
+  R.c1 = R.c0;
+  R.v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  R.v1 = R.v0;
+  if (i0 < e) {
+    R.c0 = ldcol4(col, i0);
+    R.v0 = Ld<PV>::four(val, i0);
+  }
+  if (i0 + 4 < e) {
+    R.c1 = ldcol4(col, i0 + 4);
+    R.v1 = Ld<PV>::four(val, i0 + 4);
+  }
+}
+
+template <typename PV, typename GX>
+__device__ __forceinline__ float row_pre_dot(const int32_t* __restrict__ col,
+                                             const PV* __restrict__ val, GX x, const RowPre<PV>& R) {
+  const int64_t b = R.b, e = R.e;
+  const int64_t i0 = (b >> 2) << 2;
+  float acc = 0.f;
+  const int cc[8] = {R.c0.x, R.c0.y, R.c0.z, R.c0.w, R.c1.x, R.c1.y, R.c1.z, R.c1.w};
+  const float pp[8] = {R.v0.x, R.v0.y, R.v0.z, R.v0.w, R.v1.x, R.v1.y, R.v1.z, R.v1.w};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= b && i < e) acc = fmaf(pp[q], x(cc[q]), acc);
+  }
+  for (int64_t g = (i0 >> 2) + 2; (g << 2) < e; ++g) {
+    const int64_t j0 = g << 2;
+    const int4 c = ldcol4(col, j0);
+    const float4 p = Ld<PV>::four(val, j0);
+    acc = fmaf(p.x, x(c.x), acc);
+    if (j0 + 1 < e) acc = fmaf(p.y, x(c.y), acc);
+    if (j0 + 2 < e) acc = fmaf(p.z, x(c.z), acc);
+    if (j0 + 3 < e) acc = fmaf(p.w, x(c.w), acc);
+  }
+  return acc;
+}
+
 template <typename GX>
 __device__ __forceinline__ void row_dot_ff_g1(const int32_t* __restrict__ col,
                                               const float* __restrict__ val,

@@ -129,6 +129,36 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
               }
             }
           }
+        } else if (VW == 1) {
+          // short rows: two states per thread with the actions, row pointers and
+          // first two packed groups of both rows in flight together
+          int32_t act[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int64_t s = s0 + p * NT + threadIdx.x;
+            act[p] = s < P.n ? __ldg(pi + s) : 0;
+          }
+#pragma unroll
+          for (int p = 0; p < 4; p += 2) {
+            int64_t s2[2], r2[2];
+            RowPre<PV> R[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              s2[u] = s0 + (p + u) * NT + threadIdx.x;
+              int64_t b = 0, e = 0;
+              r2[u] = s2[u] * P.m + act[p + u];
+              if (s2[u] < P.n) row_bounds<IdxT>(P.rp, P.uniform_len, r2[u], b, e);
+              row_pre<PV>(P.col, val, b, e, R[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (s2[u] < P.n) {
+                float d = row_pre_dot<PV>(P.col, val, gx, R[u]);
+                if (lp) d *= __ldcs(P.row_scale + r2[u]);
+                uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+              }
+            }
+          }
         } else {
           for (int base = 0; base < TS; base += NV) {
             const int64_t s = s0 + base + vec;

@@ -1,0 +1,80 @@
+"""Host logic of the serving loop (queue, admission by memory budget, concurrency)
+with a fake solver: no GPU needed."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2502_14474_gb300 import serve
+
+
+class _FakeMDP:
+    def __init__(self, n):
+        self.n, self.m, self.gamma = n, 1, 0.9
+        self.row_ptr = np.arange(n + 1, dtype=np.int64)
+
+
+def _fake_solver(active, peak, lock):
+    def solve(req, w):
+        with lock:
+            active[0] += 1
+            peak[0] = max(peak[0], active[0])
+        time.sleep(0.01)
+        with lock:
+            active[0] -= 1
+        return np.full(req.mdp.n, req.rid, float), None, {"status": "MDP_OK", "transitions": 1.0}
+    return solve
+
+
+def test_budget_bounds_concurrency_and_fifo_admission():
+    active, peak, lock = [0], [0], threading.Lock()
+    srv = serve.Server(budget_bytes=300, workers=8, solver=_fake_solver(active, peak, lock),
+                       bytes_fn=lambda r: r.mdp.n).start()
+    reqs = [serve.Request(rid=i, mdp=_FakeMDP(100)) for i in range(12)]
+    for r in reqs:
+        srv.submit(r)
+    srv.close()
+    assert all(r.status == "MDP_OK" for r in reqs)
+    assert peak[0] <= 3 and srv.peak_used <= 300 and srv.peak_active <= 3
+    # FIFO: admission times are ordered like the submissions
+    t = [r.t_admit for r in reqs]
+    assert t == sorted(t)
+    assert all(r.V[0] == r.rid for r in reqs)
+
+
+def test_oversize_request_is_rejected_not_blocking():
+    active, peak, lock = [0], [0], threading.Lock()
+    srv = serve.Server(budget_bytes=150, workers=2, solver=_fake_solver(active, peak, lock),
+                       bytes_fn=lambda r: r.mdp.n).start()
+    big = serve.Request(rid=0, mdp=_FakeMDP(1000))
+    small = serve.Request(rid=1, mdp=_FakeMDP(100))
+    srv.submit(big)
+    srv.submit(small)
+    srv.close()
+    assert big.status == "rejected" and small.status == "MDP_OK"
+
+
+def test_trace_replay_and_summary():
+    active, peak, lock = [0], [0], threading.Lock()
+    srv = serve.Server(budget_bytes=1e9, workers=4, solver=_fake_solver(active, peak, lock),
+                       bytes_fn=lambda r: r.mdp.n).start()
+    arr = serve.poisson_arrivals(40, rate=400.0, seed=5)
+    reqs = [serve.Request(rid=i, mdp=_FakeMDP(50), arrival=float(a)) for i, a in enumerate(arr)]
+    wall = srv.run_trace(reqs)
+    srv.close()
+    summ = serve.summarize(reqs, wall)
+    assert summ["completed"] == 40 and summ["latency_p99_ms"] >= summ["latency_p50_ms"] > 0
+    assert peak[0] >= 2  # arrivals overlapped in service
+
+
+def test_worker_error_is_isolated():
+    def solver(req, w):
+        if req.rid == 2:
+            raise RuntimeError("poisoned request")
+        return np.zeros(1), None, {"status": "MDP_OK", "transitions": 1.0}
+    srv = serve.Server(budget_bytes=1e9, workers=2, solver=solver, bytes_fn=lambda r: 1).start()
+    reqs = [serve.Request(rid=i, mdp=_FakeMDP(1)) for i in range(5)]
+    for r in reqs:
+        srv.submit(r)
+    srv.close()
+    assert [r.status for r in reqs] == ["MDP_OK", "MDP_OK", "error", "MDP_OK", "MDP_OK"]
