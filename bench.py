@@ -53,9 +53,17 @@ def _args():
                    help="one solve, nothing else (for ncu launch lists)")
     p.add_argument("--no-profile", action="store_true",
                    help="no per-kernel events in the timed region (roofline omitted)")
-    p.add_argument("--workload", choices=["banded4m", "grid4096"], default="banded4m",
+    p.add_argument("--workload", choices=["banded4m", "grid4096", "batch512", "serve"],
+                   default="banded4m",
                    help="banded4m: the headline MDP; grid4096: the 4096^2 grid world of the "
-                        "precision path (gamma = 0.999)")
+                        "precision path (gamma = 0.999); batch512: 512 uneven random MDPs "
+                        "solved concurrently; serve: Poisson request stream through the "
+                        "continuous-batching loop")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--streams", type=int, default=16)
+    p.add_argument("--requests", type=int, default=2000)
+    p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--budget-gb", type=float, default=100.0)
     p.add_argument("--store", choices=["f32", "bf16", "f16"], default="f32",
                    help="probabilities of the inner GMRES SpMV")
     p.add_argument("--inner-norm", choices=["2", "inf"], default="2")
@@ -227,10 +235,115 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """512 independent random MDPs of uneven size solved concurrently (one JSON line)."""
+    import torch
+    import synth
+    from paper_2502_14474_gb300 import MDP, capi
+    t0 = time.perf_counter()
+    params = synth.uneven_batch_params(args.batch_count, seed=4)
+    mdps = [synth.uneven_mdp(p) for p in params]
+    gen_s = time.perf_counter() - t0
+    hs = [MDP.from_csr(m, autotune=True) for m in mdps]
+    nnz = sum(m.nnz for m in mdps)
+    Vs = [torch.empty(m.n, dtype=torch.float64, device="cuda") for m in mdps]
+    pis = [torch.empty(m.n, dtype=torch.int32, device="cuda") for m in mdps]
+    opts = capi.mdp_default_opts()
+    opts.max_inner = args.max_inner
+
+    def go(streams):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        stats, status = capi.mdp_batch_solve([h.h for h in hs], Vs, pis, opts=opts,
+                                             n_streams=streams, raise_on_error=False)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, stats, status
+
+    for _ in range(max(1, args.warmup)):
+        go(args.streams)
+    times, stats, status = [], None, None
+    for _ in range(args.steps):
+        el, stats, status = go(args.streams)
+        times.append(el)
+    seq_el, _, _ = go(1)
+    trans = sum(st["transitions"] for st in stats)
+    el = float(np.median(times))
+    sample = list(range(0, len(mdps), max(1, len(mdps) // 5)))
+    import oracle
+    cert = [oracle.certificate(mdps[i], Vs[i].cpu().numpy())["res_inf"] for i in sample]
+    line = {"metric": METRIC, "value": trans / el, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"uneven_batch_{len(mdps)}", "mdps": len(mdps), "nnz": nnz,
+                       "n_range": [min(m.n for m in mdps), max(m.n for m in mdps)],
+                       "streams": args.streams, "tol": 1e-9, "autotune": True,
+                       "generation_s": gen_s},
+            "converged": sum(1 for x in status if x == "MDP_OK"),
+            "sequential_ms": seq_el * 1e3, "speedup_vs_one_stream": seq_el / el,
+            "oracle_residual_sample": cert}
+    print(json.dumps(line), flush=True)
+    for h in hs:
+        h.close()
+    return 0
+
+
+def run_serve(args):
+    """Poisson request stream through the continuous-batching loop (one JSON line)."""
+    import torch
+    import synth
+    import oracle
+    from paper_2502_14474_gb300 import serve
+    rng = np.random.default_rng(5)
+    pool = [synth.uneven_mdp(p) for p in synth.uneven_batch_params(48, seed=5)]
+    large = [synth.random_sparse(1 << 20, 8, 16, 1.0, 0.99, seed=5_000_000 + i,
+                                 dtype=np.float32, name="random_n1048576_m8_k16")
+             for i in range(2)]
+    arrivals = serve.poisson_arrivals(args.requests, args.rate, seed=5)
+    reqs = []
+    for i, a in enumerate(arrivals):
+        mdp = large[int(rng.integers(2))] if rng.random() < 0.01 else pool[int(rng.integers(48))]
+        reqs.append(serve.Request(rid=i, mdp=mdp, arrival=float(a)))
+    srv = serve.Server(budget_bytes=args.budget_gb * 1e9, workers=args.streams,
+                       solve_opts={"max_inner": args.max_inner}).start()
+    # warm the library and the kernels on a few requests outside the trace
+    warm = [serve.Request(rid=-1 - i, mdp=pool[i]) for i in range(4)]
+    for r in warm:
+        srv.submit(r)
+    with srv.cv:
+        while len(srv.done) < len(warm):
+            srv.cv.wait(timeout=1.0)
+        srv.done.clear()
+    wall = srv.run_trace(reqs)
+    srv.close()
+    summ = serve.summarize(reqs, wall)
+    sample = [r for r in reqs if r.rid % 100 == 0 and r.status == "MDP_OK"]
+    errs = [oracle.certificate(r.mdp, r.V) for r in sample]
+    line = {"metric": "solves/s (with p50/p99 latency)", "value": summ["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "poisson_request_stream", "requests": args.requests,
+                       "rate_per_s": args.rate, "budget_gb": args.budget_gb,
+                       "workers": args.streams, "pool_mdps": 48, "large_fraction": 0.01,
+                       "large": "n=2^20, m=8, 16 successors"},
+            "serving": summ, "peak_active": srv.peak_active,
+            "peak_budget_gb": srv.peak_used / 1e9,
+            "oracle_sample": {"requests": len(sample),
+                              "max_residual_inf": max((e["res_inf"] for e in errs), default=None),
+                              "max_error_bound": max((e["bound"] for e in errs), default=None)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global WORKLOAD
     args = _args()
     WORKLOAD = args.workload
+    if args.workload == "batch512":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
