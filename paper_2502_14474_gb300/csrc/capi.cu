@@ -109,6 +109,8 @@ struct mdp_s {
   int32_t val_t = MDP_F32;
   Prof prof;
   int64_t launches = 0;
+  cudaStream_t home = nullptr;   // stream of mdp_create: device memory is allocated in its order
+  cudaEvent_t done_ev = nullptr; // recorded at the end of every call: destroy waits on it
 };
 
 namespace {
@@ -134,15 +136,36 @@ struct DeviceGuard {
     }                                                                                    \
   } while (0)
 
+// Device memory comes from the device's stream-ordered pool (cudaMallocAsync /
+// cudaFreeAsync): creating and destroying handles does not synchronise the
+// device, so handles of concurrent solves (batch, serving) come and go while
+// other streams keep running.
 template <typename T>
 cudaError_t dalloc(mdp_s* h, T** p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, h->home);
   if (e == cudaSuccess) {
     *p = static_cast<T*>(q);
     h->bytes += bytes;
   }
   return e;
+}
+
+// One non-blocking stream per device on which handles are freed after their
+// last call's completion event.
+std::mutex g_free_mu;
+cudaStream_t g_free_stream[64] = {nullptr};
+
+cudaStream_t free_stream(int dev) {
+  std::lock_guard<std::mutex> lk(g_free_mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!g_free_stream[dev]) {
+    if (cudaStreamCreateWithFlags(&g_free_stream[dev], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      g_free_stream[dev] = nullptr;
+    }
+  }
+  return g_free_stream[dev];
 }
 
 // ---- profiling -------------------------------------------------------------
@@ -234,9 +257,15 @@ double bytes_richardson(const Mat& A, bool lp) {
 void free_all(mdp_s* h) {
   void* ptrs[] = {h->rp, h->pk, h->val_lo, h->g, h->g_lo, h->val16, h->row_scale,
                   h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
+  cudaStream_t fs = free_stream(h->device);
+  if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
   for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (h->head) cudaFreeHost(h->head);
+    if (p) {
+      if (fs) cudaFreeAsync(p, fs);
+      else cudaFree(p);
+    }
+  if (h->done_ev) cudaEventDestroy(h->done_ev);
+  free(h->head);
   for (ProfRec& r : h->prof.pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -281,17 +310,38 @@ int64_t log2_bucket(int64_t x) {
 
 size_t partials_len(int num_sms) { return static_cast<size_t>(num_sms) * 8 * (kMaxBasis + 1); }
 
-mdp_status ensure_basis(mdp_s* h, int restart) {
+// Growth of the work buffers happens in the calling stream's order.
+mdp_status ensure_basis(mdp_s* h, int restart, cudaStream_t s) {
   if (restart <= h->restart_cap && h->basis) return MDP_OK;
+  const cudaStream_t home = h->home;
+  h->home = s;
   if (h->basis) {
-    cudaFree(h->basis);
+    cudaFreeAsync(h->basis, s);
     h->bytes -= static_cast<size_t>(h->restart_cap + 1) * h->ld * sizeof(float);
     h->basis = nullptr;
   }
-  ALLOC(h, h->basis, static_cast<size_t>(restart + 1) * h->ld * sizeof(float));
+  cudaError_t e = dalloc(h, &h->basis, static_cast<size_t>(restart + 1) * h->ld * sizeof(float));
+  h->home = home;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->restart_cap = 0;
+    return fail(MDP_ERR_OOM, "device allocation of the GMRES basis failed");
+  }
   h->restart_cap = restart;
   return MDP_OK;
 }
+
+// Mark the end of a call on stream s (mdp_destroy waits for the last mark).
+void mark_done(mdp_s* h, cudaStream_t s) {
+  if (h->done_ev) cudaEventRecord(h->done_ev, s);
+}
+
+// Records the completion mark on every exit path of an entry point.
+struct DoneMark {
+  mdp_s* h;
+  cudaStream_t s;
+  ~DoneMark() { mark_done(h, s); }
+};
 
 cudaError_t autotune(mdp_s* h, float* scratch_r, cudaStream_t s) {
   Mat& A = h->A;
@@ -350,10 +400,17 @@ cudaError_t autotune(mdp_s* h, float* scratch_r, cudaStream_t s) {
   return err;
 }
 
-mdp_status ensure_richardson(mdp_s* h) {
+mdp_status ensure_richardson(mdp_s* h, cudaStream_t s) {
   if (h->d0) return MDP_OK;
-  ALLOC(h, h->d0, static_cast<size_t>(h->A.n) * sizeof(float));
-  ALLOC(h, h->d1, static_cast<size_t>(h->A.n) * sizeof(float));
+  const cudaStream_t home = h->home;
+  h->home = s;
+  cudaError_t e = dalloc(h, &h->d0, static_cast<size_t>(h->A.n) * sizeof(float));
+  if (e == cudaSuccess) e = dalloc(h, &h->d1, static_cast<size_t>(h->A.n) * sizeof(float));
+  h->home = home;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, "device allocation of the Richardson vectors failed");
+  }
   return MDP_OK;
 }
 
@@ -513,6 +570,12 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
     delete h;
     return fail(MDP_ERR_CUDA, "no CUDA device");
   }
+  h->home = s;
+  if (cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(MDP_ERR_CUDA, "event creation failed");
+  }
   auto bail = [&](mdp_status st) {
     free_all(h);
     delete h;
@@ -543,7 +606,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   auto free_tmp = [&]() {
     for (void*& p : tmp)
       if (p) {
-        cudaFree(p);
+        cudaFreeAsync(p, s);
         p = nullptr;
       }
   };
@@ -554,7 +617,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
                           gbytes};
     const void* src[4] = {row_ptr, col, val, cost};
     for (int i = 0; i < 4; ++i) {
-      if (cudaMalloc(&tmp[i], sz[i]) != cudaSuccess) {
+      if (cudaMallocAsync(&tmp[i], sz[i], s) != cudaSuccess) {
         cudaGetLastError();
         free_tmp();
         return bail(fail(MDP_ERR_OOM, "staging allocation failed"));
@@ -607,7 +670,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   PrepFlags fl;
   CCK(cudaMemcpyAsync(&fl, dflags, sizeof(fl), cudaMemcpyDeviceToHost, s));
   CCK(cudaStreamSynchronize(s));
-  cudaFree(dflags);
+  cudaFreeAsync(dflags, s);
   h->bytes -= sizeof(PrepFlags);
   free_tmp();
   if (fl.bad_csr)
@@ -682,12 +745,11 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   CALLOC(h->st, sizeof(DevState));
   CALLOC(h->flag, sizeof(int));
   CCK(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
-  if (cudaMallocHost(&h->head, kHeadBytes) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(MDP_ERR_OOM, "pinned host allocation failed"));
-  }
-  if (ensure_basis(h, 30) != MDP_OK) return bail(MDP_ERR_OOM);
+  h->head = static_cast<StatusHead*>(malloc(kHeadBytes));
+  if (!h->head) return bail(fail(MDP_ERR_OOM, "host allocation failed"));
+  if (ensure_basis(h, 30, s) != MDP_OK) return bail(MDP_ERR_OOM);
   if (flags & MDP_FLAG_AUTOTUNE) CCK(autotune(h, h->basis, s));
+  mark_done(h, s);
   CCK(cudaStreamSynchronize(s));
 #undef CALLOC
 #undef CCK
@@ -698,8 +760,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
 void mdp_destroy(mdp_t h) {
   if (!h) return;
   DeviceGuard g(h->device);
-  cudaDeviceSynchronize();
-  free_all(h);
+  free_all(h);  // frees after the handle's last call completes, without a device sync
   delete h;
 }
 
@@ -734,6 +795,7 @@ mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, in
   if (V_out && V_out == V_in) return fail(MDP_ERR_ARG, "V_out must not alias V_in");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DoneMark dm{h, s};
   if (v_t == MDP_F32) {
     CK(h, run(h, s, MDP_PROF_BELLMAN_F32, 1, bytes_bellman(h->A, false, V_out != nullptr), -1, [&] {
          return launch_bellman(h->A, false, V_in, V_out, pi_out, r_out, h->partials, h->st, 0, s);
@@ -749,6 +811,7 @@ mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, in
       CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
                 [&] { return launch_from_ff(h->A.n, h->W2, V_out, 1, h->A.num_sms, s); }));
   }
+  mark_done(h, s);
   if (res_inf || res_2) {
     mdp_status rc = read_head(h, s);
     if (rc != MDP_OK) return rc;
@@ -770,10 +833,11 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
   if (max_iters < 0) return fail(MDP_ERR_ARG, "max_iters must be >= 0");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DoneMark dm{h, s};
   h->cancel.store(0);
   mdp_status rc = check_policy(h, pi, s);
   if (rc != MDP_OK) return rc;
-  rc = ensure_basis(h, restart);
+  rc = ensure_basis(h, restart, s);
   if (rc != MDP_OK) return rc;
   CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
        return launch_to_ff(h->A.n, v_inout, v_t == MDP_F64, h->V, h->A.num_sms, s);
@@ -828,6 +892,7 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
   CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
        return launch_from_ff(h->A.n, h->V, v_inout, v_t == MDP_F64, h->A.num_sms, s);
      }));
+  mark_done(h, s);
   CK(h, cudaStreamSynchronize(s));
   prof_flush(h);
   if (stats) *stats = es;
@@ -854,10 +919,11 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   if (lp && !h->val16) return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DoneMark dm{h, s};
   h->cancel.store(0);
   mdp_status rc = MDP_OK;
-  if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart);
-  else rc = ensure_richardson(h);
+  if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart, s);
+  else rc = ensure_richardson(h, s);
   if (rc != MDP_OK) return rc;
   const Mat& A = h->A;
   if (V_init)
@@ -971,6 +1037,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   if (pi_out)
     CK(h, cudaMemcpyAsync(pi_out, h->pi, static_cast<size_t>(A.n) * sizeof(int32_t),
                           cudaMemcpyDeviceToDevice, s));
+  mark_done(h, s);
   CK(h, cudaStreamSynchronize(s));
   prof_flush(h);
   ss.transitions = transitions;
