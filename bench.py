@@ -299,6 +299,12 @@ def run_serve(args):
     large = [synth.random_sparse(1 << 20, 8, 16, 1.0, 0.99, seed=5_000_000 + i,
                                  dtype=np.float32, name="random_n1048576_m8_k16")
              for i in range(2)]
+    # request payloads live in pinned host memory (as a front end that receives
+    # them into registered buffers would hold them): host-to-device copies are
+    # then asynchronous DMA instead of staged pageable copies
+    for mdp in pool + large:
+        for k in ("row_ptr", "col", "val", "g"):
+            setattr(mdp, k, torch.from_numpy(getattr(mdp, k)).pin_memory().numpy())
     arrivals = serve.poisson_arrivals(args.requests, args.rate, seed=5)
     reqs = []
     for i, a in enumerate(arrivals):
