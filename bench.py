@@ -71,6 +71,21 @@ def _args():
     return p.parse_args()
 
 
+def aggregate(ms_local: float, transitions_local: float, dist=None, device=None):
+    """Whole-job throughput of weak-scaled replicas: every rank solved its own
+    copy; the job time is the slowest rank's, the work is the sum over ranks.
+    Returns (ms_max, value_transitions_per_s)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, transitions_local / (ms_local / 1e3)
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    w = torch.tensor([transitions_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return ms_max, float(w.item()) / (ms_max / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -415,12 +430,8 @@ def main():
     time.sleep(0.3)
     ms, stats, prof_plain = timed(False)
     clocks = sampler.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     trans = sum(s["transitions"] for s in stats)
-    value = trans * ws / (ms_max / 1e3)
+    ms_max, value = aggregate(ms, trans, dist if ws > 1 else None, dev)
     # ---- second timed region, same K solves, CUDA events around every launch on
     # the solve stream: per-kernel durations for the roofline (the events add ~7%
     # to a step, so they are kept out of the headline region)
