@@ -86,6 +86,7 @@ struct mdp_s {
   float* g = nullptr;
   float* g_lo = nullptr;
   void* val16 = nullptr;
+  uint4* lpk = nullptr;     // packed 16-bit inner copy (band < 2^15)
   float* row_scale = nullptr;
   float2* V = nullptr;      // float-float iterate
   float2* W1 = nullptr;     // float-float scratch (mdp_bellman input)
@@ -238,8 +239,8 @@ double bytes_policy_resid(const Mat& A) {
 }
 double bytes_spmv(const Mat& A, bool lp) {
   const double n = A.n;
-  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
-              (lp ? 4.0 : 0.0) + 4.0 + 4.0);
+  const double per_entry = lp ? (A.lpk ? 4.0 : 6.0) : 8.0;
+  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * per_entry + (lp ? 4.0 : 0.0) + 4.0 + 4.0);
 }
 double bytes_dots(const Mat& A, int j) { return 4.0 * A.n * (j + 2); }
 double bytes_ortho(const Mat& A, int j, int cgs2) {
@@ -255,7 +256,7 @@ double bytes_richardson(const Mat& A, bool lp) {
 }
 
 void free_all(mdp_s* h) {
-  void* ptrs[] = {h->rp, h->pk, h->val_lo, h->g, h->g_lo, h->val16, h->row_scale,
+  void* ptrs[] = {h->rp, h->pk, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
                   h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
   cudaStream_t fs = free_stream(h->device);
   if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
@@ -727,11 +728,19 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   h->store_t = store_t;
   A.store_t = store_t;
   if (store_t == MDP_BF16 || store_t == MDP_F16) {
-    CALLOC(h->val16, static_cast<size_t>(padded) * 2);  // group loads read whole quads
-    CCK(cudaMemsetAsync(h->val16, 0, static_cast<size_t>(padded) * 2, s));
     CALLOC(h->row_scale, static_cast<size_t>(rows) * 4);
-    CCK(launch_prep_lowp(A, h->val16, h->row_scale, store_t, s));
-    A.val16 = h->val16;
+    if (h->band < 32768 && !getenv("MDP_NO_LP_PACK")) {
+      // 16-byte groups of int16 column offsets and 16-bit values
+      CALLOC(h->lpk, static_cast<size_t>(padded) * 4);
+      CCK(cudaMemsetAsync(h->lpk, 0, static_cast<size_t>(padded) * 4, s));
+      CCK(launch_prep_lowp_packed(A, h->lpk, h->row_scale, store_t, s));
+      A.lpk = h->lpk;
+    } else {
+      CALLOC(h->val16, static_cast<size_t>(padded) * 2);  // group loads read whole quads
+      CCK(cudaMemsetAsync(h->val16, 0, static_cast<size_t>(padded) * 2, s));
+      CCK(launch_prep_lowp(A, h->val16, h->row_scale, store_t, s));
+      A.val16 = h->val16;
+    }
     A.row_scale = h->row_scale;
   }
 
@@ -779,7 +788,7 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
   info->uniform_len = h->A.uniform_len;
   info->idx64 = h->A.idx64;
   info->band = h->band;
-  info->has_low_precision = h->val16 != nullptr;
+  info->has_low_precision = (h->val16 != nullptr || h->lpk != nullptr) ? 1 : 0;
   info->store_t = h->store_t;
   info->device_bytes = h->bytes;
   info->gamma = h->A.gamma;
@@ -916,7 +925,8 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
     return fail(MDP_ERR_ARG, "unknown inner solver");
   if (o.inner_norm != 0 && o.inner_norm != 1) return fail(MDP_ERR_ARG, "inner_norm is 0 or 1");
   const bool lp = o.low_precision_inner != 0;
-  if (lp && !h->val16) return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
+  if (lp && !h->val16 && !h->lpk)
+    return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DoneMark dm{h, s};

@@ -479,6 +479,7 @@ static Csr<IdxT> make_csr(const Mat& A) {
   P.g = A.g;
   P.g_lo = A.g_lo;
   P.val16 = A.val16;
+  P.lpk = A.lpk;
   P.row_scale = A.row_scale;
   P.n = A.n;
   P.m = A.m;

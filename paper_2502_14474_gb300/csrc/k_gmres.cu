@@ -265,7 +265,13 @@ __global__ void __launch_bounds__(kThreads)
       row = s * P.m + __ldg(pi + s);
       row_bounds<IdxT>(P.rp, P.uniform_len, row, b, e);
     }
-    float d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+    float d;
+    if constexpr (sizeof(PV) == 2) {
+      d = P.lpk ? row_dot_lp<VW, PV>(P.lpk, GatherF32{d_in}, s, b, e, lane)
+                : row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+    } else {
+      d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+    }
     d = group_sum<VW>(d);
     if (lane == 0 && s < P.n) {
       if (lp) d *= __ldcs(P.row_scale + row);
@@ -336,6 +342,7 @@ static Csr<IdxT> csr_of(const Mat& A) {
   P.g = A.g;
   P.g_lo = A.g_lo;
   P.val16 = A.val16;
+  P.lpk = A.lpk;
   P.row_scale = A.row_scale;
   P.n = A.n;
   P.m = A.m;

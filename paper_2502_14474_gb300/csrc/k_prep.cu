@@ -148,6 +148,31 @@ __global__ void k_prep_lowp(int64_t rows, const IdxT* __restrict__ rp, int32_t u
   }
 }
 
+// One thread per row: entry i of row r (state s = r / m) goes to group i/4,
+// slot i%4: int16 (col - s) in the first 8 bytes, the rounded value in the
+// last 8; row_scale[r] = 1 / sum of the rounded row.
+template <typename IdxT, typename Q>
+__global__ void k_prep_lowp_packed(int64_t rows, int32_t m, const IdxT* __restrict__ rp,
+                                   int32_t uniform_len, const float* __restrict__ pk,
+                                   uint16_t* __restrict__ lpk, float* __restrict__ scale) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t b = uniform_len > 0 ? r * uniform_len : static_cast<int64_t>(rp[r]);
+    const int64_t e = uniform_len > 0 ? b + uniform_len : static_cast<int64_t>(rp[r + 1]);
+    const int64_t st = r / m;
+    double sum = 0.0;
+    for (int64_t i = b; i < e; ++i) {
+      const int64_t slot = ((i >> 2) << 3) + (i & 3);
+      const int32_t c = __float_as_int(pk[((i >> 2) << 3) + (i & 3)]);
+      const Q v = Round16<Q>::q(pk[((i >> 2) << 3) + 4 + (i & 3)]);
+      lpk[slot] = static_cast<uint16_t>(static_cast<int16_t>(c - st));
+      lpk[slot + 4] = *reinterpret_cast<const uint16_t*>(&v);
+      sum += static_cast<double>(Round16<Q>::f(v));
+    }
+    scale[r] = sum > 0.0 ? static_cast<float>(1.0 / sum) : 0.f;
+  }
+}
+
 static unsigned grid_of(int64_t work, int num_sms) {
   int64_t b = (work + 255) / 256;
   const int64_t cap = static_cast<int64_t>(num_sms) * 16;
@@ -198,6 +223,33 @@ cudaError_t launch_prep_lowp(const Mat& A, void* val16, float* row_scale, int st
       k_prep_lowp<int32_t, __nv_bfloat16><<<nb, 256, 0, s>>>(
           A.rows, static_cast<const int32_t*>(A.rp), A.uniform_len, A.val,
           static_cast<__nv_bfloat16*>(val16), row_scale);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mdpk
+
+namespace mdpk {
+
+cudaError_t launch_prep_lowp_packed(const Mat& A, uint4* lpk, float* row_scale, int store_t,
+                                    cudaStream_t s) {
+  const unsigned nb = grid_of(A.rows, A.num_sms);
+  const float* pk = A.val;
+  uint16_t* out = reinterpret_cast<uint16_t*>(lpk);
+  if (store_t == 3) {
+    if (A.idx64)
+      k_prep_lowp_packed<int64_t, __half><<<nb, 256, 0, s>>>(
+          A.rows, A.m, static_cast<const int64_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+    else
+      k_prep_lowp_packed<int32_t, __half><<<nb, 256, 0, s>>>(
+          A.rows, A.m, static_cast<const int32_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+  } else {
+    if (A.idx64)
+      k_prep_lowp_packed<int64_t, __nv_bfloat16><<<nb, 256, 0, s>>>(
+          A.rows, A.m, static_cast<const int64_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+    else
+      k_prep_lowp_packed<int32_t, __nv_bfloat16><<<nb, 256, 0, s>>>(
+          A.rows, A.m, static_cast<const int32_t*>(A.rp), A.uniform_len, pk, out, row_scale);
   }
   return cudaGetLastError();
 }

@@ -441,6 +441,74 @@ __device__ __forceinline__ void vec_rows_ff(const int32_t* __restrict__ col,
   }
 }
 
+// ---- packed 16-bit inner copy ------------------------------------------------
+// Group g is one uint4: .x/.y hold int16 offsets (col - s) of entries 4g..4g+3
+// from the state s of the entry's row, .z/.w the 16-bit values.  A policy row
+// of 16 entries is 64 bytes (half the FP32 group bytes).
+template <typename Q>
+struct Q16;
+template <>
+struct Q16<__nv_bfloat16> {
+  static __device__ __forceinline__ float f(uint32_t u) { return __uint_as_float(u << 16); }
+};
+template <>
+struct Q16<__half> {
+  static __device__ __forceinline__ float f(uint32_t u) {
+    return __half2float(__ushort_as_half(static_cast<unsigned short>(u & 0xffffu)));
+  }
+};
+
+__device__ __forceinline__ int32_t lp_off(uint32_t w, int hi) {
+  return static_cast<int32_t>(static_cast<int16_t>(hi ? (w >> 16) : (w & 0xffffu)));
+}
+
+// Entries of group G (entry indices i0..i0+3) that fall inside [b, e), in order.
+template <typename Q, typename GX>
+__device__ __forceinline__ float lp_group_dot(uint4 G, int64_t i0, int64_t b, int64_t e,
+                                              int64_t s, GX x, float acc) {
+  const uint32_t dw[2] = {G.x, G.y};
+  const uint32_t qw[2] = {G.z, G.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= b && i < e) {
+      const int32_t c = static_cast<int32_t>(s) + lp_off(dw[q >> 1], q & 1);
+      const float v = Q16<Q>::f(q & 1 ? (qw[q >> 1] >> 16) : (qw[q >> 1] & 0xffffu));
+      acc = fmaf(v, x(c), acc);
+    }
+  }
+  return acc;
+}
+
+// Lane `lane` of VW takes groups g0 + lane, g0 + lane + VW, ... of row [b, e)
+// of state s; the caller reduces over the VW lanes.
+template <int VW, typename Q, typename GX>
+__device__ __forceinline__ float row_dot_lp(const uint4* __restrict__ lpk, GX x, int64_t s,
+                                            int64_t b, int64_t e, int lane) {
+  float acc = 0.f;
+  const int64_t g1 = (e + 3) >> 2;
+#pragma unroll 2
+  for (int64_t g = (b >> 2) + lane; g < g1; g += VW)
+    acc = lp_group_dot<Q>(__ldcs(lpk + g), g << 2, b, e, s, x, acc);
+  return acc;
+}
+
+// Fast path: VW rows (states srow[u]) of 4*VW aligned entries; lane l loads
+// group l of each row before any gather.
+template <int VW, typename Q, typename GX>
+__device__ __forceinline__ void vec_rows_lp(const uint4* __restrict__ lpk, GX x,
+                                            const int64_t (&b)[VW], const int64_t (&srow)[VW],
+                                            const bool (&valid)[VW], int lane, float (&p)[VW]) {
+  uint4 G[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) G[u] = valid[u] ? __ldcs(lpk + (b[u] >> 2) + lane) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    const int64_t i0 = b[u] + 4 * lane;
+    p[u] = valid[u] ? lp_group_dot<Q>(G[u], i0, i0, i0 + 4, srow[u], x, 0.f) : 0.f;
+  }
+}
+
 // Pointer form (global gathers) kept for the callers that stream a vector.
 template <int VW, typename PV>
 __device__ __forceinline__ float row_dot_f32(const int32_t* __restrict__ col,

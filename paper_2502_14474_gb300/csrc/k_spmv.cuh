@@ -121,12 +121,40 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
                 vd[u] = __shfl_sync(0xffffffffu, valid ? 1 : 0, u, VW) != 0;
               }
               float part[VW];
-              vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
+              if constexpr (sizeof(PV) == 2) {
+                if (P.lpk) {
+                  int64_t srow[VW];
+#pragma unroll
+                  for (int u = 0; u < VW; ++u) srow[u] = s - lane + u;
+                  vec_rows_lp<VW, PV>(P.lpk, gx, b, srow, vd, lane, part);
+                } else {
+                  vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
+                }
+              } else {
+                vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
+              }
               float d = reduce_scatter<VW>(part, lane);
               if (valid) {
                 if (lp) d *= __ldcs(P.row_scale + r);
                 uw[s] = sj * fmaf(-P.gamma, d, xs(s));
               }
+            }
+          }
+        } else if (sizeof(PV) == 2 && P.lpk) {
+          // packed 16-bit copy: lanes stride over the 16-byte groups of a row
+          for (int base = 0; base < TS; base += NV) {
+            const int64_t s = s0 + base + vec;
+            int64_t b = 0, e = 0, r = 0;
+            if (s < P.n) {
+              r = s * P.m + __ldg(pi + s);
+              row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+            }
+            float d = 0.f;
+            if constexpr (sizeof(PV) == 2) d = row_dot_lp<VW, PV>(P.lpk, gx, s, b, e, lane);
+            d = group_sum<VW>(d);
+            if (lane == 0 && s < P.n) {
+              d *= __ldcs(P.row_scale + r);
+              uw[s] = sj * fmaf(-P.gamma, d, xs(s));
             }
           }
         } else if (VW == 1) {
@@ -301,6 +329,7 @@ inline Csr<IdxT> csr_view(const Mat& A) {
   P.g = A.g;
   P.g_lo = A.g_lo;
   P.val16 = A.val16;
+  P.lpk = A.lpk;
   P.row_scale = A.row_scale;
   P.n = A.n;
   P.m = A.m;

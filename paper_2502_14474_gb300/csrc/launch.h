@@ -20,6 +20,7 @@ struct Mat {
   const float* g = nullptr;
   const float* g_lo = nullptr;
   const void* val16 = nullptr;
+  const uint4* lpk = nullptr;  // [4 x int16 col - s | 4 x 16-bit value] groups (band < 2^15)
   const float* row_scale = nullptr;
   int32_t store_t = 0;      // MDP_F32 / MDP_BF16 / MDP_F16 of val16
   int32_t uniform_len = 0;
@@ -107,5 +108,9 @@ cudaError_t launch_pack(int64_t nnz, const int32_t* col_in, const void* val_in, 
                         uint32_t* pk, float* val_lo_out, int num_sms, cudaStream_t s);
 cudaError_t launch_prep_lowp(const Mat& A, void* val16, float* row_scale, int store_t,
                              cudaStream_t s);
+// Packed 16-bit inner copy: per 4-entry group, 4 int16 column offsets from the
+// entry's row state and the 4 rounded values, 16 bytes; plus row_scale.
+cudaError_t launch_prep_lowp_packed(const Mat& A, uint4* lpk, float* row_scale, int store_t,
+                                    cudaStream_t s);
 
 }  // namespace mdpk

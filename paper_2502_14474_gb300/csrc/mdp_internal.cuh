@@ -260,6 +260,7 @@ struct Csr {
   const float* g;         // [rows]
   const float* g_lo;      // [rows] or nullptr
   const void* val16;      // [nnz] bf16/f16 copy or nullptr
+  const uint4* lpk;       // packed 16-bit inner copy (16-byte groups) or nullptr
   const float* row_scale; // [rows] renormalisation of the 16-bit copy
   int64_t n;
   int32_t m;

@@ -203,3 +203,25 @@ def test_solve_banded_4m_full_size(banded_4m_gpu):
         assert cert["res_inf"] <= tol * 1.05
         clear = cert["gap"] > 2 * tol + 1e-12
         assert np.array_equal(pig[s0:s0 + 4096][clear], cert["pi"][clear])
+
+
+@pytest.mark.parametrize("store", ["bf16", "f16"])
+@pytest.mark.parametrize("packed", [True, False])
+def test_solve_banded_low_precision_inner(store, packed, monkeypatch):
+    """16-bit inner probabilities (packed 16-byte groups with int16 column offsets,
+    or the plain 16-bit array) refined by the float-float outer residual reach
+    the FP32-P problem's 1e-9 residual."""
+    from paper_2502_14474_gb300 import MDP
+    mdp = synth.banded(120000, 8, 16, 3000, 0.5, 0.99, seed=34, dtype=np.float32)
+    if not packed:
+        monkeypatch.setenv("MDP_NO_LP_PACK", "1")
+    h = MDP.from_csr(mdp, store=store)
+    monkeypatch.delenv("MDP_NO_LP_PACK", raising=False)
+    assert h.info()["has_low_precision"]
+    V, pi, st = h.solve(tol=1e-9)
+    assert st["converged"]
+    cert = oracle.certificate(mdp, V.cpu().numpy())
+    assert cert["res_inf"] <= 1.05e-9
+    clear = cert["gap"] > 2.1e-9
+    assert np.array_equal(pi.cpu().numpy()[clear], cert["pi"][clear])
+    h.close()
