@@ -240,7 +240,8 @@ double bytes_policy_resid(const Mat& A) {
 double bytes_spmv(const Mat& A, bool lp) {
   const double n = A.n;
   const double per_entry = lp ? (A.lpk ? 4.0 : 6.0) : 8.0;
-  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * per_entry + (lp ? 4.0 : 0.0) + 4.0 + 4.0);
+  const double row_scale = (lp && !A.lpk) ? 4.0 : 0.0;  // the packed copy renormalises on the fly
+  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * per_entry + row_scale + 4.0 + 4.0);
 }
 double bytes_dots(const Mat& A, int j) { return 4.0 * A.n * (j + 2); }
 double bytes_ortho(const Mat& A, int j, int cgs2) {

@@ -265,16 +265,23 @@ __global__ void __launch_bounds__(kThreads)
       row = s * P.m + __ldg(pi + s);
       row_bounds<IdxT>(P.rp, P.uniform_len, row, b, e);
     }
-    float d;
+    float d, den = 0.f;
+    bool packed = false;
     if constexpr (sizeof(PV) == 2) {
-      d = P.lpk ? row_dot_lp<VW, PV>(P.lpk, GatherF32{d_in}, s, b, e, lane)
-                : row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+      if (P.lpk) {
+        row_dot_lp<VW, PV>(P.lpk, GatherF32{d_in}, s, b, e, lane, d, den);
+        packed = true;
+      } else {
+        d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
+      }
     } else {
       d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
     }
     d = group_sum<VW>(d);
+    if (packed) den = group_sum<VW>(den);
     if (lane == 0 && s < P.n) {
-      if (lp) d *= __ldcs(P.row_scale + row);
+      if (packed) d = den > 0.f ? d / den : 0.f;
+      else if (lp) d *= __ldcs(P.row_scale + row);
       const float nv = fmaf(P.gamma, d, r[s]);
       d_out[s] = nv;
       const double df = static_cast<double>(nv - d_in[s]);

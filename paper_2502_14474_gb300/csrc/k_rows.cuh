@@ -462,10 +462,13 @@ __device__ __forceinline__ int32_t lp_off(uint32_t w, int hi) {
   return static_cast<int32_t>(static_cast<int16_t>(hi ? (w >> 16) : (w & 0xffffu)));
 }
 
-// Entries of group G (entry indices i0..i0+3) that fall inside [b, e), in order.
+// Entries of group G (entry indices i0..i0+3) that fall inside [b, e), in
+// order: num += q_e x(col_e), den += q_e.  The row's renormalised inner
+// operator is num / den (row sum of the rounded values computed on the fly,
+// so no per-row factor has to be gathered).
 template <typename Q, typename GX>
-__device__ __forceinline__ float lp_group_dot(uint4 G, int64_t i0, int64_t b, int64_t e,
-                                              int64_t s, GX x, float acc) {
+__device__ __forceinline__ void lp_group_dot(uint4 G, int64_t i0, int64_t b, int64_t e, int64_t s,
+                                             GX x, float& num, float& den) {
   const uint32_t dw[2] = {G.x, G.y};
   const uint32_t qw[2] = {G.z, G.w};
 #pragma unroll
@@ -474,23 +477,24 @@ __device__ __forceinline__ float lp_group_dot(uint4 G, int64_t i0, int64_t b, in
     if (i >= b && i < e) {
       const int32_t c = static_cast<int32_t>(s) + lp_off(dw[q >> 1], q & 1);
       const float v = Q16<Q>::f(q & 1 ? (qw[q >> 1] >> 16) : (qw[q >> 1] & 0xffffu));
-      acc = fmaf(v, x(c), acc);
+      num = fmaf(v, x(c), num);
+      den += v;
     }
   }
-  return acc;
 }
 
 // Lane `lane` of VW takes groups g0 + lane, g0 + lane + VW, ... of row [b, e)
-// of state s; the caller reduces over the VW lanes.
+// of state s; the caller reduces num and den over the VW lanes.
 template <int VW, typename Q, typename GX>
-__device__ __forceinline__ float row_dot_lp(const uint4* __restrict__ lpk, GX x, int64_t s,
-                                            int64_t b, int64_t e, int lane) {
-  float acc = 0.f;
+__device__ __forceinline__ void row_dot_lp(const uint4* __restrict__ lpk, GX x, int64_t s,
+                                           int64_t b, int64_t e, int lane, float& num,
+                                           float& den) {
+  num = 0.f;
+  den = 0.f;
   const int64_t g1 = (e + 3) >> 2;
 #pragma unroll 2
   for (int64_t g = (b >> 2) + lane; g < g1; g += VW)
-    acc = lp_group_dot<Q>(__ldcs(lpk + g), g << 2, b, e, s, x, acc);
-  return acc;
+    lp_group_dot<Q>(__ldcs(lpk + g), g << 2, b, e, s, x, num, den);
 }
 
 // Fast path: VW rows (states srow[u]) of 4*VW aligned entries; lane l loads
@@ -498,14 +502,18 @@ __device__ __forceinline__ float row_dot_lp(const uint4* __restrict__ lpk, GX x,
 template <int VW, typename Q, typename GX>
 __device__ __forceinline__ void vec_rows_lp(const uint4* __restrict__ lpk, GX x,
                                             const int64_t (&b)[VW], const int64_t (&srow)[VW],
-                                            const bool (&valid)[VW], int lane, float (&p)[VW]) {
+                                            const bool (&valid)[VW], int lane, float (&num)[VW],
+                                            float (&den)[VW]) {
   uint4 G[VW];
 #pragma unroll
-  for (int u = 0; u < VW; ++u) G[u] = valid[u] ? __ldcs(lpk + (b[u] >> 2) + lane) : make_uint4(0, 0, 0, 0);
+  for (int u = 0; u < VW; ++u)
+    G[u] = valid[u] ? __ldcs(lpk + (b[u] >> 2) + lane) : make_uint4(0, 0, 0, 0);
 #pragma unroll
   for (int u = 0; u < VW; ++u) {
     const int64_t i0 = b[u] + 4 * lane;
-    p[u] = valid[u] ? lp_group_dot<Q>(G[u], i0, i0, i0 + 4, srow[u], x, 0.f) : 0.f;
+    num[u] = 0.f;
+    den[u] = 0.f;
+    if (valid[u]) lp_group_dot<Q>(G[u], i0, i0, i0 + 4, srow[u], x, num[u], den[u]);
   }
 }
 

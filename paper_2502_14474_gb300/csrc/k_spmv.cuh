@@ -121,21 +121,28 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
                 vd[u] = __shfl_sync(0xffffffffu, valid ? 1 : 0, u, VW) != 0;
               }
               float part[VW];
+              bool packed = false;
+              float d = 0.f;
               if constexpr (sizeof(PV) == 2) {
                 if (P.lpk) {
                   int64_t srow[VW];
+                  float den[VW];
 #pragma unroll
                   for (int u = 0; u < VW; ++u) srow[u] = s - lane + u;
-                  vec_rows_lp<VW, PV>(P.lpk, gx, b, srow, vd, lane, part);
+                  vec_rows_lp<VW, PV>(P.lpk, gx, b, srow, vd, lane, part, den);
+                  d = reduce_scatter<VW>(part, lane);
+                  const float dd = reduce_scatter<VW>(den, lane);
+                  d = dd > 0.f ? d / dd : 0.f;
+                  packed = true;
                 } else {
                   vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
                 }
               } else {
                 vec_rows_f32<VW, PV>(P.col, val, gx, b, vd, lane, part);
               }
-              float d = reduce_scatter<VW>(part, lane);
+              if (!packed) d = reduce_scatter<VW>(part, lane);
               if (valid) {
-                if (lp) d *= __ldcs(P.row_scale + r);
+                if (lp && !packed) d *= __ldcs(P.row_scale + r);
                 uw[s] = sj * fmaf(-P.gamma, d, xs(s));
               }
             }
@@ -149,11 +156,12 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
               r = s * P.m + __ldg(pi + s);
               row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
             }
-            float d = 0.f;
-            if constexpr (sizeof(PV) == 2) d = row_dot_lp<VW, PV>(P.lpk, gx, s, b, e, lane);
-            d = group_sum<VW>(d);
+            float num = 0.f, den = 0.f;
+            if constexpr (sizeof(PV) == 2) row_dot_lp<VW, PV>(P.lpk, gx, s, b, e, lane, num, den);
+            num = group_sum<VW>(num);
+            den = group_sum<VW>(den);
             if (lane == 0 && s < P.n) {
-              d *= __ldcs(P.row_scale + r);
+              const float d = den > 0.f ? num / den : 0.f;
               uw[s] = sj * fmaf(-P.gamma, d, xs(s));
             }
           }
