@@ -378,8 +378,11 @@ def main():
 
     host = _workload(n=args.n)
     nnz = host.nnz
-    h = MDP.from_csr(host, store=args.store)
     dev = torch.device("cuda", local)
+    # a dedicated stream: the library replays each GMRES restart cycle as a CUDA
+    # graph there (the legacy default stream cannot be captured)
+    solve_stream = torch.cuda.Stream(device=dev)
+    h = MDP.from_csr(host, store=args.store, stream=solve_stream)
     opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart, inner_norm=args.inner_norm,
                 max_inner=args.max_inner)
 
@@ -403,7 +406,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K full solves (no per-launch events) ---------------------
-    stream = torch.cuda.current_stream(dev)
+    stream = solve_stream
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
                            if ws == 1 else local)
 

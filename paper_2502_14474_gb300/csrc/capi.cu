@@ -112,6 +112,16 @@ struct mdp_s {
   int64_t launches = 0;
   cudaStream_t home = nullptr;   // stream of mdp_create: device memory is allocated in its order
   cudaEvent_t done_ev = nullptr; // recorded at the end of every call: destroy waits on it
+  // captured GMRES restart cycles, replayed with one launch each
+  struct CycleGraph {
+    int steps;
+    bool lp;
+    int cgs2;
+    const int32_t* pi;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CycleGraph> graphs;
+  int64_t eager_cycles = 0;
 };
 
 namespace {
@@ -267,6 +277,8 @@ void free_all(mdp_s* h) {
       else cudaFree(p);
     }
   if (h->done_ev) cudaEventDestroy(h->done_ev);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
   free(h->head);
   for (ProfRec& r : h->prof.pending) {
     cudaEventDestroy(r.a);
@@ -463,27 +475,84 @@ mdp_status check_policy(mdp_s* h, const int32_t* pi, cudaStream_t s) {
   return MDP_OK;
 }
 
+// Enqueue the kernels of one restart cycle: `steps` Arnoldi steps (policy-row
+// SpMV, Gram-Schmidt dots, orthogonalisation + Givens) and the solution update.
+cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+                          cudaStream_t s) {
+  for (int j = 0; j < steps; ++j) {
+    cudaError_t e = run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), j, [&] {
+      return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
+    });
+    if (e != cudaSuccess) return e;
+    e = run(h, s, MDP_PROF_ARNOLDI_DOTS, 1, bytes_dots(h->A, j), j, [&] {
+      return launch_arnoldi_dots(h->A, h->basis, h->ld, j, steps, 0, h->partials, h->st, s);
+    });
+    if (e != cudaSuccess) return e;
+    e = run(h, s, MDP_PROF_ARNOLDI_ORTHO, cgs2 ? 3 : 1, bytes_ortho(h->A, j, cgs2), j, [&] {
+      return launch_arnoldi_ortho(h->A, h->basis, h->ld, j, steps, cgs2, h->partials, h->st, s);
+    });
+    if (e != cudaSuccess) return e;
+  }
+  return run(h, s, MDP_PROF_GMRES_UPDATE, 1, 0.0, -1, [&] {
+    return launch_gmres_update(h->A, h->basis, h->ld, h->V, h->st, s);
+  });
+}
+
+// The captured graph of a cycle configuration (captured on first use after
+// one eager cycle has initialised every launcher); nullptr when capture is not
+// possible (legacy default stream, profiling, or a capture error).
+cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+                            cudaStream_t s) {
+  if (h->prof.on || s == nullptr || h->eager_cycles == 0 || getenv("MDP_NO_GRAPHS"))
+    return nullptr;
+  for (auto& g : h->graphs)
+    if (g.steps == steps && g.lp == lp && g.cgs2 == cgs2 && g.pi == pi) return g.exec;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;  // the caller is capturing: stay eager inside its graph
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const int64_t launches = h->launches;
+  cudaError_t e = enqueue_cycle(h, pi, steps, lp, cgs2, s);
+  h->launches = launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && e2 == cudaSuccess && graph &&
+      cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    if (h->graphs.size() >= 8) {
+      cudaGraphExecDestroy(h->graphs.front().exec);
+      h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back({steps, lp, cgs2, pi, exec});
+  } else {
+    exec = nullptr;
+    cudaGetLastError();
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return exec;
+}
+
 // One GMRES restart cycle on the current device residual (already in u_0 with
-// the cycle begun by the kernel that produced it).  Enqueues up to `steps`
-// Arnoldi steps and the solution update, then reads the cycle's outcome.
+// the cycle begun by the kernel that produced it): `steps` Arnoldi steps and
+// the solution update, replayed from a captured graph when possible; then the
+// cycle's outcome is read back.
 mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
                        cudaStream_t s, int* jdone, int* converged) {
   const size_t first = h->prof.pending.size();
-  for (int j = 0; j < steps; ++j) {
-    CK(h, run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), j, [&] {
-         return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
-       }));
-    CK(h, run(h, s, MDP_PROF_ARNOLDI_DOTS, 1, bytes_dots(h->A, j), j, [&] {
-         return launch_arnoldi_dots(h->A, h->basis, h->ld, j, steps, 0, h->partials, h->st, s);
-       }));
-    CK(h, run(h, s, MDP_PROF_ARNOLDI_ORTHO, cgs2 ? 3 : 1, bytes_ortho(h->A, j, cgs2), j, [&] {
-         return launch_arnoldi_ortho(h->A, h->basis, h->ld, j, steps, cgs2, h->partials, h->st, s);
-       }));
+  cudaGraphExec_t g = cycle_graph(h, pi, steps, lp, cgs2, s);
+  if (g) {
+    CK(h, cudaGraphLaunch(g, s));
+    h->launches += static_cast<int64_t>(steps) * (cgs2 ? 5 : 3) + 1;
+  } else {
+    CK(h, enqueue_cycle(h, pi, steps, lp, cgs2, s));
+    h->eager_cycles += 1;
   }
-  const size_t upd = h->prof.pending.size();
-  CK(h, run(h, s, MDP_PROF_GMRES_UPDATE, 1, 0.0, -1, [&] {
-       return launch_gmres_update(h->A, h->basis, h->ld, h->V, h->st, s);
-     }));
+  const size_t upd = h->prof.pending.empty() ? 0 : h->prof.pending.size() - 1;
   mdp_status rc = read_head(h, s, false);
   if (rc != MDP_OK) return rc;
   *jdone = h->head->jdone;
@@ -492,7 +561,7 @@ mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2
   for (size_t i = first; i < h->prof.pending.size(); ++i) {
     ProfRec& r = h->prof.pending[i];
     if (r.j >= *jdone) r.skipped = true;
-    if (i == upd) {
+    if (i == upd && r.kind == MDP_PROF_GMRES_UPDATE) {
       r.bytes = bytes_update(h->A, *jdone);
       r.skipped = *jdone == 0;
     }
