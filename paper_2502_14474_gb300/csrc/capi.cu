@@ -498,12 +498,14 @@ cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int c
   });
 }
 
-// The captured graph of a cycle configuration (captured on first use after
-// one eager cycle has initialised every launcher); nullptr when capture is not
-// possible (legacy default stream, profiling, or a capture error).
+// The captured graph of a cycle configuration (captured once the handle has
+// run four eager cycles, which also initialised every launcher); nullptr when
+// capture is not possible (legacy default stream, profiling, or a capture error).
 cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
                             cudaStream_t s) {
-  if (h->prof.on || s == nullptr || h->eager_cycles == 0 || getenv("MDP_NO_GRAPHS"))
+  // capture pays off for handles that run many cycles (long or repeated
+  // solves); short-lived handles stay eager (instantiation costs ~a cycle)
+  if (h->prof.on || s == nullptr || h->eager_cycles < 4 || getenv("MDP_NO_GRAPHS"))
     return nullptr;
   for (auto& g : h->graphs)
     if (g.steps == steps && g.lp == lp && g.cgs2 == cgs2 && g.pi == pi) return g.exec;
