@@ -104,33 +104,50 @@ __device__ void givens_step(DevState* st, int j, double nrm) {
 // mode 2: second pass of CGS2 with st->h2 (added into H), then Givens.
 // ---------------------------------------------------------------------------
 // Subtract sum_i c_i u_i from one float4 quad of u_{j+1} (c_i = coef[i]).
+__device__ __forceinline__ void ortho_fma(float4& w, float c, const float4& b) {
+  w.x = fmaf(-c, b.x, w.x);
+  w.y = fmaf(-c, b.y, w.y);
+  w.z = fmaf(-c, b.z, w.z);
+  w.w = fmaf(-c, b.w, w.w);
+}
+
+// wa, wb -= sum_{i <= j} coef_i v_i at the quads starting at states sa, sb:
+// two basis vectors per step, so four 16-byte loads are in flight per thread.
+// The basis is streamed once per pass (evict-first).
+__device__ __forceinline__ void ortho_pair(const float* __restrict__ basis, int64_t ld, int j,
+                                           const float* coef, int64_t sa, int64_t sb, float4& wa,
+                                           float4& wb) {
+  int i = 0;
+  for (; i + 1 <= j; i += 2) {
+    const float* b0 = basis + static_cast<int64_t>(i) * ld;
+    const float* b1 = b0 + ld;
+    const float4 a0 = __ldcs(reinterpret_cast<const float4*>(b0 + sa));
+    const float4 c0 = __ldcs(reinterpret_cast<const float4*>(b0 + sb));
+    const float4 a1 = __ldcs(reinterpret_cast<const float4*>(b1 + sa));
+    const float4 c1 = __ldcs(reinterpret_cast<const float4*>(b1 + sb));
+    ortho_fma(wa, coef[i], a0);
+    ortho_fma(wb, coef[i], c0);
+    ortho_fma(wa, coef[i + 1], a1);
+    ortho_fma(wb, coef[i + 1], c1);
+  }
+  if (i <= j) {
+    const float* b0 = basis + static_cast<int64_t>(i) * ld;
+    ortho_fma(wa, coef[i], __ldcs(reinterpret_cast<const float4*>(b0 + sa)));
+    ortho_fma(wb, coef[i], __ldcs(reinterpret_cast<const float4*>(b0 + sb)));
+  }
+}
+
+// One quad on its own (ragged end of the vector), same order of operations.
 __device__ __forceinline__ float4 ortho_quad(const float* __restrict__ basis, int64_t ld, int j,
                                              const float* coef, int64_t s, float4 w) {
-  int i = 0;
-  for (; i + 3 <= j; i += 4) {
-    const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
-    const float4 b1 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 1) * ld + s);
-    const float4 b2 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 2) * ld + s);
-    const float4 b3 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i + 3) * ld + s);
-    const float c0 = coef[i], c1 = coef[i + 1], c2 = coef[i + 2], c3 = coef[i + 3];
-    w.x = fmaf(-c3, b3.x, fmaf(-c2, b2.x, fmaf(-c1, b1.x, fmaf(-c0, b0.x, w.x))));
-    w.y = fmaf(-c3, b3.y, fmaf(-c2, b2.y, fmaf(-c1, b1.y, fmaf(-c0, b0.y, w.y))));
-    w.z = fmaf(-c3, b3.z, fmaf(-c2, b2.z, fmaf(-c1, b1.z, fmaf(-c0, b0.z, w.z))));
-    w.w = fmaf(-c3, b3.w, fmaf(-c2, b2.w, fmaf(-c1, b1.w, fmaf(-c0, b0.w, w.w))));
-  }
-  for (; i <= j; ++i) {
-    const float4 b0 = *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s);
-    const float c0 = coef[i];
-    w.x = fmaf(-c0, b0.x, w.x);
-    w.y = fmaf(-c0, b0.y, w.y);
-    w.z = fmaf(-c0, b0.z, w.z);
-    w.w = fmaf(-c0, b0.w, w.w);
-  }
+  for (int i = 0; i <= j; ++i)
+    ortho_fma(w, coef[i], *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(i) * ld + s));
   return w;
 }
 
-// Tile = 8*kThreads states: thread t owns quads t and t + kThreads of the tile
-// (two independent chains of basis loads in flight).
+// Tile = 8*kThreads states, 256 per warp: lane l of warp w owns the quads at
+// states 256w + 4l and 256w + 128 + 4l, so each warp reads one contiguous
+// kilobyte of every basis vector per tile (long DRAM runs).
 __global__ void __launch_bounds__(kThreads)
     k_arnoldi_ortho(int64_t n, Grid G, float* __restrict__ basis, int64_t ld, int j, int mode,
                     double* __restrict__ partials, DevState* __restrict__ st) {
@@ -146,13 +163,12 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s_a = tile * (8 * kThreads) + 4 * threadIdx.x;
-    const int64_t s_b = s_a + 4 * kThreads;
+    const int64_t s_a = tile * (8 * kThreads) + 256 * (threadIdx.x >> 5) + 4 * (threadIdx.x & 31);
+    const int64_t s_b = s_a + 128;
     if (s_b + 3 < n) {
       float4 wa = *reinterpret_cast<const float4*>(uw + s_a);
       float4 wb = *reinterpret_cast<const float4*>(uw + s_b);
-      wa = ortho_quad(basis, ld, j, coef, s_a, wa);
-      wb = ortho_quad(basis, ld, j, coef, s_b, wb);
+      ortho_pair(basis, ld, j, coef, s_a, s_b, wa, wb);
       *reinterpret_cast<float4*>(uw + s_a) = wa;
       *reinterpret_cast<float4*>(uw + s_b) = wb;
       acc = fmaf(wa.x, wa.x, fmaf(wa.y, wa.y, fmaf(wa.z, wa.z, fmaf(wa.w, wa.w, acc))));

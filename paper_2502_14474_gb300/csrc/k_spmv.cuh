@@ -259,72 +259,6 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
 }
 
 // ---------------------------------------------------------------------------
-// Gram-Schmidt dots h_i = <w, v_i>, i <= j, of the stored w = u_{j+1}: a pure
-// stream over j+2 vectors.  Tile = 4*QPT*NT states; thread t owns QPT float4
-// quads of each tile, so one warp reduction per basis vector covers 4*QPT*32
-// states and QPT loads per vector are in flight.
-// ---------------------------------------------------------------------------
-template <int MAXB, int NT, int QPT>
-__global__ void __launch_bounds__(NT)
-    k_gs_dots(int64_t n, Grid G, const float* __restrict__ basis, int64_t ld, int j, int out_h2,
-              double* __restrict__ partials, DevState* __restrict__ st) {
-  if (!st->active) return;
-  constexpr int TS = 4 * QPT * NT;
-  __shared__ float wacc[NT / 32][MAXB];
-  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < (NT / 32) * MAXB; i += NT) (&wacc[0][0])[i] = 0.f;
-  __syncthreads();
-  const float* uw = basis + static_cast<int64_t>(j + 1) * ld;
-  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
-  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
-  for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s0 = tile * TS;
-    float4 w[QPT];
-    bool full[QPT];
-#pragma unroll
-    for (int q = 0; q < QPT; ++q) {
-      const int64_t sq = s0 + 4 * (q * NT + threadIdx.x);
-      full[q] = sq + 3 < n;
-      w[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (full[q]) {
-        w[q] = *reinterpret_cast<const float4*>(uw + sq);
-      } else if (sq < n) {
-        w[q].x = uw[sq];
-        if (sq + 1 < n) w[q].y = uw[sq + 1];
-        if (sq + 2 < n) w[q].z = uw[sq + 2];
-      }
-    }
-#pragma unroll 2
-    for (int i = 0; i <= j; ++i) {
-      const float* bi = basis + static_cast<int64_t>(i) * ld;
-      float p = 0.f;
-#pragma unroll
-      for (int q = 0; q < QPT; ++q) {
-        const int64_t sq = s0 + 4 * (q * NT + threadIdx.x);
-        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (full[q]) {
-          b4 = *reinterpret_cast<const float4*>(bi + sq);
-        } else if (sq < n) {
-          b4.x = bi[sq];
-          if (sq + 1 < n) b4.y = bi[sq + 1];
-          if (sq + 2 < n) b4.z = bi[sq + 2];
-        }
-        p = fmaf(w[q].x, b4.x, fmaf(w[q].y, b4.y, fmaf(w[q].z, b4.z, fmaf(w[q].w, b4.w, p))));
-      }
-      p = warp_sum(p);
-      if (wl == 0) wacc[warp][i] += p;
-    }
-  }
-  publish_dots_nt<MAXB, NT>(j, partials, wacc);
-  const unsigned cnt = out_h2 ? kCntDots2 : kCntDots;
-  if (last_block(&st->counter[cnt])) {
-    double* out = out_h2 ? st->h2 : st->H + static_cast<int64_t>(j) * kMaxBasis;
-    reduce_dots_nt<MAXB, NT>(partials, j, out, st->scale);
-    if (threadIdx.x == 0) st->counter[cnt] = 0;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
 template <typename IdxT>
@@ -427,27 +361,6 @@ cudaError_t spmv_entry(const Mat& A, const int32_t* pi, float* basis, int64_t ld
                        double* partials, DevState* st, cudaStream_t s) {
   return A.idx64 ? spmv_vw<int64_t, PV>(A, pi, basis, ld, j, partials, st, s)
                  : spmv_vw<int32_t, PV>(A, pi, basis, ld, j, partials, st, s);
-}
-
-// Gram-Schmidt dots of the stored u_{j+1} against v_0..v_j.
-template <int MAXB>
-cudaError_t dots_launch(const Mat& A, float* basis, int64_t ld, int j, int out_h2,
-                        double* partials, DevState* st, cudaStream_t s) {
-  constexpr int NT = 256, QPT = 4, TS = 4 * QPT * NT;
-  auto kern = k_gs_dots<MAXB, NT, QPT>;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1)
-    occ = 1;
-  const Grid G = tiles_grid((A.n + TS - 1) / TS, A.num_sms * occ, TS);
-  kern<<<static_cast<unsigned>(tiles_blocks(G)), NT, 0, s>>>(A.n, G, basis, ld, j, out_h2,
-                                                             partials, st);
-  return cudaGetLastError();
-}
-
-inline cudaError_t dots_entry(const Mat& A, float* basis, int64_t ld, int j, int restart,
-                              int out_h2, double* partials, DevState* st, cudaStream_t s) {
-  if (restart + 1 <= 32) return dots_launch<32>(A, basis, ld, j, out_h2, partials, st, s);
-  return dots_launch<kMaxBasis>(A, basis, ld, j, out_h2, partials, st, s);
 }
 
 }  // namespace mdpk

@@ -1,4 +1,6 @@
-// K2 instantiations for f32 probabilities (see k_spmv.cuh).
+// K2 instantiations for f32 probabilities (see k_spmv.cuh) and the
+// Gram-Schmidt dots (k_dots.cuh).
+#include "k_dots.cuh"
 #include "k_spmv.cuh"
 
 namespace mdpk {
