@@ -10,8 +10,13 @@
 // [ (b % VG) * VPB, +VPB ) and chunks b / VG, b / VG + S, ... of the S chunk
 // slots; consecutive blocks share a chunk, so w is fetched from DRAM once and
 // served from L2 to the other vector groups.  The FP64 partial of slot y for
-// vector i lands in partials[y * MAXB + i]; the last block sums the slots in a
-// fixed order, so results are deterministic.  Included by one translation unit.
+// vector i lands in partials[y * MAXB + i].  Two-level fixed-order reduction:
+// the last block of each run of eight slots (a ticket per run and group) sums
+// the run in slot order into the run's first slot, and the last run of each
+// group (a ticket per group) sums the runs in order and scales the result.
+// Results are deterministic, and no single block has to read every partial
+// (at 1024 slots that read cost about 8 us of L2 round trips per launch).
+// Included by one translation unit.
 #pragma once
 
 #include "launch.h"
@@ -21,6 +26,7 @@ namespace mdpk {
 
 constexpr int kDotsThreads = 256;
 constexpr int kDotsChunk = 4096;  // states of w staged per block (16 KB)
+constexpr int kDotsRun = 8;       // chunk slots per first-level reduction
 
 template <int MAXB, int WPV>
 __global__ void __launch_bounds__(kDotsThreads)
@@ -89,31 +95,61 @@ __global__ void __launch_bounds__(kDotsThreads)
       partials[slot * MAXB + ii] = s;
     }
   }
-  const unsigned cnt = out_h2 ? kCntDots2 : kCntDots;
-  if (last_block(&st->counter[cnt])) {
-    // warp w reduces dots i = w, w + 8, ...; lanes stride over the slots and a
-    // fixed shuffle tree combines them
-    double* out = out_h2 ? st->h2 : st->H + static_cast<int64_t>(j) * kMaxBasis;
-    for (int d = warp; d <= j; d += NW) {
+  __shared__ bool s_last;
+  // level 1: the last block of this run of slots sums the run, in slot order
+  const int64_t run = slot / kDotsRun, runs = (slots + kDotsRun - 1) / kDotsRun;
+  const int64_t run_len = min(static_cast<int64_t>(kDotsRun), slots - run * kDotsRun);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->dots_run[gx][run], 1u) == run_len - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < VPB) {
+    const int d = gx * VPB + threadIdx.x;
+    if (d <= j) {
+      const double* pr = partials + run * kDotsRun * MAXB + d;
+      double v[kDotsRun];
+#pragma unroll
+      for (int k = 0; k < kDotsRun; ++k) v[k] = k < run_len ? __ldcg(pr + k * MAXB) : 0.0;
       double s = 0.0;
-#pragma unroll 4
-      for (int64_t y = lane; y < slots; y += 32) s += __ldcg(partials + y * MAXB + d);
-      s = warp_sum_d(s);
-      if (lane == 0) out[d] = s * st->scale[d];
+#pragma unroll
+      for (int k = 0; k < kDotsRun; ++k) s += v[k];
+      partials[run * kDotsRun * MAXB + d] = s;  // the run's first slot
     }
-    if (threadIdx.x == 0) st->counter[cnt] = 0;
   }
+  if (threadIdx.x == 0) st->dots_run[gx][run] = 0;
+  // level 2: the last run of this vector group sums the runs in order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->dots_group[gx], 1u) == runs - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double* out = out_h2 ? st->h2 : st->H + static_cast<int64_t>(j) * kMaxBasis;
+  for (int v = warp; v < VPB; v += NW) {
+    const int d = gx * VPB + v;
+    if (d > j) break;
+    // lanes stride over the runs; a fixed shuffle tree combines them
+    double s = 0.0;
+    for (int64_t r = lane; r < runs; r += 32) s += __ldcg(partials + r * kDotsRun * MAXB + d);
+    s = warp_sum_d(s);
+    if (lane == 0) out[d] = s * st->scale[d];
+  }
+  if (threadIdx.x == 0) st->dots_group[gx] = 0;
 }
 
 // Grid: ceil((j+1)/VPB) vector groups x S chunk slots, S bounded by the
-// partials buffer (num_sms * 8 slots of MAXB doubles each, MAXB <= 65).
+// partials buffer (num_sms * 8 slots of MAXB doubles each, MAXB <= 65) and by
+// the run tickets (kDotsMaxRuns runs of kDotsRun slots).
 template <int MAXB, int WPV>
 cudaError_t dots_launch_w(const Mat& A, float* basis, int64_t ld, int j, int out_h2,
                           double* partials, DevState* st, cudaStream_t s) {
   constexpr int VPB = (kDotsThreads / 32) / WPV;
   const int vg = (j + 1 + VPB - 1) / VPB;
   const int64_t n_chunks = (A.n + kDotsChunk - 1) / kDotsChunk;
-  const int64_t max_slots = static_cast<int64_t>(A.num_sms) * 8;
+  const int64_t max_slots =
+      static_cast<int64_t>(A.num_sms < kDotsMaxRuns ? A.num_sms : kDotsMaxRuns) * kDotsRun;
   const int64_t slots = n_chunks < max_slots ? n_chunks : max_slots;
   k_gs_dots<MAXB, WPV><<<static_cast<unsigned>(slots * vg), kDotsThreads, 0, s>>>(
       A.n, n_chunks, vg, basis, ld, j, out_h2, partials, st);

@@ -12,6 +12,7 @@
 namespace mdpk {
 
 constexpr int kThreads = 256;     // threads per CTA for every streaming kernel
+constexpr int kDotsMaxRuns = 256;  // dots kernel: at most 8 * 256 chunk slots
 constexpr int kMaxRestart = 64;   // GMRES restart cap (basis holds restart+1 vectors)
 constexpr int kMaxBasis = kMaxRestart + 1;
 
@@ -232,6 +233,10 @@ struct DevState {
   double y[kMaxRestart];
   double scale[kMaxBasis];  // v_i = u_i * scale[i]
   double h2[kMaxBasis];     // second Gram-Schmidt pass coefficients
+  // tickets of the Gram-Schmidt dots kernel: per vector group, and per run of
+  // eight chunk slots within a group (two-level fixed-order reduction)
+  unsigned dots_group[kMaxBasis / 8 + 1];
+  unsigned dots_run[kMaxBasis / 8 + 1][kDotsMaxRuns];
 };
 
 // Initialise a GMRES cycle from ||r0||_2 = beta (single thread).
