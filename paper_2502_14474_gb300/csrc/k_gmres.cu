@@ -145,11 +145,13 @@ __device__ __forceinline__ float4 ortho_quad(const float* __restrict__ basis, in
   return w;
 }
 
-// Tile = 8*kThreads states, 256 per warp: lane l of warp w owns the quads at
-// states 256w + 4l and 256w + 128 + 4l, so each warp reads one contiguous
-// kilobyte of every basis vector per tile (long DRAM runs).
+// Warp tiles of 256 states: lane l owns the quads at states 256t + 4l and
+// 256t + 128 + 4l of warp tile t, so a warp reads one contiguous kilobyte of
+// every basis vector per tile (long DRAM runs).  Warps take tiles t = global
+// warp index, + total warps, ... : every warp gets the same number of tiles
+// to within one.
 __global__ void __launch_bounds__(kThreads)
-    k_arnoldi_ortho(int64_t n, Grid G, float* __restrict__ basis, int64_t ld, int j, int mode,
+    k_arnoldi_ortho(int64_t n, float* __restrict__ basis, int64_t ld, int j, int mode,
                     double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   __shared__ float coef[kMaxBasis];
@@ -160,10 +162,11 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   float* uw = basis + static_cast<int64_t>(j + 1) * ld;
   float acc = 0.f;
-  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
-  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
-  for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s_a = tile * (8 * kThreads) + 256 * (threadIdx.x >> 5) + 4 * (threadIdx.x & 31);
+  const int64_t n_wt = (n + 255) / 256;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kThreads / 32);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+       t < n_wt; t += nw) {
+    const int64_t s_a = t * 256 + 4 * (threadIdx.x & 31);
     const int64_t s_b = s_a + 128;
     if (s_b + 3 < n) {
       float4 wa = *reinterpret_cast<const float4*>(uw + s_a);
@@ -182,11 +185,11 @@ __global__ void __launch_bounds__(kThreads)
           *reinterpret_cast<float4*>(uw + sq) = w;
           acc = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, acc))));
         } else {
-          for (int64_t t = sq; t < n && t < sq + 4; ++t) {
-            float w = uw[t];
+          for (int64_t t2 = sq; t2 < n && t2 < sq + 4; ++t2) {
+            float w = uw[t2];
             for (int i = 0; i <= j; ++i)
-              w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + t], w);
-            uw[t] = w;
+              w = fmaf(-coef[i], basis[static_cast<int64_t>(i) * ld + t2], w);
+            uw[t2] = w;
             acc = fmaf(w, w, acc);
           }
         }
@@ -394,19 +397,20 @@ static Grid stream_grid(int64_t n, int num_sms, int occ) {
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
                                  int cgs2, double* partials, DevState* st, cudaStream_t s) {
   static int occ = occ_of(k_arnoldi_ortho);
-  const Grid G = grid_for((A.n + 8 * kThreads - 1) / (8 * kThreads), A.num_sms * occ,
-                          8 * kThreads);
-  const unsigned nb = static_cast<unsigned>(grid_blocks(G));
+  const int64_t warp_tiles = (A.n + 255) / 256;
+  const int64_t want = (warp_tiles + kThreads / 32 - 1) / (kThreads / 32);
+  const int64_t cap = static_cast<int64_t>(A.num_sms) * occ;
+  const unsigned nb = static_cast<unsigned>(want < cap ? (want < 1 ? 1 : want) : cap);
   if (!cgs2) {
-    k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 0, partials, st);
+    k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, basis, ld, j, 0, partials, st);
     return cudaGetLastError();
   }
-  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 1, partials, st);
+  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, basis, ld, j, 1, partials, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_arnoldi_dots(A, basis, ld, j, restart, 1, partials, st, s);
   if (e != cudaSuccess) return e;
-  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, G, basis, ld, j, 2, partials, st);
+  k_arnoldi_ortho<<<nb, kThreads, 0, s>>>(A.n, basis, ld, j, 2, partials, st);
   return cudaGetLastError();
 }
 
