@@ -480,7 +480,7 @@ def main():
 
         def one():
             m = MDP(host.n, host.m, hp["row_ptr"].numpy(), hp["col"].numpy(), hp["val"].numpy(),
-                    hp["g"].numpy(), host.gamma, store=args.store)
+                    hp["g"].numpy(), host.gamma, store=args.store, stream=solve_stream)
             Vd, pid, s = m.solve(**opts)
             Vh.copy_(Vd, non_blocking=True)
             pih.copy_(pid, non_blocking=True)

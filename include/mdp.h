@@ -305,6 +305,20 @@ mdp_status mdp_bellman_noalloc(int64_t n_states, int32_t n_actions, const int64_
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* mdp_last_error(void);
 
+/* Hand device memory cached by the library back to the device.
+ *
+ * No counterpart in the paper: a memory-management call of this
+ * implementation.  Handles take their device memory from a stream-ordered
+ * pool that the library owns, one per device, and that keeps the memory of
+ * destroyed handles mapped so that later handles reuse it without mapping new
+ * pages.  This call waits for the frees of destroyed handles on `device` to
+ * complete, then releases cached memory until at most `keep_bytes` stay
+ * reserved (memory of live handles is never released).  `reserved_after`
+ * (may be NULL) receives the bytes the pool still reserves.  Returns
+ * MDP_ERR_ARG for a device index out of range, MDP_ERR_CUDA if a CUDA call
+ * fails. */
+mdp_status mdp_pool_trim(int32_t device, uint64_t keep_bytes, uint64_t* reserved_after);
+
 /* Library version string. */
 const char* mdp_version(void);
 

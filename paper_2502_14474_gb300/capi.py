@@ -28,7 +28,7 @@ MDP_HISTORY = 128
 EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
-                   "mdp_bellman_noalloc", "mdp_batch_solve"])
+                   "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
               "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
@@ -163,6 +163,8 @@ def load(build_if_missing: bool = True):
         lib.mdp_batch_solve.argtypes = [P, I32, ctypes.POINTER(mdp_solve_opts), P, P,
                                         ctypes.POINTER(mdp_solve_stats), P, I32]
         lib.mdp_batch_solve.restype = ctypes.c_int
+        lib.mdp_pool_trim.argtypes = [I32, U64, ctypes.POINTER(U64)]
+        lib.mdp_pool_trim.restype = ctypes.c_int
         lib.mdp_last_error.argtypes = []
         lib.mdp_last_error.restype = ctypes.c_char_p
         lib.mdp_version.argtypes = []
@@ -273,6 +275,14 @@ def mdp_info(h) -> dict:
 def mdp_bytes_required(n_states, n_actions, nnz, val_t=MDP_F32, store_t=MDP_F32, restart=30):
     return int(load().mdp_bytes_required(int(n_states), int(n_actions), int(nnz), int(val_t),
                                          int(store_t), int(restart)))
+
+
+def mdp_pool_trim(device: int = 0, keep_bytes: int = 0) -> int:
+    """Release device memory cached by the library's pool on `device` down to
+    keep_bytes; returns the bytes the pool still reserves."""
+    out = ctypes.c_uint64(0)
+    _check(load().mdp_pool_trim(int(device), int(keep_bytes), ctypes.byref(out)))
+    return int(out.value)
 
 
 def mdp_cancel(h):

@@ -147,14 +147,50 @@ struct DeviceGuard {
     }                                                                                    \
   } while (0)
 
-// Device memory comes from the device's stream-ordered pool (cudaMallocAsync /
-// cudaFreeAsync): creating and destroying handles does not synchronise the
-// device, so handles of concurrent solves (batch, serving) come and go while
-// other streams keep running.
+// Device memory comes from a stream-ordered pool that the library owns, one
+// per device (cudaMemPoolCreate; cudaMallocFromPoolAsync / cudaFreeAsync):
+// creating and destroying handles does not synchronise the device, so handles
+// of concurrent solves (batch, serving) come and go while other streams keep
+// running.  The pool keeps freed memory mapped (no release threshold): a
+// handle created after another was destroyed reuses its pages instead of
+// mapping new ones, which costs milliseconds per GB.  mdp_pool_trim hands
+// cached memory back to the device.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {nullptr};
+
+cudaMemPool_t device_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+      cudaGetLastError();
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t pool_alloc(int dev, void** q, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = device_pool(dev);
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(q, bytes < 16 ? 16 : bytes, pool, s);
+}
+
 template <typename T>
 cudaError_t dalloc(mdp_s* h, T** p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, h->home);
+  cudaError_t e = pool_alloc(h->device, &q, bytes, h->home);
   if (e == cudaSuccess) {
     *p = static_cast<T*>(q);
     h->bytes += bytes;
@@ -586,6 +622,37 @@ extern "C" {
 
 const char* mdp_last_error(void) { return g_err.c_str(); }
 
+mdp_status mdp_pool_trim(int32_t device, uint64_t keep_bytes, uint64_t* reserved_after) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_CUDA, "mdp_pool_trim: no CUDA device");
+  }
+  if (device < 0 || device >= count || device >= 64)
+    return fail(MDP_ERR_ARG, "mdp_pool_trim: device %d out of range", device);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    pool = g_pool[device];
+  }
+  uint64_t reserved = 0;
+  if (pool) {
+    DeviceGuard dg(device);
+    // frees of destroyed handles are queued on the library's free stream
+    cudaStream_t fs = free_stream(device);
+    if (fs && cudaStreamSynchronize(fs) != cudaSuccess)
+      return fail(MDP_ERR_CUDA, "mdp_pool_trim: waiting for pending frees failed");
+    if (cudaMemPoolTrimTo(pool, static_cast<size_t>(keep_bytes)) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return fail(MDP_ERR_CUDA, "mdp_pool_trim: trimming the pool failed");
+    }
+  }
+  if (reserved_after) *reserved_after = reserved;
+  return MDP_OK;
+}
+
 const char* mdp_version(void) { return "mdp-gb300 0.1 (sm_103a)"; }
 
 void mdp_default_opts(mdp_solve_opts* o) {
@@ -690,7 +757,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
                           gbytes};
     const void* src[4] = {row_ptr, col, val, cost};
     for (int i = 0; i < 4; ++i) {
-      if (cudaMallocAsync(&tmp[i], sz[i], s) != cudaSuccess) {
+      if (pool_alloc(h->device, &tmp[i], sz[i], s) != cudaSuccess) {
         cudaGetLastError();
         free_tmp();
         return bail(fail(MDP_ERR_OOM, "staging allocation failed"));
