@@ -28,7 +28,7 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
 }
 
 template <typename IdxT, int VW, typename PV, int NT, bool WIN>
-__global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
+__global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
     k_arnoldi_spmv(Csr<IdxT> P, int64_t states_per_block, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
                    DevState* __restrict__ st) {
@@ -110,6 +110,47 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 3 : 1))
               if (valid) {
                 if (lp && !packed) d *= __ldcs(P.row_scale + r);
                 uw[s] = sj * fmaf(-P.gamma, d, xs(s));
+              }
+            }
+          }
+        } else if (VW == 1 && sizeof(PV) == 2 && P.lpk) {
+          // packed 16-bit copy, short rows: two states per thread with the
+          // actions, row pointers and first two groups of both rows in flight
+          // together (a row of up to 5 entries never spans more than two groups)
+          if constexpr (VW == 1 && sizeof(PV) == 2) {
+            int32_t act[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              act[p] = s < s_lim ? __ldg(pi + s) : 0;
+            }
+#pragma unroll
+            for (int p = 0; p < 4; p += 2) {
+              int64_t s2[2], b2[2], e2[2];
+              uint4 G0[2], G1[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                s2[u] = s0 + (p + u) * NT + threadIdx.x;
+                b2[u] = 0;
+                e2[u] = 0;
+                if (s2[u] < s_lim)
+                  row_bounds<IdxT>(P.rp, P.uniform_len, s2[u] * P.m + act[p + u], b2[u], e2[u]);
+                const int64_t g0 = b2[u] >> 2;
+                G0[u] = (g0 << 2) < e2[u] ? __ldcs(P.lpk + g0) : make_uint4(0, 0, 0, 0);
+                G1[u] = ((g0 + 1) << 2) < e2[u] ? __ldcs(P.lpk + g0 + 1) : make_uint4(0, 0, 0, 0);
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                if (s2[u] < s_lim) {
+                  const int64_t g0 = b2[u] >> 2;
+                  float num = 0.f, den = 0.f;
+                  lp_group_dot<PV>(G0[u], g0 << 2, b2[u], e2[u], s2[u], gx, num, den);
+                  lp_group_dot<PV>(G1[u], (g0 + 1) << 2, b2[u], e2[u], s2[u], gx, num, den);
+                  for (int64_t g = g0 + 2; (g << 2) < e2[u]; ++g)
+                    lp_group_dot<PV>(__ldcs(P.lpk + g), g << 2, b2[u], e2[u], s2[u], gx, num, den);
+                  const float d = den > 0.f ? num / den : 0.f;
+                  uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+                }
               }
             }
           }
