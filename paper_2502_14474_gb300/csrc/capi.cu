@@ -82,6 +82,7 @@ struct mdp_s {
   // owned device memory
   void* rp = nullptr;
   uint32_t* pk = nullptr;   // packed col/val (groups of 4 entries, 32 bytes)
+  uint32_t* pk_am = nullptr;  // action-major policy copy (short rows), same format
   float* val_lo = nullptr;
   float* g = nullptr;
   float* g_lo = nullptr;
@@ -272,6 +273,10 @@ double rp_bytes(const Mat& A) { return A.uniform_len > 0 ? 0.0 : (A.idx64 ? 8.0 
 double policy_len(const Mat& A) {
   return A.uniform_len > 0 ? A.uniform_len : static_cast<double>(A.nnz) / A.rows;
 }
+// Row-pointer bytes and entries per policy row as the policy-row kernels read
+// them (the action-major copy has uniform rows of am_len entries).
+double prp_bytes(const Mat& A) { return A.am_len > 0 ? 0.0 : rp_bytes(A); }
+double ppolicy_len(const Mat& A) { return A.am_len > 0 ? A.am_len : policy_len(A); }
 double bytes_bellman(const Mat& A, bool ff, bool v_out) {
   const double n = A.n, rows = A.rows, nnz = A.nnz;
   const double vb = ff ? 8.0 : 4.0;
@@ -280,14 +285,15 @@ double bytes_bellman(const Mat& A, bool ff, bool v_out) {
 }
 double bytes_policy_resid(const Mat& A) {
   const double n = A.n;
-  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (8.0 + (A.val_lo ? 4.0 : 0.0)) + 4.0 +
+  return n * (4.0 + 2.0 * prp_bytes(A) +
+              ppolicy_len(A) * (8.0 + (A.val_lo && !A.am_len ? 4.0 : 0.0)) + 4.0 +
               (A.g_lo ? 4.0 : 0.0) + 8.0 + 4.0);
 }
 double bytes_spmv(const Mat& A, bool lp) {
   const double n = A.n;
   const double per_entry = lp ? (A.lpk ? 4.0 : 6.0) : 8.0;
   const double row_scale = (lp && !A.lpk) ? 4.0 : 0.0;  // the packed copy renormalises on the fly
-  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * per_entry + row_scale + 4.0 + 4.0);
+  return n * (4.0 + 2.0 * prp_bytes(A) + ppolicy_len(A) * per_entry + row_scale + 4.0 + 4.0);
 }
 double bytes_dots(const Mat& A, int j) { return 4.0 * A.n * (j + 2); }
 double bytes_ortho(const Mat& A, int j, int cgs2) {
@@ -298,12 +304,12 @@ double bytes_ortho(const Mat& A, int j, int cgs2) {
 double bytes_update(const Mat& A, int J) { return 4.0 * J * A.n + 16.0 * A.n; }
 double bytes_richardson(const Mat& A, bool lp) {
   const double n = A.n;
-  return n * (4.0 + 2.0 * rp_bytes(A) + policy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
+  return n * (4.0 + 2.0 * prp_bytes(A) + ppolicy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
               (lp ? 4.0 : 0.0) + 12.0);
 }
 
 void free_all(mdp_s* h) {
-  void* ptrs[] = {h->rp, h->pk, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
+  void* ptrs[] = {h->rp, h->pk, h->pk_am, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
                   h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
   cudaStream_t fs = free_stream(h->device);
   if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
@@ -680,6 +686,8 @@ size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, md
   b += static_cast<size_t>(nnz) * (4 + 4 + (val_t == MDP_F64 ? 4 : 0));
   b += static_cast<size_t>(rows) * 4 * 2;  // g (+ g_lo bound)
   if (store_t == MDP_BF16 || store_t == MDP_F16) b += static_cast<size_t>(nnz) * 2 + rows * 4;
+  // action-major policy copy of short rows: at most 1.25 nnz padded entries
+  if (nnz < 12 * rows) b += static_cast<size_t>(nnz + nnz / 4 + 4) * 8;
   b += static_cast<size_t>(n) * (8 * 3 + 4);
   b += static_cast<size_t>(restart + 1) * ld * 4;
   b += sizeof(DevState) + (1 << 20);
@@ -866,12 +874,32 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
 
   h->store_t = store_t;
   A.store_t = store_t;
-  if (store_t == MDP_BF16 || store_t == MDP_F16) {
+  const bool lp_store = store_t == MDP_BF16 || store_t == MDP_F16;
+  // Short rows (one thread per row, no aligned 16-byte slices) read by the
+  // policy-row kernels come from an action-major copy padded to the longest
+  // row, when padding costs at most a quarter more entries: states that share
+  // an action then read adjacent rows instead of one short row per 128-byte
+  // line.  Not for FP64 probabilities (the copy has no low parts) nor for a
+  // 16-bit copy that cannot be packed.
+  const int64_t am_entries = rows * static_cast<int64_t>(fl.max_len);
+  if (A.vw == 1 && !A.vec4 && fl.max_len > 0 && fl.max_len <= 16 && !h->val_lo &&
+      am_entries <= nnz + nnz / 4 && (!lp_store || h->band < 32768) &&
+      !getenv("MDP_NO_POLICY_COPY")) {
+    const int64_t am_padded = (am_entries + 3) & ~int64_t(3);
+    CALLOC(h->pk_am, static_cast<size_t>(am_padded) * 8);
+    CCK(cudaMemsetAsync(h->pk_am, 0, static_cast<size_t>(am_padded) * 8, s));
+    CCK(launch_build_am(A, h->pk_am, fl.max_len, s));
+    A.pk_am = h->pk_am;
+    A.am_len = fl.max_len;
+  }
+  if (lp_store) {
     CALLOC(h->row_scale, static_cast<size_t>(rows) * 4);
     if (h->band < 32768 && !getenv("MDP_NO_LP_PACK")) {
       // 16-byte groups of int16 column offsets and 16-bit values
-      CALLOC(h->lpk, static_cast<size_t>(padded) * 4);
-      CCK(cudaMemsetAsync(h->lpk, 0, static_cast<size_t>(padded) * 4, s));
+      const int64_t lp_padded =
+          A.am_len > 0 ? ((rows * static_cast<int64_t>(A.am_len) + 3) & ~int64_t(3)) : padded;
+      CALLOC(h->lpk, static_cast<size_t>(lp_padded) * 4);
+      CCK(cudaMemsetAsync(h->lpk, 0, static_cast<size_t>(lp_padded) * 4, s));
       CCK(launch_prep_lowp_packed(A, h->lpk, h->row_scale, store_t, s));
       A.lpk = h->lpk;
     } else {

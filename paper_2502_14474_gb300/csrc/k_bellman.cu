@@ -259,8 +259,9 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t s = tile * NV + vec;
     int64_t b = 0, e = 0, r = 0;
     if (s < P.n) {
-      r = s * P.m + __ldg(pi + s);
-      row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+      const int32_t a = __ldg(pi + s);
+      r = s * P.m + a;  // cost row
+      row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, a), b, e);
     }
     float hi, lo;
     row_dot_ff<VW>(P.col, P.val, P.val_lo, V, b, e, lane, vec4, hi, lo);
@@ -485,6 +486,7 @@ static Csr<IdxT> make_csr(const Mat& A) {
   P.m = A.m;
   P.vec4 = A.vec4;
   P.uniform_len = A.uniform_len;
+  P.am = 0;
   P.gamma = static_cast<float>(A.gamma);
   P.gamma_hi = static_cast<float>(A.gamma);
   P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma_hi));
@@ -617,6 +619,7 @@ static cudaError_t presid_vw(const Mat& A, const int32_t* pi, const float2* V, f
   const int64_t n_tiles = (A.n + NV - 1) / NV;
   const Grid G = make_grid(n_tiles, A.num_sms * occ, NV);
   Csr<IdxT> P = make_csr<IdxT>(A);
+  use_policy_copy(P, A);
   kern<<<static_cast<unsigned>(n_blocks(G)), kThreads, 0, s>>>(P, G, pi, V, r, partials, st);
   return cudaGetLastError();
 }

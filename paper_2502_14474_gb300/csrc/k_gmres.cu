@@ -281,8 +281,9 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t s = tile * NV + vec;
     int64_t b = 0, e = 0, row = 0;
     if (s < P.n) {
-      row = s * P.m + __ldg(pi + s);
-      row_bounds<IdxT>(P.rp, P.uniform_len, row, b, e);
+      const int32_t a = __ldg(pi + s);
+      row = s * P.m + a;  // row of the 16-bit scale (the unpacked copy has no action-major form)
+      row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, a), b, e);
     }
     float d, den = 0.f;
     bool packed = false;
@@ -377,6 +378,7 @@ static Csr<IdxT> csr_of(const Mat& A) {
   P.gamma = static_cast<float>(A.gamma);
   P.gamma_hi = P.gamma;
   P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma));
+  use_policy_copy(P, A);
   return P;
 }
 

@@ -152,14 +152,15 @@ __global__ void k_prep_lowp(int64_t rows, const IdxT* __restrict__ rp, int32_t u
 // slot i%4: int16 (col - s) in the first 8 bytes, the rounded value in the
 // last 8; row_scale[r] = 1 / sum of the rounded row.
 template <typename IdxT, typename Q>
-__global__ void k_prep_lowp_packed(int64_t rows, int32_t m, const IdxT* __restrict__ rp,
-                                   int32_t uniform_len, const float* __restrict__ pk,
-                                   uint16_t* __restrict__ lpk, float* __restrict__ scale) {
+__global__ void k_prep_lowp_packed(int64_t rows, int32_t m, int64_t n, int am,
+                                   const IdxT* __restrict__ rp, int32_t uniform_len,
+                                   const float* __restrict__ pk, uint16_t* __restrict__ lpk,
+                                   float* __restrict__ scale) {
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t b = uniform_len > 0 ? r * uniform_len : static_cast<int64_t>(rp[r]);
     const int64_t e = uniform_len > 0 ? b + uniform_len : static_cast<int64_t>(rp[r + 1]);
-    const int64_t st = r / m;
+    const int64_t st = am ? r % n : r / m;  // the state whose transitions row r holds
     double sum = 0.0;
     for (int64_t i = b; i < e; ++i) {
       const int64_t slot = ((i >> 2) << 3) + (i & 3);
@@ -234,23 +235,71 @@ namespace mdpk {
 cudaError_t launch_prep_lowp_packed(const Mat& A, uint4* lpk, float* row_scale, int store_t,
                                     cudaStream_t s) {
   const unsigned nb = grid_of(A.rows, A.num_sms);
-  const float* pk = A.val;
+  // from the action-major policy copy when there is one (the 16-bit copy is read
+  // only by the policy-row kernels), else from the packed CSR
+  const int am = A.am_len > 0 ? 1 : 0;
+  const float* pk = am ? reinterpret_cast<const float*>(A.pk_am) : A.val;
+  const int32_t ul = am ? A.am_len : A.uniform_len;
   uint16_t* out = reinterpret_cast<uint16_t*>(lpk);
   if (store_t == 3) {
     if (A.idx64)
       k_prep_lowp_packed<int64_t, __half><<<nb, 256, 0, s>>>(
-          A.rows, A.m, static_cast<const int64_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+          A.rows, A.m, A.n, am, static_cast<const int64_t*>(A.rp), ul, pk, out, row_scale);
     else
       k_prep_lowp_packed<int32_t, __half><<<nb, 256, 0, s>>>(
-          A.rows, A.m, static_cast<const int32_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+          A.rows, A.m, A.n, am, static_cast<const int32_t*>(A.rp), ul, pk, out, row_scale);
   } else {
     if (A.idx64)
       k_prep_lowp_packed<int64_t, __nv_bfloat16><<<nb, 256, 0, s>>>(
-          A.rows, A.m, static_cast<const int64_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+          A.rows, A.m, A.n, am, static_cast<const int64_t*>(A.rp), ul, pk, out, row_scale);
     else
       k_prep_lowp_packed<int32_t, __nv_bfloat16><<<nb, 256, 0, s>>>(
-          A.rows, A.m, static_cast<const int32_t*>(A.rp), A.uniform_len, pk, out, row_scale);
+          A.rows, A.m, A.n, am, static_cast<const int32_t*>(A.rp), ul, pk, out, row_scale);
   }
+  return cudaGetLastError();
+}
+
+// Action-major policy copy: original row r = s*m + a goes to row a*n + s of
+// length L; its entries keep their order, and the row is padded with
+// zero-probability entries pointing at s (they add exact zeros to every sum).
+// The packed format is the CSR's: entry i sits at word ((i >> 2) << 3) + (i & 3)
+// (column) and the same + 4 (value).
+template <typename IdxT>
+__global__ void k_build_am(int64_t rows, int32_t m, int64_t n, const IdxT* __restrict__ rp,
+                           int32_t uniform_len, const uint32_t* __restrict__ pk, int32_t L,
+                           uint32_t* __restrict__ pk_am) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t b = uniform_len > 0 ? r * uniform_len : static_cast<int64_t>(rp[r]);
+    const int64_t e = uniform_len > 0 ? b + uniform_len : static_cast<int64_t>(rp[r + 1]);
+    const int64_t st = r / m;
+    const int64_t a = r - st * m;
+    const int64_t base = (a * n + st) * L;
+    for (int64_t k = 0; k < L; ++k) {
+      const int64_t o = base + k;
+      const int64_t wo = ((o >> 2) << 3) + (o & 3);
+      if (b + k < e) {
+        const int64_t i = b + k;
+        const int64_t wi = ((i >> 2) << 3) + (i & 3);
+        pk_am[wo] = pk[wi];
+        pk_am[wo + 4] = pk[wi + 4];
+      } else {
+        pk_am[wo] = static_cast<uint32_t>(st);
+        pk_am[wo + 4] = 0u;  // +0.0f
+      }
+    }
+  }
+}
+
+cudaError_t launch_build_am(const Mat& A, uint32_t* pk_am, int32_t L, cudaStream_t s) {
+  const unsigned nb = grid_of(A.rows, A.num_sms);
+  const uint32_t* pk = reinterpret_cast<const uint32_t*>(A.val);
+  if (A.idx64)
+    k_build_am<int64_t><<<nb, 256, 0, s>>>(A.rows, A.m, A.n, static_cast<const int64_t*>(A.rp),
+                                           A.uniform_len, pk, L, pk_am);
+  else
+    k_build_am<int32_t><<<nb, 256, 0, s>>>(A.rows, A.m, A.n, static_cast<const int32_t*>(A.rp),
+                                           A.uniform_len, pk, L, pk_am);
   return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             for (int p = 0; p < 4; ++p) {
               const int64_t s = s0 + p * NT + threadIdx.x;
               const bool valid = s < s_lim;
-              const int64_t r = s * P.m + act[p];
+              const int64_t r = policy_row(P, s, act[p]);
               const int64_t rb = r * P.uniform_len;
               int64_t b[VW];
               bool vd[VW];
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
                 b2[u] = 0;
                 e2[u] = 0;
                 if (s2[u] < s_lim)
-                  row_bounds<IdxT>(P.rp, P.uniform_len, s2[u] * P.m + act[p + u], b2[u], e2[u]);
+                  row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s2[u], act[p + u]), b2[u],
+                                   e2[u]);
                 const int64_t g0 = b2[u] >> 2;
                 G0[u] = (g0 << 2) < e2[u] ? __ldcs(P.lpk + g0) : make_uint4(0, 0, 0, 0);
                 G1[u] = ((g0 + 1) << 2) < e2[u] ? __ldcs(P.lpk + g0 + 1) : make_uint4(0, 0, 0, 0);
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             const int64_t s = s0 + base + vec;
             int64_t b = 0, e = 0, r = 0;
             if (s < s_lim) {
-              r = s * P.m + __ldg(pi + s);
+              r = policy_row(P, s, __ldg(pi + s));
               row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
             }
             float num = 0.f, den = 0.f;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             for (int u = 0; u < 2; ++u) {
               s2[u] = s0 + (p + u) * NT + threadIdx.x;
               int64_t b = 0, e = 0;
-              r2[u] = s2[u] * P.m + act[p + u];
+              r2[u] = policy_row(P, s2[u], act[p + u]);
               if (s2[u] < s_lim) row_bounds<IdxT>(P.rp, P.uniform_len, r2[u], b, e);
               row_pre<PV>(P.col, val, b, e, R[u]);
             }
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             const int64_t s = s0 + base + vec;
             int64_t b = 0, e = 0, r = 0;
             if (s < s_lim) {
-              r = s * P.m + __ldg(pi + s);
+              r = policy_row(P, s, __ldg(pi + s));
               row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
             }
             float d = row_dot_f32<VW, PV>(P.col, val, gx, b, e, lane, vec4);
@@ -251,6 +252,7 @@ inline Csr<IdxT> csr_view(const Mat& A) {
   P.gamma = static_cast<float>(A.gamma);
   P.gamma_hi = P.gamma;
   P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma));
+  use_policy_copy(P, A);
   return P;
 }
 

@@ -20,7 +20,15 @@ struct Mat {
   const float* g = nullptr;
   const float* g_lo = nullptr;
   const void* val16 = nullptr;
-  const uint4* lpk = nullptr;  // [4 x int16 col - s | 4 x 16-bit value] groups (band < 2^15)
+  const uint4* lpk = nullptr;  // [4 x int16 col - s | 4 x 16-bit value] groups (band < 2^15);
+                               // in the action-major row order when am_len > 0
+  // Action-major policy copy for short rows: row (s, a) at a*n + s, every row
+  // padded to am_len entries with zero probabilities (column s) at its end, in
+  // the packed 32-byte group format.  Read by the policy-row kernels (SpMV,
+  // policy residual, Richardson): states that share an action read adjacent
+  // rows.  am_len == 0: no copy.
+  const uint32_t* pk_am = nullptr;
+  int32_t am_len = 0;
   const float* row_scale = nullptr;
   int32_t store_t = 0;      // MDP_F32 / MDP_BF16 / MDP_F16 of val16
   int32_t uniform_len = 0;
@@ -98,6 +106,24 @@ struct PrepFlags {
   unsigned long long band; // max |col - s|
   double max_sum_err;
 };
+
+// Point a policy-row kernel's view at the action-major copy, when there is one.
+template <typename CsrT>
+inline void use_policy_copy(CsrT& P, const Mat& A) {
+  P.am = 0;
+  if (A.am_len > 0) {
+    P.col = reinterpret_cast<const int32_t*>(A.pk_am);
+    P.val = reinterpret_cast<const float*>(A.pk_am);
+    P.val_lo = nullptr;
+    P.uniform_len = A.am_len;
+    P.vec4 = 0;
+    P.am = 1;
+  }
+}
+
+// Build the action-major policy copy (rows padded to L entries) from the
+// packed CSR of A.
+cudaError_t launch_build_am(const Mat& A, uint32_t* pk_am, int32_t L, cudaStream_t s);
 
 cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const int32_t* col_in,
                              const void* val_in, int val_f64, const void* g_in, int g_f64,

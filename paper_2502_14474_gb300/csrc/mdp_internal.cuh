@@ -271,9 +271,17 @@ struct Csr {
   int32_t m;
   int32_t vec4;           // 1: 16-byte vector loads of col/val (rows long enough)
   int32_t uniform_len;    // > 0: every row has this many entries (rp unused)
+  int32_t am;             // 1: policy rows action-major, row (s, a) at a*n + s
   float gamma;            // FP32 gamma
   float gamma_hi, gamma_lo;  // float-float gamma
 };
+
+// Row of P holding the transitions of state s under action a: s*m + a in the
+// CSR as given, a*n + s in the action-major policy copy.
+template <typename IdxT>
+__device__ __forceinline__ int64_t policy_row(const Csr<IdxT>& P, int64_t s, int32_t a) {
+  return P.am ? static_cast<int64_t>(a) * P.n + s : s * P.m + a;
+}
 
 struct Grid {
   int64_t n_tiles;
