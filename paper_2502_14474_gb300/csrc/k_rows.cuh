@@ -483,6 +483,24 @@ __device__ __forceinline__ void lp_group_dot(uint4 G, int64_t i0, int64_t b, int
   }
 }
 
+// The same over the entries q of group G with lo <= q < hi (positions
+// relative to the group's first entry; 32-bit bounds for short rows).
+template <typename Q, typename GX>
+__device__ __forceinline__ void lp_group_dot_rel(uint4 G, int32_t lo, int32_t hi, int64_t s, GX x,
+                                                 float& num, float& den) {
+  const uint32_t dw[2] = {G.x, G.y};
+  const uint32_t qw[2] = {G.z, G.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q >= lo && q < hi) {
+      const int32_t c = static_cast<int32_t>(s) + lp_off(dw[q >> 1], q & 1);
+      const float v = Q16<Q>::f(q & 1 ? (qw[q >> 1] >> 16) : (qw[q >> 1] & 0xffffu));
+      num = fmaf(v, x(c), num);
+      den += v;
+    }
+  }
+}
+
 // Lane `lane` of VW takes groups g0 + lane, g0 + lane + VW, ... of row [b, e)
 // of state s; the caller reduces num and den over the VW lanes.
 template <int VW, typename Q, typename GX>

@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             }
           }
         } else if (VW == 1 && sizeof(PV) == 2 && P.lpk) {
-          // packed 16-bit copy, short rows: two states per thread with the
-          // actions, row pointers and first two groups of both rows in flight
-          // together (a row of up to 5 entries never spans more than two groups)
+          // packed 16-bit copy, short rows: the four states of a thread have
+          // their actions, then the first two groups of all four rows, in
+          // flight together (a row of up to 5 entries spans at most two groups;
+          // longer rows load the rest on the way)
           if constexpr (VW == 1 && sizeof(PV) == 2) {
             int32_t act[4];
 #pragma unroll
@@ -124,34 +125,35 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
               const int64_t s = s0 + p * NT + threadIdx.x;
               act[p] = s < s_lim ? __ldg(pi + s) : 0;
             }
+            int32_t oe[4];  // (row start & 3) | (row end - row start) << 2
+            uint4 G0[4], G1[4];
 #pragma unroll
-            for (int p = 0; p < 4; p += 2) {
-              int64_t s2[2], b2[2], e2[2];
-              uint4 G0[2], G1[2];
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              int64_t b = 0, e = 0;
+              if (s < s_lim) row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p]), b, e);
+              const int32_t o = static_cast<int32_t>(b & 3), len = static_cast<int32_t>(e - b);
+              oe[p] = o | (len << 2);
+              G0[p] = len > 0 ? __ldcs(P.lpk + (b >> 2)) : make_uint4(0, 0, 0, 0);
+              G1[p] = o + len > 4 ? __ldcs(P.lpk + (b >> 2) + 1) : make_uint4(0, 0, 0, 0);
+            }
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                s2[u] = s0 + (p + u) * NT + threadIdx.x;
-                b2[u] = 0;
-                e2[u] = 0;
-                if (s2[u] < s_lim)
-                  row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s2[u], act[p + u]), b2[u],
-                                   e2[u]);
-                const int64_t g0 = b2[u] >> 2;
-                G0[u] = (g0 << 2) < e2[u] ? __ldcs(P.lpk + g0) : make_uint4(0, 0, 0, 0);
-                G1[u] = ((g0 + 1) << 2) < e2[u] ? __ldcs(P.lpk + g0 + 1) : make_uint4(0, 0, 0, 0);
-              }
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                if (s2[u] < s_lim) {
-                  const int64_t g0 = b2[u] >> 2;
-                  float num = 0.f, den = 0.f;
-                  lp_group_dot<PV>(G0[u], g0 << 2, b2[u], e2[u], s2[u], gx, num, den);
-                  lp_group_dot<PV>(G1[u], (g0 + 1) << 2, b2[u], e2[u], s2[u], gx, num, den);
-                  for (int64_t g = g0 + 2; (g << 2) < e2[u]; ++g)
-                    lp_group_dot<PV>(__ldcs(P.lpk + g), g << 2, b2[u], e2[u], s2[u], gx, num, den);
-                  const float d = den > 0.f ? num / den : 0.f;
-                  uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              if (s < s_lim) {
+                const int32_t o = oe[p] & 3, len = oe[p] >> 2;
+                float num = 0.f, den = 0.f;
+                lp_group_dot_rel<PV>(G0[p], o, o + len, s, gx, num, den);
+                lp_group_dot_rel<PV>(G1[p], o - 4, o + len - 4, s, gx, num, den);
+                if (o + len > 8) {  // rows longer than two groups: the rest on the way
+                  int64_t b = 0, e = 0;
+                  row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p]), b, e);
+                  for (int32_t k = 8; k < o + len; k += 4)
+                    lp_group_dot_rel<PV>(__ldcs(P.lpk + (b >> 2) + (k >> 2)), o - k, o + len - k,
+                                         s, gx, num, den);
                 }
+                const float d = den > 0.f ? __fdividef(num, den) : 0.f;
+                uw[s] = sj * fmaf(-P.gamma, d, xs(s));
               }
             }
           }
