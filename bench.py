@@ -329,8 +329,9 @@ def run_serve(args):
         reqs.append(serve.Request(rid=i, mdp=mdp, arrival=float(a)))
     srv = serve.Server(budget_bytes=args.budget_gb * 1e9, workers=args.streams,
                        solve_opts={"max_inner": args.max_inner}).start()
-    # warm the library and the kernels on a few requests outside the trace
-    warm = [serve.Request(rid=-1 - i, mdp=pool[i]) for i in range(4)]
+    # warm the library, the kernels of both request classes and the memory pool
+    # on a few requests outside the trace (a server warms up before it takes traffic)
+    warm = [serve.Request(rid=-1 - i, mdp=m) for i, m in enumerate(pool[:4] + large)]
     for r in warm:
         srv.submit(r)
     with srv.cv:
