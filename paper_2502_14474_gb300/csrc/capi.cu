@@ -883,7 +883,8 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   // 16-bit copy that cannot be packed.
   const int64_t am_entries = rows * static_cast<int64_t>(fl.max_len);
   if (A.vw == 1 && !A.vec4 && fl.max_len > 0 && fl.max_len <= 16 && !h->val_lo &&
-      am_entries <= nnz + nnz / 4 && (!lp_store || h->band < 32768) &&
+      am_entries <= nnz + nnz / 4 &&
+      (!lp_store || (h->band < 32768 && !getenv("MDP_NO_LP_PACK"))) &&
       !getenv("MDP_NO_POLICY_COPY")) {
     const int64_t am_padded = (am_entries + 3) & ~int64_t(3);
     CALLOC(h->pk_am, static_cast<size_t>(am_padded) * 8);

@@ -28,7 +28,7 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
 }
 
 template <typename IdxT, int VW, typename PV, int NT, bool WIN>
-__global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
+__global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
     k_arnoldi_spmv(Csr<IdxT> P, int64_t states_per_block, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
                    DevState* __restrict__ st) {
@@ -59,20 +59,31 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
   // policy rows before any gather, then a reduce-scatter gives each lane the
   // row sum of its own state
   const bool fast = VW <= 4 && P.uniform_len == 4 * VW && vec4;
+  // The branches that take a thread's four states s0 + p*NT + t at once (the
+  // fast path and the one-thread-per-row branches) read their actions one tile
+  // ahead: the action load is then off the tile's dependent chain (action,
+  // row, gather).
+  const bool ahead = fast || VW == 1;
+  int32_t act_nx[4] = {0, 0, 0, 0};
+  auto load_act = [&](int64_t t0, int32_t(&a)[4]) {
+    const int64_t lim = min(s_end, t0 + TS);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int64_t s = t0 + p * NT + threadIdx.x;
+      a[p] = s < lim ? __ldg(pi + s) : 0;
+    }
+  };
+  if (ahead && s_begin < s_end) load_act(s_begin, act_nx);
   for (int64_t s0 = s_begin; s0 < s_end; s0 += TS) {
     const int64_t s_lim = min(s_end, s0 + TS);  // states of this tile: [s0, s_lim)
+    int32_t act[4] = {act_nx[0], act_nx[1], act_nx[2], act_nx[3]};
+    if (ahead && s0 + TS < s_end) load_act(s0 + TS, act_nx);
     {
       if (WIN && s0 + TS < s_end)  // next tile's leading edge; disjoint from live slots
         ring_fill_f32<NT>(ring, mask, uj, s0 + TS + band, min(P.n, s0 + 2 * TS + band));
       auto phase_a = [&](auto gx, auto xs) {
         if (fast) {
           if constexpr (VW <= 4) {
-            int32_t act[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int64_t s = s0 + p * NT + threadIdx.x;
-              act[p] = s < s_lim ? __ldg(pi + s) : 0;
-            }
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
               const int64_t s = s0 + p * NT + threadIdx.x;
@@ -119,12 +130,6 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
           // flight together (a row of up to 5 entries spans at most two groups;
           // longer rows load the rest on the way)
           if constexpr (VW == 1 && sizeof(PV) == 2) {
-            int32_t act[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int64_t s = s0 + p * NT + threadIdx.x;
-              act[p] = s < s_lim ? __ldg(pi + s) : 0;
-            }
             int32_t oe[4];  // (row start & 3) | (row end - row start) << 2
             uint4 G0[4], G1[4];
 #pragma unroll
@@ -176,32 +181,28 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? (VW == 1 ? 2 : 3) : 1))
             }
           }
         } else if (VW == 1) {
-          // short rows: two states per thread with the actions, row pointers and
-          // first two packed groups of both rows in flight together
-          int32_t act[4];
+          if constexpr (VW == 1) {
+            // short rows: two states per thread with the actions, row pointers and
+            // first two packed groups of both rows in flight together
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int64_t s = s0 + p * NT + threadIdx.x;
-            act[p] = s < s_lim ? __ldg(pi + s) : 0;
-          }
+            for (int p = 0; p < 4; p += 2) {
+              int64_t s2[2], r2[2];
+              RowPre<PV> R[2];
 #pragma unroll
-          for (int p = 0; p < 4; p += 2) {
-            int64_t s2[2], r2[2];
-            RowPre<PV> R[2];
+              for (int u = 0; u < 2; ++u) {
+                s2[u] = s0 + (p + u) * NT + threadIdx.x;
+                int64_t b = 0, e = 0;
+                r2[u] = policy_row(P, s2[u], act[p + u]);
+                if (s2[u] < s_lim) row_bounds<IdxT>(P.rp, P.uniform_len, r2[u], b, e);
+                row_pre<PV>(P.col, val, b, e, R[u]);
+              }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              s2[u] = s0 + (p + u) * NT + threadIdx.x;
-              int64_t b = 0, e = 0;
-              r2[u] = policy_row(P, s2[u], act[p + u]);
-              if (s2[u] < s_lim) row_bounds<IdxT>(P.rp, P.uniform_len, r2[u], b, e);
-              row_pre<PV>(P.col, val, b, e, R[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              if (s2[u] < s_lim) {
-                float d = row_pre_dot<PV>(P.col, val, gx, R[u]);
-                if (lp) d *= __ldcs(P.row_scale + r2[u]);
-                uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+              for (int u = 0; u < 2; ++u) {
+                if (s2[u] < s_lim) {
+                  float d = row_pre_dot<PV>(P.col, val, gx, R[u]);
+                  if (lp) d *= __ldcs(P.row_scale + r2[u]);
+                  uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+                }
               }
             }
           }
