@@ -76,8 +76,18 @@ __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int
     if (lr[u] < rows_here) row_bounds<IdxT>(P.rp, P.uniform_len, r0 + lr[u], b[u], e[u]);
   if constexpr (FF) {
     float hi[2], lo[2];
+    if (!P.val_lo) {
+      // both rows' first two packed groups in flight before any gather
+      RowPre<float> R[2];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) row_dot_ff_g1(P.col, P.val, P.val_lo, gx, b[u], e[u], hi[u], lo[u]);
+      for (int u = 0; u < 2; ++u) row_pre<float>(P.col, P.val, b[u], e[u], R[u]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) row_pre_dot_ff(P.col, P.val, gx, R[u], hi[u], lo[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        row_dot_ff_g1(P.col, P.val, P.val_lo, gx, b[u], e[u], hi[u], lo[u]);
+    }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (lr[u] < rows_here) {
@@ -267,6 +277,72 @@ __global__ void __launch_bounds__(kThreads)
     row_dot_ff<VW>(P.col, P.val, P.val_lo, V, b, e, lane, vec4, hi, lo);
     group_sum_ff<VW>(hi, lo);
     if (lane == 0 && s < P.n) {
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+      const float2 v = V[s];
+      const float rr = ff_diff_to_float(q.hi, q.lo, v.x, v.y);
+      r_out[s] = rr;
+      const double rd = static_cast<double>(rr);
+      my_max = fmax(my_max, fabs(rd));
+      my_sq += rd * rd;
+    }
+  }
+  const double bmax = block_max_d(my_max, red);
+  const double bsq = block_sum_d(my_sq, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bmax;
+    partials[2 * blockIdx.x + 1] = bsq;
+  }
+  if (last_block(&st->counter[kCntPolicy])) {
+    double mx = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += kThreads) {
+      mx = fmax(mx, __ldcg(partials + 2 * i));
+      sq += __ldcg(partials + 2 * i + 1);
+    }
+    mx = block_max_d(mx, red);
+    sq = block_sum_d(sq, red);
+    if (threadIdx.x == 0) {
+      st->res_inf = mx;
+      st->res_2 = sqrt(sq);
+      st->counter[kCntPolicy] = 0;
+      gmres_begin(st, sqrt(sq));
+    }
+  }
+}
+
+// Fast form for rows of exactly 4*VW entries with 16-byte aligned starts (the
+// layout of the policy SpMV's fast path): a thread per state, a vector of VW
+// lanes owns VW consecutive states and each lane loads its 16-byte slice of
+// all VW policy rows before any gather; a reduce-scatter leaves every lane
+// with its own state's float-float row sum.
+template <typename IdxT, int VW>
+__global__ void __launch_bounds__(kThreads)
+    k_policy_residual_fast(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi,
+                           const float2* __restrict__ V, float* __restrict__ r_out,
+                           double* __restrict__ partials, DevState* __restrict__ st) {
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x % VW;
+  double my_max = 0.0, my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * kThreads + threadIdx.x;
+    const bool valid = s < P.n;
+    const int32_t a = valid ? __ldg(pi + s) : 0;
+    const int64_t rb = policy_row(P, s, a) * P.uniform_len;
+    int64_t b[VW];
+    bool vd[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+      b[u] = __shfl_sync(0xffffffffu, rb, u, VW);
+      vd[u] = __shfl_sync(0xffffffffu, valid ? 1 : 0, u, VW) != 0;
+    }
+    float ph[VW], pl[VW], hi, lo;
+    vec_rows_ff<VW>(P.col, P.val, GatherFF{V}, b, vd, lane, ph, pl);
+    reduce_scatter_ff<VW>(ph, pl, lane, hi, lo);
+    if (valid) {
+      const int64_t r = s * P.m + a;  // cost row
       const ff sum = ff_norm(hi, lo);
       const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
       const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
@@ -613,6 +689,16 @@ cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, in
 template <typename IdxT, int VW>
 static cudaError_t presid_vw(const Mat& A, const int32_t* pi, const float2* V, float* r,
                              double* partials, DevState* st, cudaStream_t s) {
+  if constexpr (VW <= 4) {
+    if (A.uniform_len == 4 * VW && A.vec4 && !A.val_lo && A.am_len == 0) {
+      auto kern = k_policy_residual_fast<IdxT, VW>;
+      static int occ = occupancy(kern, 0);
+      const Grid G = make_grid((A.n + kThreads - 1) / kThreads, A.num_sms * occ, kThreads);
+      Csr<IdxT> P = make_csr<IdxT>(A);
+      kern<<<static_cast<unsigned>(n_blocks(G)), kThreads, 0, s>>>(P, G, pi, V, r, partials, st);
+      return cudaGetLastError();
+    }
+  }
   auto kern = k_policy_residual<IdxT, VW>;
   static int occ = occupancy(kern, 0);
   constexpr int NV = kThreads / VW;

@@ -186,6 +186,43 @@ __device__ __forceinline__ float row_pre_dot(const int32_t* __restrict__ col,
   return acc;
 }
 
+// Float-float form of row_pre_dot over rows prefetched by row_pre (FP32
+// values, no FP64 low parts): the same entries in the same order as
+// row_dot_ff_g1, so the sums are bitwise those of row_dot_ff_g1.
+template <typename GX>
+__device__ __forceinline__ void row_pre_dot_ff(const int32_t* __restrict__ col,
+                                               const float* __restrict__ val, GX V,
+                                               const RowPre<float>& R, float& hi, float& lo) {
+  hi = 0.f;
+  lo = 0.f;
+  const int64_t b = R.b, e = R.e;
+  const int64_t i0 = (b >> 2) << 2;
+  const int cc[8] = {R.c0.x, R.c0.y, R.c0.z, R.c0.w, R.c1.x, R.c1.y, R.c1.z, R.c1.w};
+  const float pp[8] = {R.v0.x, R.v0.y, R.v0.z, R.v0.w, R.v1.x, R.v1.y, R.v1.z, R.v1.w};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= b && i < e) {
+      const float2 v = V(cc[q]);
+      ff_acc(hi, lo, pp[q], v.x, v.y);
+    }
+  }
+  for (int64_t g = (i0 >> 2) + 2; (g << 2) < e; ++g) {
+    const int64_t j0 = g << 2;
+    const int4 c = ldcol4(col, j0);
+    const float4 p = Ld<float>::four(val, j0);
+    const int cq[4] = {c.x, c.y, c.z, c.w};
+    const float pq[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (j0 + q < e) {
+        const float2 v = V(cq[q]);
+        ff_acc(hi, lo, pq[q], v.x, v.y);
+      }
+    }
+  }
+}
+
 template <typename GX>
 __device__ __forceinline__ void row_dot_ff_g1(const int32_t* __restrict__ col,
                                               const float* __restrict__ val,
