@@ -189,6 +189,33 @@ def _traffic_record(kernel, n):
 WORKLOAD = "banded4m"
 
 
+def _bellman_latency(h, host, stream, dev, reps=50):
+    """p50/p99 over `reps` single FP32 Bellman backups (K1) through mdp_bellman, with
+    CUDA events on the solve stream around each call, and the achieved GB/s of the
+    median against K1's algorithmic bytes (nnz*(4 col + 4 val) + rows*4 g (+ row
+    pointers when rows differ in length) + n*(4 V + 4 V' + 4 pi))."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    V = torch.rand(host.n, dtype=torch.float32, device=dev, generator=gen) * 50.0
+    lens = np.diff(host.row_ptr)
+    rp_bytes = 0 if lens.min() == lens.max() else (len(host.row_ptr)) * 4
+    nbytes = host.nnz * 8 + host.n * host.m * 4 + rp_bytes + host.n * 12
+    ms = []
+    with torch.cuda.stream(stream):
+        for i in range(reps + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.bellman(V, want_v=True, want_pi=True, want_r=False)
+            b.record(stream)
+            b.synchronize()
+            if i >= 3:
+                ms.append(a.elapsed_time(b))
+    p50, p99 = float(np.percentile(ms, 50)), float(np.percentile(ms, 99))
+    return {"kernel": "bellman_f32 (K1)", "reps": reps, "p50_ms": p50, "p99_ms": p99,
+            "bytes": float(nbytes), "GBps_p50": nbytes / (p50 / 1e3) / 1e9}
+
+
 def _workload(n=None, s0=0, s1=None):
     import synth
     if WORKLOAD == "grid4096":
@@ -469,6 +496,9 @@ def main():
                       else None}
                   for k, v in kinds.items() if v["launches"] or v["skipped"]}
 
+    # ---- per-call latency of the FP32 Bellman backup (the K1 kernel) -----------
+    bellman_k1 = None if args.no_profile else _bellman_latency(h, host, stream, dev)
+
     # ---- end to end through the public API with host buffers -------------------
     e2e = None
     if not args.no_e2e:
@@ -537,6 +567,7 @@ def main():
                       "inner_history": st0["inner_history"]},
             "roofline": roofline,
             "kernels": per_kernel,
+            "bellman_k1": bellman_k1,
             "gpu_launches": prof_plain["total_launches"],
             "roofline_region": "second timed pass of the same solves with CUDA events around "
                                "every launch on the solve stream",
