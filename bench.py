@@ -67,6 +67,10 @@ def _args():
     p.add_argument("--store", choices=["f32", "bf16", "f16"], default="f32",
                    help="probabilities of the inner GMRES SpMV")
     p.add_argument("--inner-norm", choices=["2", "inf"], default="2")
+    p.add_argument("--inner", choices=["gmres", "richardson"], default="gmres",
+                   help="inner solver of the evaluation step: GMRES (iPI) or Richardson "
+                        "sweeps (modified policy iteration; with --max-inner 1 it is value "
+                        "iteration)")
     p.add_argument("--max-inner", type=int, default=None,
                    help="cap on GMRES steps per outer iteration (default 10000; 100 for "
                         "grid4096, whose early policies make the evaluation nearly singular)")
@@ -416,7 +420,7 @@ def main():
     solve_stream = torch.cuda.Stream(device=dev)
     h = MDP.from_csr(host, store=args.store, stream=solve_stream)
     opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart, inner_norm=args.inner_norm,
-                max_inner=args.max_inner)
+                max_inner=args.max_inner, inner=args.inner, max_outer=100000)
 
     if args.profile_bellman:
         V = torch.zeros(host.n, dtype=torch.float64, device=dev)
@@ -552,7 +556,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": host.name, "n_states": host.n, "m": host.m, "nnz": nnz,
                        "gamma": host.gamma, "seed": 2 if args.workload == "banded4m" else 3,
-                       "tol": args.tol, "inner": f"gmres({args.restart})", "eta": 0.1,
+                       "tol": args.tol,
+                       "inner": (f"gmres({args.restart})" if args.inner == "gmres"
+                                 else ("value iteration" if args.max_inner == 1
+                                       else "richardson (modified PI)")),
+                       "eta": 0.1,
                        "inner_norm": args.inner_norm, "max_inner": args.max_inner,
                        "inner_probabilities": args.store,
                        "outer_iterate": "float-float (hi+lo FP32)", "l2": "inputs larger than L2",
