@@ -70,7 +70,10 @@ typedef enum {
 } mdp_status;
 
 /* mdp_create flags */
-#define MDP_FLAG_HOST_INPUT 0x1ull   /* row_ptr, col, val, cost are host pointers */
+#define MDP_FLAG_HOST_INPUT 0x1ull   /* row_ptr, col, val, cost are host pointers; in
+                                        page-locked memory they are read in place by the
+                                        packing kernel (no device staging copy), otherwise
+                                        staged on the device first */
 #define MDP_FLAG_NO_VALIDATE 0x2ull  /* skip the stochasticity check (CSR checks stay) */
 #define MDP_FLAG_AUTOTUNE 0x4ull     /* time the candidate lanes-per-row / shared-memory window
                                         schedules of the Bellman kernel at create and keep the

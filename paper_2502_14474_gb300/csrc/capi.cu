@@ -760,7 +760,29 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   };
   const size_t vbytes = static_cast<size_t>(nnz) * (val_t == MDP_F64 ? 8 : 4);
   const size_t gbytes = static_cast<size_t>(rows) * (cost_t == MDP_F64 ? 8 : 4);
-  if (host_in) {
+  // Host inputs in page-locked memory are read by the kernels in place over the
+  // host link (mapped through the unified address space): no staging copy, and
+  // each byte crosses the link once.  Other host memory is staged on the device.
+  auto mapped = [](const void* p) -> const void* {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  bool zero_copy = false;
+  if (host_in && !getenv("MDP_STAGE_HOST_INPUT")) {
+    const void* mp[4] = {mapped(row_ptr), mapped(col), mapped(val), mapped(cost)};
+    if (mp[0] && mp[1] && mp[2] && mp[3]) {
+      zero_copy = true;
+      rp_in = static_cast<const int64_t*>(mp[0]);
+      col_in = static_cast<const int32_t*>(mp[1]);
+      val_in = mp[2];
+      g_in = mp[3];
+    }
+  }
+  if (host_in && !zero_copy) {
     const size_t sz[4] = {static_cast<size_t>(rows + 1) * 8, static_cast<size_t>(nnz) * 4, vbytes,
                           gbytes};
     const void* src[4] = {row_ptr, col, val, cost};
@@ -812,9 +834,19 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   init.min_len = 0x7fffffff;
   CCK(cudaMemcpyAsync(dflags, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   const double tol = (flags & MDP_FLAG_NO_VALIDATE) ? INFINITY : 1e-5;
-  CCK(launch_prep_rows(n, m, rp_in, col_in, val_in, val_t == MDP_F64, g_in, cost_t == MDP_F64,
-                       tol, h->rp, idx64, h->g, h->g_lo, dflags, num_sms, s));
-  CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
+  if (zero_copy) {
+    // pack first (the one pass over the host's col/val), then check the rows
+    // against the packed copy
+    CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
+    CCK(launch_prep_rows(n, m, nnz, rp_in, nullptr, nullptr, val_t == MDP_F64, h->pk, h->val_lo,
+                         g_in, cost_t == MDP_F64, tol, h->rp, idx64, h->g, h->g_lo, dflags,
+                         num_sms, s));
+  } else {
+    CCK(launch_prep_rows(n, m, nnz, rp_in, col_in, val_in, val_t == MDP_F64, nullptr, nullptr,
+                         g_in, cost_t == MDP_F64, tol, h->rp, idx64, h->g, h->g_lo, dflags,
+                         num_sms, s));
+    CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
+  }
   PrepFlags fl;
   CCK(cudaMemcpyAsync(&fl, dflags, sizeof(fl), cudaMemcpyDeviceToHost, s));
   CCK(cudaStreamSynchronize(s));

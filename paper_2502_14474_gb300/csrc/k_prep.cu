@@ -16,12 +16,17 @@ __device__ __forceinline__ void atomic_max_double_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
 }
 
-// One thread per row.
+// One thread per row.  The entries come either from the caller's col/val or,
+// when pk is given, from the packed copy that k_pack already wrote (FP32 value
+// + FP32 remainder for FP64 inputs), so that inputs in host memory are read
+// over the host link only once.
 __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __restrict__ rp_in,
                             const int32_t* __restrict__ col, const void* __restrict__ val,
-                            int val_f64, const void* __restrict__ g_in, int g_f64, double tol,
-                            void* __restrict__ rp_out, int idx64, float* __restrict__ g_out,
-                            float* __restrict__ g_lo_out, PrepFlags* __restrict__ flags) {
+                            int val_f64, const uint32_t* __restrict__ pk,
+                            const float* __restrict__ pk_lo, const void* __restrict__ g_in,
+                            int g_f64, double tol, void* __restrict__ rp_out, int idx64,
+                            float* __restrict__ g_out, float* __restrict__ g_lo_out,
+                            PrepFlags* __restrict__ flags) {
   const int64_t rows = n * m;
   unsigned bad_csr = 0, nonfinite = 0, negative = 0, not_stoch = 0, not_aligned = 0;
   int32_t mn = 0x7fffffff, mx = 0;
@@ -51,7 +56,8 @@ __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __
     const int64_t s = r / m;
     double sum = 0.0;
     for (int64_t i = b; i < e; ++i) {
-      const int32_t c = col[i];
+      const int64_t slot = ((i >> 2) << 3) + (i & 3);
+      const int32_t c = pk ? static_cast<int32_t>(pk[slot]) : col[i];
       if (c < 0 || c >= n) {
         bad_csr = 1;
       } else {
@@ -59,8 +65,13 @@ __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __
             static_cast<unsigned long long>(c > s ? c - s : s - c);
         band = d > band ? d : band;
       }
-      const double p = val_f64 ? static_cast<const double*>(val)[i]
-                               : static_cast<double>(static_cast<const float*>(val)[i]);
+      double p;
+      if (pk)
+        p = static_cast<double>(__uint_as_float(pk[slot + 4])) +
+            (pk_lo ? static_cast<double>(pk_lo[i]) : 0.0);
+      else
+        p = val_f64 ? static_cast<const double*>(val)[i]
+                    : static_cast<double>(static_cast<const float*>(val)[i]);
       if (!isfinite(p)) nonfinite = 1;
       else if (p < 0.0) negative = 1;
       sum += p;
@@ -181,19 +192,14 @@ static unsigned grid_of(int64_t work, int num_sms) {
   return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const int32_t* col_in,
-                             const void* val_in, int val_f64, const void* g_in, int g_f64,
+cudaError_t launch_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* rp_in,
+                             const int32_t* col_in, const void* val_in, int val_f64,
+                             const uint32_t* pk, const float* pk_lo, const void* g_in, int g_f64,
                              double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
                              PrepFlags* flags, int num_sms, cudaStream_t s) {
-  // nnz is read inside the kernel bounds check from the host-provided value
-  int64_t nnz = 0;
-  cudaError_t e = cudaMemcpyAsync(&nnz, rp_in + n * m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
   k_prep_rows<<<grid_of(n * m, num_sms), 256, 0, s>>>(n, m, nnz, rp_in, col_in, val_in, val_f64,
-                                                      g_in, g_f64, tol, rp_out, idx64, g_out,
-                                                      g_lo_out, flags);
+                                                      pk, pk_lo, g_in, g_f64, tol, rp_out, idx64,
+                                                      g_out, g_lo_out, flags);
   return cudaGetLastError();
 }
 

@@ -125,8 +125,9 @@ inline void use_policy_copy(CsrT& P, const Mat& A) {
 // packed CSR of A.
 cudaError_t launch_build_am(const Mat& A, uint32_t* pk_am, int32_t L, cudaStream_t s);
 
-cudaError_t launch_prep_rows(int64_t n, int32_t m, const int64_t* rp_in, const int32_t* col_in,
-                             const void* val_in, int val_f64, const void* g_in, int g_f64,
+cudaError_t launch_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* rp_in,
+                             const int32_t* col_in, const void* val_in, int val_f64,
+                             const uint32_t* pk, const float* pk_lo, const void* g_in, int g_f64,
                              double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
                              PrepFlags* flags, int num_sms, cudaStream_t s);
 // Interleave col/val into the packed layout (groups of 4 entries, 32 bytes).

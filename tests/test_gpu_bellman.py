@@ -115,15 +115,31 @@ def test_zero_value_vector_gives_costs():
     h.close()
 
 
-def test_host_input_matches_device_input():
-    mdp = synth.random_sparse(3000, 4, 10, 1.0, 0.95, seed=11, dtype=np.float32)
+def _pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("where", ["pageable", "pinned", "pinned_staged"])
+@pytest.mark.parametrize("f64", [False, True])
+def test_host_input_matches_device_input(where, f64, monkeypatch):
+    """Host inputs are staged on the device (pageable memory) or read in place by
+    the packing kernel (page-locked memory); both give the device-input handle."""
+    mdp = synth.random_sparse(3000, 4, 10, 1.0, 0.95, seed=11,
+                              dtype=np.float64 if f64 else np.float32)
     from paper_2502_14474_gb300 import MDP
     a = MDP.from_csr(mdp)
-    b = MDP.from_csr(mdp, host_input=True)
+    arrs = [mdp.row_ptr, mdp.col, mdp.val, mdp.g]
+    if where != "pageable":
+        arrs = [_pinned(x) for x in arrs]
+    if where == "pinned_staged":
+        monkeypatch.setenv("MDP_STAGE_HOST_INPUT", "1")
+    b = MDP(mdp.n, mdp.m, *arrs, mdp.gamma)
+    monkeypatch.delenv("MDP_STAGE_HOST_INPUT", raising=False)
     V = torch.rand(mdp.n, dtype=torch.float64, device="cuda")
     oa, ob = a.bellman(V), b.bellman(V)
     assert torch.equal(oa["V"], ob["V"]) and torch.equal(oa["pi"], ob["pi"])
     assert oa["res_inf"] == ob["res_inf"] and oa["res_2"] == ob["res_2"]
+    assert a.info() == b.info()
     a.close()
     b.close()
 
@@ -140,9 +156,10 @@ def test_deterministic_reductions():
     h.close()
 
 
+@pytest.mark.parametrize("where", ["device", "pinned"])
 @pytest.mark.parametrize("bad", ["not_stochastic", "nan", "col_range", "empty_row", "neg",
                                  "gamma", "rowptr"])
-def test_create_rejects_bad_input(bad):
+def test_create_rejects_bad_input(bad, where):
     from paper_2502_14474_gb300 import MDP, MDPError
     mdp = synth.random_sparse(100, 2, 4, 1.0, 0.9, seed=13, dtype=np.float32)
     val, col, rp, g, gamma = mdp.val.copy(), mdp.col.copy(), mdp.row_ptr.copy(), mdp.g.copy(), 0.9
@@ -165,8 +182,9 @@ def test_create_rejects_bad_input(bad):
         gamma = 1.0
     elif bad == "rowptr":
         rp[10] = rp[11] + 1
+    put = dev if where == "device" else _pinned
     with pytest.raises(MDPError) as ei:
-        MDP(mdp.n, mdp.m, dev(rp), dev(col), dev(val), dev(g), gamma)
+        MDP(mdp.n, mdp.m, put(rp), put(col), put(val), put(g), gamma)
     assert ei.value.status_name == expect
 
 
