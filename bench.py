@@ -496,6 +496,7 @@ def main():
                 "launches": dk["launches"]} if not args.no_profile else None
     per_kernel = {k: {"launches": v["launches"], "skipped": v["skipped"],
                       "ms_total": round(v["ms"], 3),
+                      "p50_ms": round(v["p50_ms"], 4), "p99_ms": round(v["p99_ms"], 4),
                       "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"]
                       else None}
                   for k, v in kinds.items() if v["launches"] or v["skipped"]}

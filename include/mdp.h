@@ -269,6 +269,8 @@ typedef struct {
                                        the value vector excluded: they hit L2) */
   int64_t total_launches;           /* every kernel launch of the handle since the last reset,
                                        counted whether or not timing is on */
+  double p50_ms[MDP_PROF_KINDS];    /* median duration of one timed launch (nearest rank) */
+  double p99_ms[MDP_PROF_KINDS];    /* 99th percentile of the same (nearest rank) */
 } mdp_profile_t;
 
 /* Turn event timing of every kernel launch on (1) or off (0); resets the

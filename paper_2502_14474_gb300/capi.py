@@ -93,7 +93,8 @@ class mdp_info_t(ctypes.Structure):
 class mdp_profile_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 12), ("skipped", ctypes.c_int64 * 12),
                 ("ms", ctypes.c_double * 12), ("bytes", ctypes.c_double * 12),
-                ("total_launches", ctypes.c_int64)]
+                ("total_launches", ctypes.c_int64), ("p50_ms", ctypes.c_double * 12),
+                ("p99_ms", ctypes.c_double * 12)]
 
     def as_dict(self):
         kinds = {}
@@ -101,7 +102,8 @@ class mdp_profile_t(ctypes.Structure):
             if name.startswith("unused"):
                 continue
             kinds[name] = dict(launches=self.launches[i], skipped=self.skipped[i],
-                               ms=self.ms[i], bytes=self.bytes[i])
+                               ms=self.ms[i], bytes=self.bytes[i], p50_ms=self.p50_ms[i],
+                               p99_ms=self.p99_ms[i])
         return dict(kinds=kinds, total_launches=self.total_launches)
 
 

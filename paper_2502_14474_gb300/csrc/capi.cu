@@ -67,7 +67,18 @@ struct Prof {
   std::vector<cudaEvent_t> free_ev;
   std::vector<ProfRec> pending;
   mdp_profile_t agg;
+  std::vector<float> samples[MDP_PROF_KINDS];  // per-launch durations of the timed launches
 };
+
+// Nearest-rank percentile q (0 < q <= 1) of v (reorders v).
+double percentile(std::vector<float>& v, double q) {
+  if (v.empty()) return 0.0;
+  size_t k = static_cast<size_t>(std::ceil(q * static_cast<double>(v.size())));
+  k = k < 1 ? 0 : k - 1;
+  if (k >= v.size()) k = v.size() - 1;
+  std::nth_element(v.begin(), v.begin() + static_cast<std::ptrdiff_t>(k), v.end());
+  return v[k];
+}
 
 }  // namespace
 
@@ -257,6 +268,7 @@ void prof_flush(mdp_s* h) {
       if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
         h->prof.agg.ms[r.kind] += ms;
         h->prof.agg.launches[r.kind] += 1;
+        h->prof.samples[r.kind].push_back(ms);
         h->prof.agg.bytes[r.kind] += r.bytes;
       } else {
         cudaGetLastError();
@@ -1317,6 +1329,7 @@ mdp_status mdp_profile_enable(mdp_t h, int on) {
   for (ProfRec& r : h->prof.pending) cudaEventSynchronize(r.b);
   prof_flush(h);
   memset(&h->prof.agg, 0, sizeof(h->prof.agg));
+  for (auto& v : h->prof.samples) v.clear();
   h->launches = 0;
   h->prof.on = on != 0;
   return MDP_OK;
@@ -1329,6 +1342,11 @@ mdp_status mdp_profile_read(mdp_t h, mdp_profile_t* out) {
   prof_flush(h);
   *out = h->prof.agg;
   out->total_launches = h->launches;
+  for (int k = 0; k < MDP_PROF_KINDS; ++k) {
+    std::vector<float> v = h->prof.samples[k];
+    out->p50_ms[k] = percentile(v, 0.50);
+    out->p99_ms[k] = percentile(v, 0.99);
+  }
   return MDP_OK;
 }
 

@@ -272,3 +272,30 @@ def test_action_major_policy_copy_is_bitwise_neutral(store, kind, monkeypatch):
     assert cert["res_inf"] <= 1.05e-9
     a.close()
     b.close()
+
+
+def test_profiler_counts_and_bytes_match_the_solve():
+    """The event profiler behind the roofline numbers: one timed launch per
+    executed GMRES step and per sweep, the algorithmic bytes of the policy-row
+    SpMV (4 action + 16 x 8 packed row + 4 v_j + 4 w bytes per state), and
+    percentiles that bracket the mean."""
+    mdp = synth.banded(65536, 8, 16, 4096, 0.5, 0.99, seed=2, dtype=np.float32)
+    h = _mk(mdp)
+    h.profile(True)
+    V, pi, st = h.solve(tol=1e-9)
+    prof = h.profile_read()
+    h.profile(False)
+    k = prof["kinds"]
+    assert st["converged"]
+    assert k["arnoldi_spmv"]["launches"] == st["inner_iters"]
+    assert k["arnoldi_dots"]["launches"] == st["inner_iters"]
+    assert k["arnoldi_ortho"]["launches"] == st["inner_iters"]
+    assert k["bellman_ff"]["launches"] == st["bellman_sweeps"]
+    assert k["policy_residual"]["launches"] == st["policy_sweeps"] - st["inner_iters"]
+    sp = k["arnoldi_spmv"]
+    assert sp["bytes"] == pytest.approx(sp["launches"] * 140.0 * mdp.n)
+    mean = sp["ms"] / sp["launches"]
+    assert 0 < sp["p50_ms"] <= sp["p99_ms"]
+    assert sp["p50_ms"] <= 2 * mean and sp["p99_ms"] >= 0.5 * mean
+    assert prof["total_launches"] >= sum(v["launches"] + v["skipped"] for v in k.values())
+    h.close()
