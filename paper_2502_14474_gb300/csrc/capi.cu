@@ -1230,26 +1230,43 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
     } else {
       // modified policy iteration in correction form: d_1 = r, d_{k+1} = r + gamma P_pi d_k;
       // V + d_k equals T_pi^k V, and ||d_{k+1} - d_k||_2 is the residual of d_k.
+      // Sweeps are enqueued eight at a time; each returns at once once an earlier
+      // one met the target, so the host reads the status once per batch.  Sweep k
+      // reads d_(k&1) and writes d_((k+1)&1); the last one that ran wrote d_(e&1).
       const float* rsave = reinterpret_cast<const float*>(h->W1);
-      float* da = h->d0;
-      float* db = h->d1;
-      CK(h, cudaMemcpyAsync(da, rsave, static_cast<size_t>(A.n) * sizeof(float),
+      float* dbuf[2] = {h->d0, h->d1};
+      CK(h, cudaMemcpyAsync(dbuf[0], rsave, static_cast<size_t>(A.n) * sizeof(float),
                             cudaMemcpyDeviceToDevice, s));
-      used = 1;
-      while (used < o.max_inner) {
-        CK(h, run(h, s, MDP_PROF_RICHARDSON, 1, bytes_richardson(A, lp), -1, [&] {
-             return launch_richardson(A, lp, h->pi, rsave, da, db, h->partials, h->st, s);
-           }));
-        used += 1;
-        ss.policy_sweeps += 1;
-        transitions += policy_nnz;
-        std::swap(da, db);
-        rc = read_head(h, s);
-        if (rc != MDP_OK) return rc;
-        if (h->head->res_2 <= target) break;
-      }
       CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
-                [&] { return launch_ff_axpy(A.n, h->V, da, A.num_sms, s); }));
+                [&] { return launch_richardson_begin(h->st, target, s); }));
+      used = 1;
+      int executed = 0;
+      while (used < o.max_inner) {
+        const int batch = std::min(8, o.max_inner - used);
+        const size_t first = h->prof.pending.size();
+        for (int i = 0; i < batch; ++i) {
+          const int k = executed + i;
+          CK(h, run(h, s, MDP_PROF_RICHARDSON, 1, bytes_richardson(A, lp), k, [&] {
+               return launch_richardson(A, lp, h->pi, rsave, dbuf[k & 1], dbuf[(k + 1) & 1],
+                                        h->partials, h->st, s);
+             }));
+        }
+        rc = read_head(h, s, false);
+        if (rc != MDP_OK) return rc;
+        const int now = h->head->jdone;
+        for (size_t i = first; i < h->prof.pending.size(); ++i)
+          if (h->prof.pending[i].j >= now) h->prof.pending[i].skipped = true;
+        prof_flush(h);
+        ss.policy_sweeps += now - executed;
+        transitions += policy_nnz * (now - executed);
+        used += now - executed;
+        executed = now;
+        if (!h->head->active) break;
+        if (h->cancel.load()) break;
+      }
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+           return launch_ff_axpy(A.n, h->V, dbuf[executed & 1], A.num_sms, s);
+         }));
     }
     ss.inner_iters += used;
     if (ss.outer_iters - 1 < MDP_HISTORY) ss.inner_history[ss.outer_iters - 1] = used;

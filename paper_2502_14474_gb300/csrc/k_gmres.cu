@@ -261,12 +261,15 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Richardson sweep of the correction system: d_out = r + gamma P_pi d_in;
-// ||d_out - d_in||_2 (the residual of d_in) into st->res_2.
+// ||d_out - d_in||_2 (the residual of d_in) into st->res_2.  The host enqueues
+// several sweeps at a time: a sweep returns at once when an earlier one has
+// met st->target (st->active cleared), and st->jdone counts the sweeps that ran.
 template <typename IdxT, int VW, typename PV>
 __global__ void __launch_bounds__(kThreads)
     k_richardson(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, const float* __restrict__ r,
                  const float* __restrict__ d_in, float* __restrict__ d_out,
                  double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
   __shared__ double red[kThreads / 32];
   constexpr int NV = kThreads / VW;
   const int lane = threadIdx.x % VW;
@@ -318,8 +321,17 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x == 0) {
       st->counter[kCntMisc] = 0;
       st->res_2 = sqrt(sq);
+      st->jdone += 1;
+      if (!(st->res_2 > st->target)) st->active = 0;
     }
   }
+}
+
+// Start a run of Richardson sweeps toward the residual target.
+__global__ void k_richardson_begin(DevState* st, double target) {
+  st->active = 1;
+  st->jdone = 0;
+  st->target = target;
 }
 
 __global__ void k_ff_axpy(int64_t n, float2* __restrict__ V, const float* __restrict__ d) {
@@ -471,6 +483,11 @@ static unsigned ew_blocks(int64_t n, int num_sms) {
   const int64_t cap = static_cast<int64_t>(num_sms) * 8;
   if (b > cap) b = cap;
   return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_richardson_begin(DevState* st, double target, cudaStream_t s) {
+  k_richardson_begin<<<1, 1, 0, s>>>(st, target);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ff_axpy(int64_t n, float2* V, const float* d, int num_sms, cudaStream_t s) {

@@ -82,6 +82,9 @@ cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* 
 
 // Richardson sweep of the correction system (modified policy iteration):
 // d_out = r + gamma P_pi d_in, ||d_out - d_in||_2 into st->res_2.
+// Arm the device-side stop of a run of Richardson sweeps (target on res_2).
+cudaError_t launch_richardson_begin(DevState* st, double target, cudaStream_t s);
+
 cudaError_t launch_richardson(const Mat& A, bool lp, const int32_t* pi, const float* r,
                               const float* d_in, float* d_out, double* partials, DevState* st,
                               cudaStream_t s);

@@ -299,3 +299,20 @@ def test_profiler_counts_and_bytes_match_the_solve():
     assert sp["p50_ms"] <= 2 * mean and sp["p99_ms"] >= 0.5 * mean
     assert prof["total_launches"] >= sum(v["launches"] + v["skipped"] for v in k.values())
     h.close()
+
+
+def test_richardson_sweeps_stop_on_device():
+    """Modified PI enqueues Richardson sweeps eight at a time and each returns at
+    once after one met the target: the sweeps that ran are exactly the policy
+    sweeps counted, one inner step per outer iteration is the initial d = r."""
+    mdp = synth.random_sparse(3000, 4, 8, 1.0, 0.97, seed=34, dtype=np.float32)
+    h = _mk(mdp)
+    h.profile(True)
+    V, pi, st = h.solve(tol=1e-9, inner="richardson", max_inner=500)
+    k = h.profile_read()["kinds"]["richardson"]
+    h.profile(False)
+    assert st["converged"]
+    assert k["launches"] == st["policy_sweeps"]
+    assert st["inner_iters"] == st["policy_sweeps"] + st["outer_iters"]
+    assert oracle.certificate(mdp, V.cpu().numpy())["res_inf"] <= 1.01e-9
+    h.close()
