@@ -93,3 +93,19 @@ def test_serving_budget_admits_one_at_a_time():
     srv.close()
     assert all(r.status == "MDP_OK" for r in reqs)
     assert srv.peak_active == 1 and srv.peak_used <= need * 1.5
+
+
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+def test_bytes_required_bounds_the_handle(store):
+    """Admission control reserves mdp_bytes_required per request: it must cover
+    what a handle really holds (action-major copies of short rows included)."""
+    from paper_2502_14474_gb300 import MDP, capi
+    code = {"f32": capi.MDP_F32, "bf16": capi.MDP_BF16}[store]
+    for mdp in (synth.banded(40000, 8, 16, 2000, 0.5, 0.99, seed=61, dtype=np.float32),
+                synth.grid_world(96, 80, 0.99, seed=62, dtype=np.float32),
+                synth.random_sparse(20000, 5, 4, 1.0, 0.95, seed=63, k_max=32, dtype=np.float32)):
+        h = MDP.from_csr(mdp, store=store)
+        held = h.info()["device_bytes"]
+        need = capi.mdp_bytes_required(mdp.n, mdp.m, int(mdp.row_ptr[-1]), capi.MDP_F32, code, 30)
+        assert need >= held, (mdp.name, need, held)
+        h.close()
