@@ -697,10 +697,13 @@ size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, md
   b += static_cast<size_t>(rows + 1) * (idx64 ? 8 : 4);
   b += static_cast<size_t>(nnz) * (4 + 4 + (val_t == MDP_F64 ? 4 : 0));
   b += static_cast<size_t>(rows) * 4 * 2;  // g (+ g_lo bound)
-  if (store_t == MDP_BF16 || store_t == MDP_F16) b += static_cast<size_t>(nnz) * 2 + rows * 4;
+  // 16-bit copy: packed groups take 4 bytes per entry (2 for the column offset),
+  // in the action-major order of short rows up to 1.25 nnz entries; row scales
+  if (store_t == MDP_BF16 || store_t == MDP_F16)
+    b += static_cast<size_t>(nnz + nnz / 4 + 4) * 4 + static_cast<size_t>(rows) * 4;
   // action-major policy copy of short rows: at most 1.25 nnz padded entries
   if (nnz < 12 * rows) b += static_cast<size_t>(nnz + nnz / 4 + 4) * 8;
-  b += static_cast<size_t>(n) * (8 * 3 + 4);
+  b += static_cast<size_t>(n) * (8 * 3 + 4 + 8);  // V, W1, W2, pi; Richardson d0, d1
   b += static_cast<size_t>(restart + 1) * ld * 4;
   b += sizeof(DevState) + (1 << 20);
   return b;
