@@ -13,8 +13,8 @@
 //
 // Per Arnoldi step j the host enqueues:
 //   K2  k_arnoldi_spmv : w = v_j - gamma P_pi v_j (row s*m+pi(s) gathered from
-//                        the full CSR), stored in u_{j+1}; h_i = <w, v_i>, i <= j
-//                        (block partials, last block reduces in FP64).
+//                        the full CSR), stored in u_{j+1} (k_spmv.cuh);
+//       k_gs_dots      : h_i = <w, v_i>, i <= j (k_dots.cuh);
 //   K3  k_arnoldi_ortho: u_{j+1} = w - sum h_i v_i, ||u_{j+1}||_2; the last
 //                        block appends column j of H, applies the Givens
 //                        rotations, updates |g_{j+1}| and decides convergence
@@ -23,6 +23,8 @@
 //   K5  k_gmres_update : V += sum_i y_i v_i in float-float.
 // Every kernel of a step first reads st->active and returns at once when the
 // cycle has ended, so a whole cycle can be enqueued without host round trips.
+// Modified policy iteration's Richardson sweeps run through the policy-row
+// kernel (its RICH form); this file holds their start kernel.
 #include "k_rows.cuh"
 #include "launch.h"
 
@@ -260,73 +262,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Richardson sweep of the correction system: d_out = r + gamma P_pi d_in;
-// ||d_out - d_in||_2 (the residual of d_in) into st->res_2.  The host enqueues
-// several sweeps at a time: a sweep returns at once when an earlier one has
-// met st->target (st->active cleared), and st->jdone counts the sweeps that ran.
-template <typename IdxT, int VW, typename PV>
-__global__ void __launch_bounds__(kThreads)
-    k_richardson(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi, const float* __restrict__ r,
-                 const float* __restrict__ d_in, float* __restrict__ d_out,
-                 double* __restrict__ partials, DevState* __restrict__ st) {
-  if (!st->active) return;
-  __shared__ double red[kThreads / 32];
-  constexpr int NV = kThreads / VW;
-  const int lane = threadIdx.x % VW;
-  const int vec = threadIdx.x / VW;
-  const bool lp = sizeof(PV) != 4;
-  const PV* val = sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
-                                  : static_cast<const PV*>(P.val16);
-  double my_sq = 0.0;
-  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
-  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
-  for (int64_t tile = t_begin; tile < t_end; ++tile) {
-    const int64_t s = tile * NV + vec;
-    int64_t b = 0, e = 0, row = 0;
-    if (s < P.n) {
-      const int32_t a = __ldg(pi + s);
-      row = s * P.m + a;  // row of the 16-bit scale (the unpacked copy has no action-major form)
-      row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, a), b, e);
-    }
-    float d, den = 0.f;
-    bool packed = false;
-    if constexpr (sizeof(PV) == 2) {
-      if (P.lpk) {
-        row_dot_lp<VW, PV>(P.lpk, GatherF32{d_in}, s, b, e, lane, d, den);
-        packed = true;
-      } else {
-        d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
-      }
-    } else {
-      d = row_dot_f32<VW, PV>(P.col, val, d_in, b, e, lane, P.vec4 != 0);
-    }
-    d = group_sum<VW>(d);
-    if (packed) den = group_sum<VW>(den);
-    if (lane == 0 && s < P.n) {
-      if (packed) d = den > 0.f ? d / den : 0.f;
-      else if (lp) d *= __ldcs(P.row_scale + row);
-      const float nv = fmaf(P.gamma, d, r[s]);
-      d_out[s] = nv;
-      const double df = static_cast<double>(nv - d_in[s]);
-      my_sq += df * df;
-    }
-  }
-  const double bs = block_sum_d(my_sq, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-  if (last_block(&st->counter[kCntMisc])) {
-    double sq = 0.0;
-    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kThreads)
-      sq += __ldcg(partials + b);
-    sq = block_sum_d(sq, red);
-    if (threadIdx.x == 0) {
-      st->counter[kCntMisc] = 0;
-      st->res_2 = sqrt(sq);
-      st->jdone += 1;
-      if (!(st->res_2 > st->target)) st->active = 0;
-    }
-  }
-}
-
 // Start a run of Richardson sweeps toward the residual target.
 __global__ void k_richardson_begin(DevState* st, double target) {
   st->active = 1;
@@ -371,29 +306,6 @@ __global__ void k_from_ff(int64_t n, const float2* __restrict__ src, void* __res
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename IdxT>
-static Csr<IdxT> csr_of(const Mat& A) {
-  Csr<IdxT> P;
-  P.rp = static_cast<const IdxT*>(A.rp);
-  P.col = A.col;
-  P.val = A.val;
-  P.val_lo = A.val_lo;
-  P.g = A.g;
-  P.g_lo = A.g_lo;
-  P.val16 = A.val16;
-  P.lpk = A.lpk;
-  P.row_scale = A.row_scale;
-  P.n = A.n;
-  P.m = A.m;
-  P.vec4 = A.vec4;
-  P.uniform_len = A.uniform_len;
-  P.gamma = static_cast<float>(A.gamma);
-  P.gamma_hi = P.gamma;
-  P.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(P.gamma));
-  use_policy_copy(P, A);
-  return P;
-}
-
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
                                 int64_t ld, int j, int restart, double* partials, DevState* st,
                                 cudaStream_t s) {
@@ -437,45 +349,12 @@ cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* 
   return cudaGetLastError();
 }
 
-template <typename IdxT, int VW, typename PV>
-static cudaError_t rich_go(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
-                           float* d_out, double* partials, DevState* st, cudaStream_t s) {
-  auto kern = k_richardson<IdxT, VW, PV>;
-  static int occ = occ_of(kern);
-  constexpr int NV = kThreads / VW;
-  const Grid G = grid_for((A.n + NV - 1) / NV, A.num_sms * occ, NV);
-  kern<<<static_cast<unsigned>(grid_blocks(G)), kThreads, 0, s>>>(csr_of<IdxT>(A), G, pi, r, d_in,
-                                                                   d_out, partials, st);
-  return cudaGetLastError();
-}
-
-template <typename IdxT, typename PV>
-static cudaError_t rich_v(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
-                          float* d_out, double* partials, DevState* st, cudaStream_t s) {
-  switch (A.vw) {
-    case 1: return rich_go<IdxT, 1, PV>(A, pi, r, d_in, d_out, partials, st, s);
-    case 2: return rich_go<IdxT, 2, PV>(A, pi, r, d_in, d_out, partials, st, s);
-    case 4: return rich_go<IdxT, 4, PV>(A, pi, r, d_in, d_out, partials, st, s);
-    case 8: return rich_go<IdxT, 8, PV>(A, pi, r, d_in, d_out, partials, st, s);
-    case 16: return rich_go<IdxT, 16, PV>(A, pi, r, d_in, d_out, partials, st, s);
-    default: return rich_go<IdxT, 32, PV>(A, pi, r, d_in, d_out, partials, st, s);
-  }
-}
-
-template <typename IdxT>
-static cudaError_t rich_i(const Mat& A, bool lp, const int32_t* pi, const float* r,
-                          const float* d_in, float* d_out, double* partials, DevState* st,
-                          cudaStream_t s) {
-  if (!lp) return rich_v<IdxT, float>(A, pi, r, d_in, d_out, partials, st, s);
-  if (A.store_t == 3) return rich_v<IdxT, __half>(A, pi, r, d_in, d_out, partials, st, s);
-  return rich_v<IdxT, __nv_bfloat16>(A, pi, r, d_in, d_out, partials, st, s);
-}
-
 cudaError_t launch_richardson(const Mat& A, bool lp, const int32_t* pi, const float* r,
                               const float* d_in, float* d_out, double* partials, DevState* st,
                               cudaStream_t s) {
-  return A.idx64 ? rich_i<int64_t>(A, lp, pi, r, d_in, d_out, partials, st, s)
-                 : rich_i<int32_t>(A, lp, pi, r, d_in, d_out, partials, st, s);
+  if (!lp) return launch_richardson_f32(A, pi, r, d_in, d_out, partials, st, s);
+  if (A.store_t == 3) return launch_richardson_f16(A, pi, r, d_in, d_out, partials, st, s);
+  return launch_richardson_bf16(A, pi, r, d_in, d_out, partials, st, s);
 }
 
 static unsigned ew_blocks(int64_t n, int num_sms) {

@@ -27,11 +27,18 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
   for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
 }
 
-template <typename IdxT, int VW, typename PV, int NT, bool WIN>
+// RICH: the same policy-row product as a Richardson sweep of the correction
+// system (modified policy iteration): xout = r + gamma P_pi xin, with
+// ||xout - xin||_2 reduced in a fixed order into st->res_2 by the last block,
+// st->jdone counting the sweeps that ran and st->active cleared once the
+// residual meets st->target (later sweeps of the batch return at once).
+// Otherwise xin = u_j, xout = u_{j+1} = scale_j (u_j - gamma P_pi u_j).
+template <typename IdxT, int VW, typename PV, int NT, bool WIN, bool RICH>
 __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
     k_arnoldi_spmv(Csr<IdxT> P, int64_t states_per_block, int64_t band, int ring_log2,
-                   const int32_t* __restrict__ pi, float* __restrict__ basis, int64_t ld, int j,
-                   DevState* __restrict__ st) {
+                   const int32_t* __restrict__ pi, const float* __restrict__ xin,
+                   float* __restrict__ xout, int j, const float* __restrict__ rvec,
+                   double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int TS = 4 * NT;  // states per tile (four passes of NT states)
   constexpr int NV = NT / VW;
@@ -39,9 +46,21 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
   const int lane = threadIdx.x % VW;
   const int vec = threadIdx.x / VW;
   const bool vec4 = P.vec4 != 0;
-  const float* uj = basis + static_cast<int64_t>(j) * ld;
-  float* uw = basis + static_cast<int64_t>(j + 1) * ld;
-  const float sj = static_cast<float>(st->scale[j]);
+  const float* uj = xin;
+  float* uw = xout;
+  const float sj = RICH ? 1.f : static_cast<float>(st->scale[j]);
+  double racc = 0.0;  // RICH: this thread's part of ||xout - xin||^2
+  // the result of state s from its row product d and its own input xv
+  auto emit = [&](int64_t s, float d, float xv) {
+    if constexpr (RICH) {
+      const float v = fmaf(P.gamma, d, rvec[s]);
+      uw[s] = v;
+      const double df = static_cast<double>(v - xv);
+      racc += df * df;
+    } else {
+      uw[s] = sj * fmaf(-P.gamma, d, xv);
+    }
+  };
   const PV* val = sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
                                   : static_cast<const PV*>(P.val16);
   const bool lp = sizeof(PV) != 4;
@@ -120,7 +139,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
               if (!packed) d = reduce_scatter<VW>(part, lane);
               if (valid) {
                 if (lp && !packed) d *= __ldcs(P.row_scale + r);
-                uw[s] = sj * fmaf(-P.gamma, d, xs(s));
+                emit(s, d, xs(s));
               }
             }
           }
@@ -158,7 +177,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
                                          s, gx, num, den);
                 }
                 const float d = den > 0.f ? __fdividef(num, den) : 0.f;
-                uw[s] = sj * fmaf(-P.gamma, d, xs(s));
+                emit(s, d, xs(s));
               }
             }
           }
@@ -177,7 +196,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
             den = group_sum<VW>(den);
             if (lane == 0 && s < s_lim) {
               const float d = den > 0.f ? num / den : 0.f;
-              uw[s] = sj * fmaf(-P.gamma, d, xs(s));
+              emit(s, d, xs(s));
             }
           }
         } else if (VW == 1) {
@@ -201,7 +220,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
                 if (s2[u] < s_lim) {
                   float d = row_pre_dot<PV>(P.col, val, gx, R[u]);
                   if (lp) d *= __ldcs(P.row_scale + r2[u]);
-                  uw[s2[u]] = sj * fmaf(-P.gamma, d, xs(s2[u]));
+                  emit(s2[u], d, xs(s2[u]));
                 }
               }
             }
@@ -218,7 +237,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
             d = group_sum<VW>(d);
             if (lane == 0 && s < s_lim) {
               if (lp) d *= __ldcs(P.row_scale + r);
-              uw[s] = sj * fmaf(-P.gamma, d, xs(s));
+              emit(s, d, xs(s));
             }
           }
         }
@@ -229,6 +248,23 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
         phase_a(GatherF32{uj}, [&](int64_t s) { return uj[s]; });
       }
       __syncthreads();  // the tile's w (global) visible to the block; ring edge complete
+    }
+  }
+  if constexpr (RICH) {
+    __shared__ double red[NT / 32];
+    const double bs = block_sum_nt<NT>(racc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+    if (last_block(&st->counter[kCntMisc])) {
+      double sq = 0.0;
+      for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += NT)
+        sq += __ldcg(partials + b);
+      sq = block_sum_nt<NT>(sq, red);
+      if (threadIdx.x == 0) {
+        st->counter[kCntMisc] = 0;
+        st->res_2 = sqrt(sq);
+        st->jdone += 1;
+        if (!(st->res_2 > st->target)) st->active = 0;
+      }
     }
   }
 }
@@ -277,10 +313,21 @@ inline int64_t balanced_states_per_block(int64_t n, int64_t max_blocks) {
   return per < 32 ? 32 : per;
 }
 
-template <typename IdxT, int VW, typename PV, int NT, bool WIN>
-cudaError_t spmv_launch(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j, int lg,
-                        DevState* st, cudaStream_t s) {
-  auto kern = k_arnoldi_spmv<IdxT, VW, PV, NT, WIN>;
+// One launch of the policy-row kernel: xin/xout are u_j/u_{j+1} of the GMRES
+// basis (RICH false) or the two Richardson iterates (RICH true, with the
+// right-hand side rvec and one partial per block in `partials`).
+struct SpmvArgs {
+  const float* xin;
+  float* xout;
+  int j;
+  const float* rvec;
+  double* partials;
+};
+
+template <typename IdxT, int VW, typename PV, int NT, bool WIN, bool RICH>
+cudaError_t spmv_launch(const Mat& A, const int32_t* pi, const SpmvArgs& a, int lg, DevState* st,
+                        cudaStream_t s) {
+  auto kern = k_arnoldi_spmv<IdxT, VW, PV, NT, WIN, RICH>;
   const size_t smem = WIN ? (size_t(1) << lg) * sizeof(float) : 0;
   if (smem > 0)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -289,45 +336,62 @@ cudaError_t spmv_launch(const Mat& A, const int32_t* pi, float* basis, int64_t l
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess ||
       occ < 1)
     occ = 1;
-  const int64_t per = balanced_states_per_block(A.n, static_cast<int64_t>(A.num_sms) * occ);
+  // at most num_sms * 8 blocks: one Richardson partial each fits the partials buffer
+  const int64_t cap = static_cast<int64_t>(A.num_sms) * (occ < 8 ? occ : 8);
+  const int64_t per = balanced_states_per_block(A.n, cap);
   const int64_t blocks = (A.n + per - 1) / per;
   kern<<<static_cast<unsigned>(blocks < 1 ? 1 : blocks), NT, smem, s>>>(
-      csr_view<IdxT>(A), per, A.band, lg, pi, basis, ld, j, st);
+      csr_view<IdxT>(A), per, A.band, lg, pi, a.xin, a.xout, a.j, a.rvec, a.partials, st);
   return cudaGetLastError();
 }
 
-// SpMV only (w into u_{j+1}); the ring window for banded matrices.
-template <typename IdxT, int VW, typename PV>
-cudaError_t spmv_only(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                      double* partials, DevState* st, cudaStream_t s) {
+// The ring window for banded matrices, else gathers through L1/L2.
+template <typename IdxT, int VW, typename PV, bool RICH>
+cudaError_t spmv_only(const Mat& A, const int32_t* pi, const SpmvArgs& a, DevState* st,
+                      cudaStream_t s) {
   if (A.window) {
     constexpr int NT = 512;
     const int lg = ring_log2_for(A.band, 4 * NT, sizeof(float), 64 * 1024);
-    if (lg > 0)
-      return spmv_launch<IdxT, VW, PV, NT, true>(A, pi, basis, ld, j, lg, st, s);
+    if (lg > 0) return spmv_launch<IdxT, VW, PV, NT, true, RICH>(A, pi, a, lg, st, s);
   }
-  return spmv_launch<IdxT, VW, PV, 256, false>(A, pi, basis, ld, j, 0, st, s);
+  return spmv_launch<IdxT, VW, PV, 256, false, RICH>(A, pi, a, 0, st, s);
 }
 
-// Lanes per row are 2, 4, 8 or 32 (the create-time choice is rounded to these).
-template <typename IdxT, typename PV>
-cudaError_t spmv_vw(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                    double* partials, DevState* st, cudaStream_t s) {
+// Lanes per row are 1, 2, 4, 8 or 32 (the create-time choice is rounded to these).
+template <typename IdxT, typename PV, bool RICH>
+cudaError_t spmv_vw(const Mat& A, const int32_t* pi, const SpmvArgs& a, DevState* st,
+                    cudaStream_t s) {
   switch (A.vw) {
-    case 1: return spmv_only<IdxT, 1, PV>(A, pi, basis, ld, j, partials, st, s);
-    case 2: return spmv_only<IdxT, 2, PV>(A, pi, basis, ld, j, partials, st, s);
-    case 4: return spmv_only<IdxT, 4, PV>(A, pi, basis, ld, j, partials, st, s);
+    case 1: return spmv_only<IdxT, 1, PV, RICH>(A, pi, a, st, s);
+    case 2: return spmv_only<IdxT, 2, PV, RICH>(A, pi, a, st, s);
+    case 4: return spmv_only<IdxT, 4, PV, RICH>(A, pi, a, st, s);
     case 8:
-    case 16: return spmv_only<IdxT, 8, PV>(A, pi, basis, ld, j, partials, st, s);
-    default: return spmv_only<IdxT, 32, PV>(A, pi, basis, ld, j, partials, st, s);
+    case 16: return spmv_only<IdxT, 8, PV, RICH>(A, pi, a, st, s);
+    default: return spmv_only<IdxT, 32, PV, RICH>(A, pi, a, st, s);
   }
+}
+
+template <typename PV, bool RICH>
+cudaError_t spmv_entry(const Mat& A, const int32_t* pi, const SpmvArgs& a, DevState* st,
+                       cudaStream_t s) {
+  return A.idx64 ? spmv_vw<int64_t, PV, RICH>(A, pi, a, st, s)
+                 : spmv_vw<int32_t, PV, RICH>(A, pi, a, st, s);
+}
+
+// The two entry points every probability type's translation unit instantiates.
+template <typename PV>
+cudaError_t arnoldi_spmv_tu(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
+                            DevState* st, cudaStream_t s) {
+  const SpmvArgs a{basis + static_cast<int64_t>(j) * ld, basis + static_cast<int64_t>(j + 1) * ld,
+                   j, nullptr, nullptr};
+  return spmv_entry<PV, false>(A, pi, a, st, s);
 }
 
 template <typename PV>
-cudaError_t spmv_entry(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                       double* partials, DevState* st, cudaStream_t s) {
-  return A.idx64 ? spmv_vw<int64_t, PV>(A, pi, basis, ld, j, partials, st, s)
-                 : spmv_vw<int32_t, PV>(A, pi, basis, ld, j, partials, st, s);
+cudaError_t richardson_tu(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
+                          float* d_out, double* partials, DevState* st, cudaStream_t s) {
+  const SpmvArgs a{d_in, d_out, 0, r, partials};
+  return spmv_entry<PV, true>(A, pi, a, st, s);
 }
 
 }  // namespace mdpk

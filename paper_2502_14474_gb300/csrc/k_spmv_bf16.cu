@@ -7,7 +7,14 @@ cudaError_t launch_arnoldi_spmv_bf16(const Mat& A, const int32_t* pi, float* bas
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s) {
   (void)restart;
-  return spmv_entry<__nv_bfloat16>(A, pi, basis, ld, j, partials, st, s);
+  (void)partials;
+  return arnoldi_spmv_tu<__nv_bfloat16>(A, pi, basis, ld, j, st, s);
+}
+
+cudaError_t launch_richardson_bf16(const Mat& A, const int32_t* pi, const float* r,
+                                   const float* d_in, float* d_out, double* partials,
+                                   DevState* st, cudaStream_t s) {
+  return richardson_tu<__nv_bfloat16>(A, pi, r, d_in, d_out, partials, st, s);
 }
 
 }  // namespace mdpk

@@ -7,7 +7,14 @@ cudaError_t launch_arnoldi_spmv_f16(const Mat& A, const int32_t* pi, float* basi
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s) {
   (void)restart;
-  return spmv_entry<__half>(A, pi, basis, ld, j, partials, st, s);
+  (void)partials;
+  return arnoldi_spmv_tu<__half>(A, pi, basis, ld, j, st, s);
+}
+
+cudaError_t launch_richardson_f16(const Mat& A, const int32_t* pi, const float* r,
+                                   const float* d_in, float* d_out, double* partials,
+                                   DevState* st, cudaStream_t s) {
+  return richardson_tu<__half>(A, pi, r, d_in, d_out, partials, st, s);
 }
 
 }  // namespace mdpk

@@ -9,7 +9,14 @@ cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basi
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s) {
   (void)restart;
-  return spmv_entry<float>(A, pi, basis, ld, j, partials, st, s);
+  (void)partials;
+  return arnoldi_spmv_tu<float>(A, pi, basis, ld, j, st, s);
+}
+
+cudaError_t launch_richardson_f32(const Mat& A, const int32_t* pi, const float* r,
+                                   const float* d_in, float* d_out, double* partials,
+                                   DevState* st, cudaStream_t s) {
+  return richardson_tu<float>(A, pi, r, d_in, d_out, partials, st, s);
 }
 
 cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, int restart,

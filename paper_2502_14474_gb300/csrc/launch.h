@@ -58,6 +58,16 @@ cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float*
                                 int64_t ld, int j, int restart, double* partials, DevState* st,
                                 cudaStream_t s);
 
+// Richardson sweeps through the policy-row kernel (one per probability type).
+cudaError_t launch_richardson_f32(const Mat& A, const int32_t* pi, const float* r,
+                                  const float* d_in, float* d_out, double* partials,
+                                  DevState* st, cudaStream_t s);
+cudaError_t launch_richardson_bf16(const Mat& A, const int32_t* pi, const float* r,
+                                   const float* d_in, float* d_out, double* partials,
+                                   DevState* st, cudaStream_t s);
+cudaError_t launch_richardson_f16(const Mat& A, const int32_t* pi, const float* r,
+                                  const float* d_in, float* d_out, double* partials,
+                                  DevState* st, cudaStream_t s);
 cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
                                     int j, int restart, double* partials, DevState* st,
                                     cudaStream_t s);
