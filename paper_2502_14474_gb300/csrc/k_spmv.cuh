@@ -144,40 +144,44 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
             }
           }
         } else if (VW == 1 && sizeof(PV) == 2 && P.lpk) {
-          // packed 16-bit copy, short rows: the four states of a thread have
-          // their actions, then the first two groups of all four rows, in
-          // flight together (a row of up to 5 entries spans at most two groups;
-          // longer rows load the rest on the way)
+          // packed 16-bit copy, short rows: two of a thread's four states at a
+          // time have the first two groups of their rows in flight together (a
+          // row of up to 5 entries spans at most two groups; longer rows load
+          // the rest on the way); two, not four, to stay within 64 registers
           if constexpr (VW == 1 && sizeof(PV) == 2) {
-            int32_t oe[4];  // (row start & 3) | (row end - row start) << 2
-            uint4 G0[4], G1[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int64_t s = s0 + p * NT + threadIdx.x;
-              int64_t b = 0, e = 0;
-              if (s < s_lim) row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p]), b, e);
-              const int32_t o = static_cast<int32_t>(b & 3), len = static_cast<int32_t>(e - b);
-              oe[p] = o | (len << 2);
-              G0[p] = len > 0 ? __ldcs(P.lpk + (b >> 2)) : make_uint4(0, 0, 0, 0);
-              G1[p] = o + len > 4 ? __ldcs(P.lpk + (b >> 2) + 1) : make_uint4(0, 0, 0, 0);
-            }
+            for (int p0 = 0; p0 < 4; p0 += 2) {
+              int32_t oe[2];  // (row start & 3) | (row end - row start) << 2
+              uint4 G0[2], G1[2];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int64_t s = s0 + p * NT + threadIdx.x;
-              if (s < s_lim) {
-                const int32_t o = oe[p] & 3, len = oe[p] >> 2;
-                float num = 0.f, den = 0.f;
-                lp_group_dot_rel<PV>(G0[p], o, o + len, s, gx, num, den);
-                lp_group_dot_rel<PV>(G1[p], o - 4, o + len - 4, s, gx, num, den);
-                if (o + len > 8) {  // rows longer than two groups: the rest on the way
-                  int64_t b = 0, e = 0;
-                  row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p]), b, e);
-                  for (int32_t k = 8; k < o + len; k += 4)
-                    lp_group_dot_rel<PV>(__ldcs(P.lpk + (b >> 2) + (k >> 2)), o - k, o + len - k,
-                                         s, gx, num, den);
+              for (int u = 0; u < 2; ++u) {
+                const int64_t s = s0 + (p0 + u) * NT + threadIdx.x;
+                int64_t b = 0, e = 0;
+                if (s < s_lim)
+                  row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p0 + u]), b, e);
+                const int32_t o = static_cast<int32_t>(b & 3), len = static_cast<int32_t>(e - b);
+                oe[u] = o | (len << 2);
+                G0[u] = len > 0 ? __ldcs(P.lpk + (b >> 2)) : make_uint4(0, 0, 0, 0);
+                G1[u] = o + len > 4 ? __ldcs(P.lpk + (b >> 2) + 1) : make_uint4(0, 0, 0, 0);
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int64_t s = s0 + (p0 + u) * NT + threadIdx.x;
+                if (s < s_lim) {
+                  const int32_t o = oe[u] & 3, len = oe[u] >> 2;
+                  float num = 0.f, den = 0.f;
+                  lp_group_dot_rel<PV>(G0[u], o, o + len, s, gx, num, den);
+                  lp_group_dot_rel<PV>(G1[u], o - 4, o + len - 4, s, gx, num, den);
+                  if (o + len > 8) {  // rows longer than two groups: the rest on the way
+                    int64_t b = 0, e = 0;
+                    row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, act[p0 + u]), b, e);
+                    for (int32_t k = 8; k < o + len; k += 4)
+                      lp_group_dot_rel<PV>(__ldcs(P.lpk + (b >> 2) + (k >> 2)), o - k,
+                                           o + len - k, s, gx, num, den);
+                  }
+                  const float d = den > 0.f ? __fdividef(num, den) : 0.f;
+                  emit(s, d, xs(s));
                 }
-                const float d = den > 0.f ? __fdividef(num, den) : 0.f;
-                emit(s, d, xs(s));
               }
             }
           }
@@ -200,7 +204,23 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
             }
           }
         } else if (VW == 1) {
-          if constexpr (VW == 1) {
+          if constexpr (VW == 1 && sizeof(PV) == 2) {
+            // unpacked 16-bit copy (bands too wide for the packed one): one row
+            // at a time, so that this rare branch does not raise the register
+            // budget of the packed branch compiled into the same kernel
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int64_t s = s0 + p * NT + threadIdx.x;
+              if (s < s_lim) {
+                int64_t b = 0, e = 0;
+                const int64_t r = policy_row(P, s, act[p]);
+                row_bounds<IdxT>(P.rp, P.uniform_len, r, b, e);
+                float d = row_dot_f32<1, PV>(P.col, val, gx, b, e, 0, vec4);
+                d *= __ldcs(P.row_scale + r);
+                emit(s, d, xs(s));
+              }
+            }
+          } else if constexpr (VW == 1) {
             // short rows: two states per thread with the actions, row pointers and
             // first two packed groups of both rows in flight together
 #pragma unroll
