@@ -531,9 +531,10 @@ mdp_status check_policy(mdp_s* h, const int32_t* pi, cudaStream_t s) {
 
 // Enqueue the kernels of one restart cycle: `steps` Arnoldi steps (policy-row
 // SpMV, Gram-Schmidt dots, orthogonalisation + Givens) and the solution update.
-cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
-                          cudaStream_t s) {
-  for (int j = 0; j < steps; ++j) {
+// Arnoldi steps j0 .. j1-1 of a cycle of `steps` steps.
+cudaError_t enqueue_steps(mdp_s* h, const int32_t* pi, int j0, int j1, int steps, bool lp,
+                          int cgs2, cudaStream_t s) {
+  for (int j = j0; j < j1; ++j) {
     cudaError_t e = run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), j, [&] {
       return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
     });
@@ -547,10 +548,27 @@ cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int c
     });
     if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_update(mdp_s* h, cudaStream_t s) {
   return run(h, s, MDP_PROF_GMRES_UPDATE, 1, 0.0, -1, [&] {
     return launch_gmres_update(h->A, h->basis, h->ld, h->V, h->st, s);
   });
 }
+
+cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+                          cudaStream_t s) {
+  const cudaError_t e = enqueue_steps(h, pi, 0, steps, steps, lp, cgs2, s);
+  return e != cudaSuccess ? e : enqueue_update(h, s);
+}
+
+// Below this many states a GMRES step takes a few microseconds and the launches
+// of the steps past the end of a cycle (which return at once, but still pass
+// through the GPU's launch queue) outweigh a host check: such cycles are
+// enqueued kChunkSteps steps at a time, with a status read between chunks.
+constexpr int64_t kChunkedBelow = int64_t(1) << 20;
+constexpr int kChunkSteps = 8;
 
 // The captured graph of a cycle configuration (captured once the handle has
 // run four eager cycles, which also initialised every launcher); nullptr when
@@ -600,8 +618,20 @@ cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int
 mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
                        cudaStream_t s, int* jdone, int* converged) {
   const size_t first = h->prof.pending.size();
-  cudaGraphExec_t g = cycle_graph(h, pi, steps, lp, cgs2, s);
-  if (g) {
+  const bool chunked =
+      h->A.n < kChunkedBelow && steps > kChunkSteps && !getenv("MDP_NO_CYCLE_CHUNKS");
+  cudaGraphExec_t g = chunked ? nullptr : cycle_graph(h, pi, steps, lp, cgs2, s);
+  if (chunked) {
+    for (int j0 = 0; j0 < steps; j0 += kChunkSteps) {
+      const int j1 = std::min(steps, j0 + kChunkSteps);
+      CK(h, enqueue_steps(h, pi, j0, j1, steps, lp, cgs2, s));
+      if (j1 == steps) break;
+      mdp_status rc = read_head(h, s, false);
+      if (rc != MDP_OK) return rc;
+      if (!h->head->active) break;
+    }
+    CK(h, enqueue_update(h, s));
+  } else if (g) {
     CK(h, cudaGraphLaunch(g, s));
     h->launches += static_cast<int64_t>(steps) * (cgs2 ? 5 : 3) + 1;
   } else {
@@ -1302,6 +1332,12 @@ mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts*
       if (hs[i] == hs[k]) return fail(MDP_ERR_ARG, "mdp_batch_solve: a handle appears twice");
   std::vector<mdp_status> st(static_cast<size_t>(count), MDP_OK);
   std::vector<std::string> msg(static_cast<size_t>(count));
+  // largest first (by nonzeros): a large MDP taken last would leave the other
+  // workers idle while it runs alone; results do not depend on the order
+  std::vector<int32_t> order(static_cast<size_t>(count));
+  for (int32_t i = 0; i < count; ++i) order[static_cast<size_t>(i)] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return hs[a]->A.nnz > hs[b]->A.nnz; });
   std::atomic<int32_t> next{0};
   const int workers = std::min<int>(n_streams, std::max<int32_t>(count, 1));
   std::vector<std::thread> pool;
@@ -1318,8 +1354,9 @@ mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts*
         return;
       }
       for (;;) {
-        const int32_t i = next.fetch_add(1);
-        if (i >= count) break;
+        const int32_t k = next.fetch_add(1);
+        if (k >= count) break;
+        const int32_t i = order[static_cast<size_t>(k)];
         mdp_solve_stats one;
         st[i] = mdp_solve(hs[i], opts, nullptr, MDP_F64, V_out[i], pi_out ? pi_out[i] : nullptr,
                           &one, s);

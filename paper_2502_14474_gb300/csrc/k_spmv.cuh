@@ -356,9 +356,12 @@ cudaError_t spmv_launch(const Mat& A, const int32_t* pi, const SpmvArgs& a, int 
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess ||
       occ < 1)
     occ = 1;
-  // at most num_sms * 8 blocks: one Richardson partial each fits the partials buffer
+  // at most num_sms * 8 blocks (one Richardson partial each fits the partials
+  // buffer), and at least NT states per block: a small matrix gets fewer blocks
+  // with every thread busy, which leaves room for other streams' kernels
   const int64_t cap = static_cast<int64_t>(A.num_sms) * (occ < 8 ? occ : 8);
-  const int64_t per = balanced_states_per_block(A.n, cap);
+  int64_t per = balanced_states_per_block(A.n, cap);
+  if (per < NT) per = NT;
   const int64_t blocks = (A.n + per - 1) / per;
   kern<<<static_cast<unsigned>(blocks < 1 ? 1 : blocks), NT, smem, s>>>(
       csr_view<IdxT>(A), per, A.band, lg, pi, a.xin, a.xout, a.j, a.rvec, a.partials, st);

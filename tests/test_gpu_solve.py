@@ -231,7 +231,9 @@ def test_graph_replayed_cycles_match_eager():
     """Restart cycles replayed from captured CUDA graphs (side stream) give bitwise
     the same solve as eagerly launched cycles (legacy default stream)."""
     from paper_2502_14474_gb300 import MDP
-    mdp = synth.banded(60000, 8, 16, 1500, 0.5, 0.99, seed=35, dtype=np.float32)
+    # large enough (2^20 states) for whole cycles, which smaller matrices enqueue
+    # in chunks of eight steps instead
+    mdp = synth.banded(1 << 20, 4, 16, 1500, 0.5, 0.99, seed=35, dtype=np.float32)
     eager = MDP.from_csr(mdp)
     Ve, pie, se = eager.solve(tol=1e-9)
     side = torch.cuda.Stream()
@@ -316,3 +318,19 @@ def test_richardson_sweeps_stop_on_device():
     assert st["inner_iters"] == st["policy_sweeps"] + st["outer_iters"]
     assert oracle.certificate(mdp, V.cpu().numpy())["res_inf"] <= 1.01e-9
     h.close()
+
+
+def test_chunked_cycles_match_whole_cycles(monkeypatch):
+    """Below 2^20 states a restart cycle is enqueued eight steps at a time with a
+    status check between chunks; the steps that run, hence the solve, are
+    bitwise those of a whole enqueued cycle."""
+    from paper_2502_14474_gb300 import MDP
+    mdp = synth.random_sparse(20000, 6, 8, 1.0, 0.99, seed=36, dtype=np.float32)
+    a = MDP.from_csr(mdp)
+    Va, pa, sa = a.solve(tol=1e-9)
+    monkeypatch.setenv("MDP_NO_CYCLE_CHUNKS", "1")
+    Vb, pb, sb = a.solve(tol=1e-9)
+    monkeypatch.delenv("MDP_NO_CYCLE_CHUNKS")
+    assert torch.equal(Va, Vb) and torch.equal(pa, pb)
+    assert sa["inner_iters"] == sb["inner_iters"] and sa["outer_iters"] == sb["outer_iters"]
+    a.close()
