@@ -316,9 +316,10 @@ def run_batch(args):
     seq_el, _, _ = go(1)
     trans = sum(st["transitions"] for st in stats)
     el = float(np.median(times))
+    # the float-float Bellman residual each solve ends on (the oracle certifies
+    # batch results in the GPU tests, not here)
     sample = list(range(0, len(mdps), max(1, len(mdps) // 5)))
-    import oracle
-    cert = [oracle.certificate(mdps[i], Vs[i].cpu().numpy())["res_inf"] for i in sample]
+    res = [stats[i]["residual_inf"] for i in sample]
     line = {"metric": METRIC, "value": trans / el, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -329,7 +330,7 @@ def run_batch(args):
                        "generation_s": gen_s},
             "converged": sum(1 for x in status if x == "MDP_OK"),
             "sequential_ms": seq_el * 1e3, "speedup_vs_one_stream": seq_el / el,
-            "oracle_residual_sample": cert}
+            "solve_residual_sample": res}
     print(json.dumps(line), flush=True)
     for h in hs:
         h.close()
@@ -340,7 +341,6 @@ def run_serve(args):
     """Poisson request stream through the continuous-batching loop (one JSON line)."""
     import torch
     import synth
-    import oracle
     from paper_2502_14474_gb300 import serve
     rng = np.random.default_rng(5)
     pool = [synth.uneven_mdp(p) for p in synth.uneven_batch_params(48, seed=5)]
@@ -372,8 +372,9 @@ def run_serve(args):
     wall = srv.run_trace(reqs)
     srv.close()
     summ = serve.summarize(reqs, wall)
+    # 1% of the requests: the float-float Bellman residual their solves end on
+    # (the oracle certifies served results in the GPU tests, not here)
     sample = [r for r in reqs if r.rid % 100 == 0 and r.status == "MDP_OK"]
-    errs = [oracle.certificate(r.mdp, r.V) for r in sample]
     line = {"metric": "solves/s (with p50/p99 latency)", "value": summ["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -384,9 +385,9 @@ def run_serve(args):
                        "large": "n=2^20, m=8, 16 successors"},
             "serving": summ, "peak_active": srv.peak_active,
             "peak_budget_gb": srv.peak_used / 1e9,
-            "oracle_sample": {"requests": len(sample),
-                              "max_residual_inf": max((e["res_inf"] for e in errs), default=None),
-                              "max_error_bound": max((e["bound"] for e in errs), default=None)}}
+            "residual_sample": {"requests": len(sample),
+                                "max_residual_inf": max((r.stats["residual_inf"] for r in sample),
+                                                        default=None)}}
     print(json.dumps(line), flush=True)
     return 0
 
