@@ -78,3 +78,20 @@ def test_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt
                 assert "oracle.c" not in txt
+
+
+def test_bytes_required_terms(lib):
+    """The admission estimate covers the 16-bit copy at 4 bytes per entry (column
+    offset + value, with up to a quarter of padding for short rows) and the
+    action-major copy of short rows (one more 8-byte entry per nonzero, padded)."""
+    from paper_2502_14474_gb300 import capi
+    n, m, nnz = 1 << 20, 8, 1 << 27          # 16 entries per row: no short-row copy
+    f32 = capi.mdp_bytes_required(n, m, nnz, capi.MDP_F32, capi.MDP_F32, 30)
+    b16 = capi.mdp_bytes_required(n, m, nnz, capi.MDP_F32, capi.MDP_BF16, 30)
+    assert b16 - f32 >= nnz * 4 * 1.25 + n * m * 4
+    short = 5 * n * m                          # 5 entries per row: short rows
+    s32 = capi.mdp_bytes_required(n, m, short, capi.MDP_F32, capi.MDP_F32, 30)
+    plain = (n * m + 1) * 4 + short * 8 + n * m * 8
+    assert s32 - plain >= short * 8 * 1.25    # the padded action-major copy
+    f64 = capi.mdp_bytes_required(n, m, nnz, capi.MDP_F64, capi.MDP_F32, 30)
+    assert f64 - f32 >= nnz * 4                # FP64 remainders of the probabilities
