@@ -303,12 +303,22 @@ def test_profiler_counts_and_bytes_match_the_solve():
     h.close()
 
 
-def test_richardson_sweeps_stop_on_device():
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+@pytest.mark.parametrize("kind", ["random", "grid", "banded"])
+def test_richardson_sweeps_stop_on_device(store, kind):
     """Modified PI enqueues Richardson sweeps eight at a time and each returns at
     once after one met the target: the sweeps that ran are exactly the policy
-    sweeps counted, one inner step per outer iteration is the initial d = r."""
-    mdp = synth.random_sparse(3000, 4, 8, 1.0, 0.97, seed=34, dtype=np.float32)
-    h = _mk(mdp)
+    sweeps counted, one inner step per outer iteration is the initial d = r.  The
+    sweeps run through the policy-row kernel's Richardson form on every row layout
+    (short rows with the action-major copy, banded rows with the ring window,
+    packed 16-bit copies)."""
+    if kind == "random":
+        mdp = synth.random_sparse(3000, 4, 8, 1.0, 0.97, seed=34, dtype=np.float32)
+    elif kind == "grid":
+        mdp = synth.grid_world(48, 40, 0.97, seed=37, dtype=np.float32)
+    else:
+        mdp = synth.banded(40000, 4, 16, 1000, 0.5, 0.97, seed=38, dtype=np.float32)
+    h = _mk(mdp, store=store)
     h.profile(True)
     V, pi, st = h.solve(tol=1e-9, inner="richardson", max_inner=500)
     k = h.profile_read()["kinds"]["richardson"]
