@@ -216,8 +216,9 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts, const void* V_init, md
 /*
  * mdp_batch_solve -- solve `count` independent MDPs (one handle each) with the
  * inexact policy iteration of mdp_solve, concurrently: `n_streams` host
- * workers each own a CUDA stream and take the next MDP from a shared counter,
- * so the kernels of different (often small, uneven) MDPs overlap on the GPU.
+ * workers each own a CUDA stream and take the next MDP, largest (by nonzeros)
+ * first, from a shared counter, so the kernels of different (often small,
+ * uneven) MDPs overlap on the GPU and no large MDP runs alone at the end.
  *   hs[count]      distinct handles (each solved once; not shared across calls).
  *   opts           NULL = defaults, used for every MDP.
  *   V_out[i]       double[n_i] device;  pi_out[i] int32[n_i] device or NULL
