@@ -4,7 +4,8 @@
  *
  * Problem (madupite, "Problem Setting and Solution Methods"): an
  * infinite-horizon discounted MDP with n states and m actions; minimise the
- * expected discounted cost.  With P(s'|s,a) and stage cost g(s,a):
+ * expected discounted cost (or maximise a reward, MDP_FLAG_MAXIMIZE).  With
+ * P(s'|s,a) and stage cost g(s,a):
  *
  *   Q(s,a)   = g(s,a) + gamma * sum_{s'} P(s'|s,a) V(s')          (Bellman backup)
  *   (T V)(s) = min_a Q(s,a),   greedy(V)(s) = lowest a attaining it
@@ -78,6 +79,14 @@ typedef enum {
 #define MDP_FLAG_AUTOTUNE 0x4ull     /* time the candidate lanes-per-row / shared-memory window
                                         schedules of the Bellman kernel at create and keep the
                                         fastest (cached per process by matrix shape) */
+#define MDP_FLAG_MAXIMIZE 0x8ull     /* `cost` holds rewards r(s,a) to be maximised: V = max_a
+                                        [r + gamma P V], pi = lowest maximising action.  Solved
+                                        as the minimisation with g = -r; every value vector in
+                                        or out of the handle (V_in, V_out, V_init, v_inout,
+                                        r_out) is in reward terms.  Negation is exact, so the
+                                        results are bitwise the negated values (same policy,
+                                        same norms and statistics) of a minimising handle
+                                        given cost -r and value vectors -V. */
 
 /* Inner solver of the policy-evaluation step (madupite: "selecting among a wide
  * range of inner solvers for the approximate policy evaluation step"). */
@@ -136,6 +145,7 @@ typedef struct {
   int32_t store_t;       /* mdp_dtype of the inner-solve probabilities */
   size_t device_bytes;   /* library-owned device memory of this handle */
   double gamma;
+  int32_t maximize;      /* 1 when created with MDP_FLAG_MAXIMIZE */
 } mdp_info_t;
 
 /*

@@ -13,14 +13,14 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import capi
+from . import capi, ingest
 from .capi import (MDP_BF16, MDP_F16, MDP_F32, MDP_F64, MDP_FLAG_HOST_INPUT,
                    MDP_FLAG_NO_VALIDATE, MDP_INNER_GMRES, MDP_INNER_RICHARDSON, MDPError,
                    mdp_bellman, mdp_bytes_required, mdp_cancel, mdp_create, mdp_default_opts,
                    mdp_destroy, mdp_info, mdp_last_error, mdp_policy_eval, mdp_profile_enable,
                    mdp_profile_read, mdp_solve, mdp_version)
 
-__all__ = ["MDP", "MDPError", "capi", "load", "mdp_create", "mdp_destroy", "mdp_bellman",
+__all__ = ["MDP", "MDPError", "capi", "ingest", "load", "mdp_create", "mdp_destroy", "mdp_bellman",
            "mdp_policy_eval", "mdp_solve", "mdp_default_opts", "mdp_info", "mdp_bytes_required",
            "mdp_cancel", "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read", "MDP_F32", "MDP_F64", "MDP_BF16",
            "MDP_F16", "MDP_INNER_GMRES", "MDP_INNER_RICHARDSON"]
@@ -56,10 +56,12 @@ class MDP:
     or float64) are CUDA tensors, or numpy arrays (host input: the library
     copies them in).  ``store`` selects the inner-solve probability precision:
     "f32", "bf16" or "f16" (16-bit copy with per-row renormalisation).
+    ``maximize=True`` reads ``cost`` as rewards to maximise; values in and out
+    are then in reward terms (see MDP_FLAG_MAXIMIZE in include/mdp.h).
     """
 
     def __init__(self, n, m, row_ptr, col, val, cost, gamma, store="f32", stream=None,
-                 validate=True, device=None, autotune=False):
+                 validate=True, device=None, autotune=False, maximize=False):
         torch = _torch()
         self.n, self.m, self.gamma = int(n), int(m), float(gamma)
         host = isinstance(row_ptr, np.ndarray)
@@ -78,24 +80,32 @@ class MDP:
             torch.device("cuda", torch.cuda.current_device()) if host else row_ptr.device)
         flags = (MDP_FLAG_HOST_INPUT if host else 0) | (0 if validate else MDP_FLAG_NO_VALIDATE)
         flags |= capi.MDP_FLAG_AUTOTUNE if autotune else 0
+        flags |= capi.MDP_FLAG_MAXIMIZE if maximize else 0
         self.stream = stream
         with torch.cuda.device(self.device):
             self.h = mdp_create(n, m, row_ptr, col, val, _dtype_code(val), cost, _dtype_code(cost),
                                 gamma, _STORE[store], stream=self._s(), flags=flags)
         self.store = store
+        self.maximize = bool(maximize)
 
     @classmethod
     def from_csr(cls, mdp, store="f32", device="cuda", host_input=False, validate=True,
-                 autotune=False, stream=None):
-        """Build from an object with n, m, gamma, row_ptr, col, val, g (numpy)."""
+                 autotune=False, stream=None, maximize=None):
+        """Build from an object with n, m, gamma, row_ptr, col, val, g (numpy);
+        ``maximize`` defaults to the object's own ``maximize`` attribute (False
+        when it has none)."""
         torch = _torch()
+        if maximize is None:
+            maximize = bool(getattr(mdp, "maximize", False))
         if host_input:
             return cls(mdp.n, mdp.m, mdp.row_ptr, mdp.col, mdp.val, mdp.g, mdp.gamma, store=store,
-                       validate=validate, device=device, autotune=autotune, stream=stream)
+                       validate=validate, device=device, autotune=autotune, stream=stream,
+                       maximize=maximize)
         dev = torch.device(device)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         return cls(mdp.n, mdp.m, t(mdp.row_ptr), t(mdp.col), t(mdp.val), t(mdp.g), mdp.gamma,
-                   store=store, validate=validate, autotune=autotune, stream=stream)
+                   store=store, validate=validate, autotune=autotune, stream=stream,
+                   maximize=maximize)
 
     def _s(self):
         torch = _torch()

@@ -1,4 +1,5 @@
-"""ctypes binding of the C ABI in include/mdp.h (argument marshalling only).
+"""ctypes binding of the C ABI in include/mdp.h and include/mdp_ingest.h
+(argument marshalling only).
 
 Every function below has the name of the C entry point it calls and does no
 arithmetic of its own: all work runs in the CUDA library.  Array arguments
@@ -21,14 +22,18 @@ STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_ARG", 2: "MDP_ERR_NOT_STOCHASTIC", 3: "
 MDP_FLAG_HOST_INPUT = 0x1
 MDP_FLAG_NO_VALIDATE = 0x2
 MDP_FLAG_AUTOTUNE = 0x4
+MDP_FLAG_MAXIMIZE = 0x8
 MDP_INNER_GMRES, MDP_INNER_RICHARDSON = 0, 1
+MDP_UNSEEN_ERROR, MDP_UNSEEN_SELF_LOOP = 0, 1
 MDP_HISTORY = 128
 
-# Every symbol include/mdp.h declares (checked by the tests).
+# Every symbol include/*.h declares (checked by the tests).
 EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
-                   "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim"])
+                   "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim",
+                   "mdp_csr_from_functions", "mdp_csr_from_samples", "mdp_csr_read_petsc",
+                   "mdp_csr_write_petsc", "mdp_csr_free"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
               "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
@@ -84,7 +89,7 @@ class mdp_info_t(ctypes.Structure):
                 ("uniform_len", ctypes.c_int32), ("idx64", ctypes.c_int32),
                 ("band", ctypes.c_int64), ("has_low_precision", ctypes.c_int32),
                 ("store_t", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("maximize", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,6 +111,18 @@ class mdp_profile_t(ctypes.Structure):
                                p99_ms=self.p99_ms[i])
         return dict(kinds=kinds, total_launches=self.total_launches)
 
+
+class mdp_host_csr(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_int64), ("n_actions", ctypes.c_int32),
+                ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("owned", ctypes.c_int32)]
+
+
+MDP_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+MDP_ROW_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_void_p)
+MDP_COST_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p)
 
 _lock = threading.Lock()
 _lib = None
@@ -167,6 +184,20 @@ def load(build_if_missing: bool = True):
         lib.mdp_batch_solve.restype = ctypes.c_int
         lib.mdp_pool_trim.argtypes = [I32, U64, ctypes.POINTER(U64)]
         lib.mdp_pool_trim.restype = ctypes.c_int
+        HP = ctypes.POINTER(mdp_host_csr)
+        lib.mdp_csr_from_functions.argtypes = [I64, I32, MDP_ROW_FN, MDP_COST_FN, P, I32,
+                                               MDP_ALLOC_FN, P, HP]
+        lib.mdp_csr_from_functions.restype = ctypes.c_int
+        lib.mdp_csr_from_samples.argtypes = [I64, I32, I64, P, P, P, P, I32, D, I32,
+                                             MDP_ALLOC_FN, P, HP]
+        lib.mdp_csr_from_samples.restype = ctypes.c_int
+        lib.mdp_csr_read_petsc.argtypes = [ctypes.c_char_p, ctypes.c_char_p, I32, MDP_ALLOC_FN,
+                                           P, HP]
+        lib.mdp_csr_read_petsc.restype = ctypes.c_int
+        lib.mdp_csr_write_petsc.argtypes = [HP, ctypes.c_char_p, ctypes.c_char_p]
+        lib.mdp_csr_write_petsc.restype = ctypes.c_int
+        lib.mdp_csr_free.argtypes = [HP]
+        lib.mdp_csr_free.restype = None
         lib.mdp_last_error.argtypes = []
         lib.mdp_last_error.restype = ctypes.c_char_p
         lib.mdp_version.argtypes = []
@@ -329,3 +360,45 @@ def mdp_batch_solve(handles, V_outs, pi_outs=None, opts=None, n_streams=8,
         _check(rc)
     return [st[i].as_dict() for i in range(count)], [STATUS_NAMES.get(status[i], status[i])
                                                      for i in range(count)]
+
+
+def _path(p):
+    return None if p is None else os.fsencode(p)
+
+
+def _alloc_fn(alloc):
+    return alloc if alloc is not None else MDP_ALLOC_FN()
+
+
+def mdp_csr_from_functions(n_states, n_actions, row_fn, cost_fn, threads=1, alloc=None):
+    """row_fn / cost_fn: MDP_ROW_FN / MDP_COST_FN objects; alloc: an MDP_ALLOC_FN
+    or None (malloc; release with mdp_csr_free).  Returns the mdp_host_csr."""
+    out = mdp_host_csr()
+    _check(load().mdp_csr_from_functions(int(n_states), int(n_actions), row_fn, cost_fn, None,
+                                         int(threads), _alloc_fn(alloc), None, ctypes.byref(out)))
+    return out
+
+
+def mdp_csr_from_samples(n_states, n_actions, s, a, s_next, c=None, unseen=MDP_UNSEEN_ERROR,
+                         unseen_cost=0.0, threads=0, alloc=None):
+    """s, s_next int64 and a int32 arrays (c float64 or None) of one length."""
+    out = mdp_host_csr()
+    _check(load().mdp_csr_from_samples(int(n_states), int(n_actions), len(s), _ptr(s), _ptr(a),
+                                       _ptr(s_next), _ptr(c), int(unseen), float(unseen_cost),
+                                       int(threads), _alloc_fn(alloc), None, ctypes.byref(out)))
+    return out
+
+
+def mdp_csr_read_petsc(p_path, g_path=None, threads=0, alloc=None):
+    out = mdp_host_csr()
+    _check(load().mdp_csr_read_petsc(_path(p_path), _path(g_path), int(threads),
+                                     _alloc_fn(alloc), None, ctypes.byref(out)))
+    return out
+
+
+def mdp_csr_write_petsc(csr, p_path, g_path=None):
+    _check(load().mdp_csr_write_petsc(ctypes.byref(csr), _path(p_path), _path(g_path)))
+
+
+def mdp_csr_free(csr):
+    load().mdp_csr_free(ctypes.byref(csr))

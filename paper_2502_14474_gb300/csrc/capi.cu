@@ -119,6 +119,7 @@ struct mdp_s {
   int32_t min_len = 0, max_len = 0;
   int aligned = 0;
   int32_t store_t = MDP_F32;
+  int neg = 0;  // MDP_FLAG_MAXIMIZE: costs are -rewards, V is kept as -V
   int32_t val_t = MDP_F32;
   Prof prof;
   int64_t launches = 0;
@@ -755,6 +756,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
     return fail(MDP_ERR_ARG, "store_t must be MDP_F32, MDP_BF16 or MDP_F16");
   if (!(gamma >= 0.0 && gamma < 1.0)) return fail(MDP_ERR_ARG, "gamma must be in [0, 1)");
   const bool host_in = (flags & MDP_FLAG_HOST_INPUT) != 0;
+  const int neg = (flags & MDP_FLAG_MAXIMIZE) ? 1 : 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t rows = n * m;
 
@@ -884,11 +886,11 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
     // against the packed copy
     CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
     CCK(launch_prep_rows(n, m, nnz, rp_in, nullptr, nullptr, val_t == MDP_F64, h->pk, h->val_lo,
-                         g_in, cost_t == MDP_F64, tol, h->rp, idx64, h->g, h->g_lo, dflags,
+                         g_in, cost_t == MDP_F64, neg, tol, h->rp, idx64, h->g, h->g_lo, dflags,
                          num_sms, s));
   } else {
     CCK(launch_prep_rows(n, m, nnz, rp_in, col_in, val_in, val_t == MDP_F64, nullptr, nullptr,
-                         g_in, cost_t == MDP_F64, tol, h->rp, idx64, h->g, h->g_lo, dflags,
+                         g_in, cost_t == MDP_F64, neg, tol, h->rp, idx64, h->g, h->g_lo, dflags,
                          num_sms, s));
     CCK(launch_pack(nnz, col_in, val_in, val_t == MDP_F64, h->pk, h->val_lo, num_sms, s));
   }
@@ -950,6 +952,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   if (getenv("MDP_NO_WINDOW")) A.window = 0;
 
   h->store_t = store_t;
+  h->neg = neg;
   A.store_t = store_t;
   const bool lp_store = store_t == MDP_BF16 || store_t == MDP_F16;
   // Short rows (one thread per row, no aligned 16-byte slices) read by the
@@ -1035,6 +1038,7 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
   info->band = h->band;
   info->has_low_precision = (h->val16 != nullptr || h->lpk != nullptr) ? 1 : 0;
   info->store_t = h->store_t;
+  info->maximize = h->neg;
   info->device_bytes = h->bytes;
   info->gamma = h->A.gamma;
   return MDP_OK;
@@ -1051,20 +1055,34 @@ mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DoneMark dm{h, s};
   if (v_t == MDP_F32) {
+    // a maximising handle backs up -V_in (kept in W1) and negates V_out, r_out
+    const void* vin = V_in;
+    if (h->neg) {
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+           return launch_negate(h->A.n, V_in, h->W1, 0, h->A.num_sms, s);
+         }));
+      vin = h->W1;
+    }
     CK(h, run(h, s, MDP_PROF_BELLMAN_F32, 1, bytes_bellman(h->A, false, V_out != nullptr), -1, [&] {
-         return launch_bellman(h->A, false, V_in, V_out, pi_out, r_out, h->partials, h->st, 0, s);
+         return launch_bellman(h->A, false, vin, V_out, pi_out, r_out, h->partials, h->st, 0, s);
        }));
+    if (h->neg && V_out)
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+                [&] { return launch_negate(h->A.n, V_out, V_out, 0, h->A.num_sms, s); }));
   } else {
     CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
-              [&] { return launch_to_ff(h->A.n, V_in, 1, h->W1, h->A.num_sms, s); }));
+              [&] { return launch_to_ff(h->A.n, V_in, 1, h->neg, h->W1, h->A.num_sms, s); }));
     CK(h, run(h, s, MDP_PROF_BELLMAN_FF, 1, bytes_bellman(h->A, true, V_out != nullptr), -1, [&] {
          return launch_bellman(h->A, true, h->W1, V_out ? h->W2 : nullptr, pi_out, r_out,
                                h->partials, h->st, 0, s);
        }));
     if (V_out)
       CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
-                [&] { return launch_from_ff(h->A.n, h->W2, V_out, 1, h->A.num_sms, s); }));
+                [&] { return launch_from_ff(h->A.n, h->W2, V_out, 1, h->neg, h->A.num_sms, s); }));
   }
+  if (h->neg && r_out)
+    CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+              [&] { return launch_negate(h->A.n, r_out, r_out, 0, h->A.num_sms, s); }));
   mark_done(h, s);
   if (res_inf || res_2) {
     mdp_status rc = read_head(h, s);
@@ -1094,7 +1112,7 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
   rc = ensure_basis(h, restart, s);
   if (rc != MDP_OK) return rc;
   CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
-       return launch_to_ff(h->A.n, v_inout, v_t == MDP_F64, h->V, h->A.num_sms, s);
+       return launch_to_ff(h->A.n, v_inout, v_t == MDP_F64, h->neg, h->V, h->A.num_sms, s);
      }));
   rc = set_cycle(h, restart, 0, 0.0, tol, 1, s);
   if (rc != MDP_OK) return rc;
@@ -1144,7 +1162,7 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
   es.residual_2 = res;
   es.converged = res <= tol;
   CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
-       return launch_from_ff(h->A.n, h->V, v_inout, v_t == MDP_F64, h->A.num_sms, s);
+       return launch_from_ff(h->A.n, h->V, v_inout, v_t == MDP_F64, h->neg, h->A.num_sms, s);
      }));
   mark_done(h, s);
   CK(h, cudaStreamSynchronize(s));
@@ -1183,7 +1201,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   const Mat& A = h->A;
   if (V_init)
     CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
-         return launch_to_ff(A.n, V_init, vinit_t == MDP_F64, h->V, A.num_sms, s);
+         return launch_to_ff(A.n, V_init, vinit_t == MDP_F64, h->neg, h->V, A.num_sms, s);
        }));
   else CK(h, cudaMemsetAsync(h->V, 0, static_cast<size_t>(A.n) * sizeof(float2), s));
   rc = set_cycle(h, o.restart, 1, o.inner_rtol, 0.0, 0, s);
@@ -1305,7 +1323,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
     if (ss.outer_iters - 1 < MDP_HISTORY) ss.inner_history[ss.outer_iters - 1] = used;
   }
   CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
-            [&] { return launch_from_ff(A.n, h->V, V_out, 1, A.num_sms, s); }));
+            [&] { return launch_from_ff(A.n, h->V, V_out, 1, h->neg, A.num_sms, s); }));
   if (pi_out)
     CK(h, cudaMemcpyAsync(pi_out, h->pi, static_cast<size_t>(A.n) * sizeof(int32_t),
                           cudaMemcpyDeviceToDevice, s));

@@ -278,28 +278,48 @@ __global__ void k_ff_axpy(int64_t n, float2* __restrict__ V, const float* __rest
   }
 }
 
-__global__ void k_to_ff(int64_t n, const void* __restrict__ src, int f64, float2* __restrict__ dst) {
+// Caller vector -> float-float iterate.  neg: the handle maximises rewards and
+// works on -V internally (negation is exact, so the split of -v is the negated
+// split of v).
+__global__ void k_to_ff(int64_t n, const void* __restrict__ src, int f64, int neg,
+                        float2* __restrict__ dst) {
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
        s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     if (f64) {
-      const double v = static_cast<const double*>(src)[s];
+      const double v0 = static_cast<const double*>(src)[s];
+      const double v = neg ? -v0 : v0;
       const float hi = static_cast<float>(v);
       dst[s] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
     } else {
-      dst[s] = make_float2(static_cast<const float*>(src)[s], 0.f);
+      const float v0 = static_cast<const float*>(src)[s];
+      dst[s] = make_float2(neg ? -v0 : v0, 0.f);
     }
   }
 }
 
+// Float-float iterate -> caller vector; neg as in k_to_ff (the rounded sum is
+// negated, which equals the rounded sum of the negated parts).
 __global__ void k_from_ff(int64_t n, const float2* __restrict__ src, void* __restrict__ dst,
-                          int f64) {
+                          int f64, int neg) {
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
        s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float2 v = src[s];
-    if (f64)
-      static_cast<double*>(dst)[s] = static_cast<double>(v.x) + static_cast<double>(v.y);
-    else
-      static_cast<float*>(dst)[s] = __fadd_rn(v.x, v.y);
+    if (f64) {
+      const double r = static_cast<double>(v.x) + static_cast<double>(v.y);
+      static_cast<double*>(dst)[s] = neg ? -r : r;
+    } else {
+      const float r = __fadd_rn(v.x, v.y);
+      static_cast<float*>(dst)[s] = neg ? -r : r;
+    }
+  }
+}
+
+// dst = -src elementwise (FP32 or FP64); dst may equal src.
+__global__ void k_negate(int64_t n, const void* src, void* dst, int f64) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (f64) static_cast<double*>(dst)[s] = -static_cast<const double*>(src)[s];
+    else static_cast<float*>(dst)[s] = -static_cast<const float*>(src)[s];
   }
 }
 
@@ -374,15 +394,21 @@ cudaError_t launch_ff_axpy(int64_t n, float2* V, const float* d, int num_sms, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, float2* dst, int num_sms,
-                         cudaStream_t s) {
-  k_to_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, src_f64, dst);
+cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, int neg, float2* dst,
+                         int num_sms, cudaStream_t s) {
+  k_to_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, src_f64, neg, dst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int num_sms,
-                           cudaStream_t s) {
-  k_from_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, dst, dst_f64);
+cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int neg,
+                           int num_sms, cudaStream_t s) {
+  k_from_ff<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, dst, dst_f64, neg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_negate(int64_t n, const void* src, void* dst, int f64, int num_sms,
+                          cudaStream_t s) {
+  k_negate<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, dst, f64);
   return cudaGetLastError();
 }
 

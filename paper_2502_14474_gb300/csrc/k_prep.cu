@@ -24,7 +24,7 @@ __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __
                             const int32_t* __restrict__ col, const void* __restrict__ val,
                             int val_f64, const uint32_t* __restrict__ pk,
                             const float* __restrict__ pk_lo, const void* __restrict__ g_in,
-                            int g_f64, double tol, void* __restrict__ rp_out, int idx64,
+                            int g_f64, int g_neg, double tol, void* __restrict__ rp_out, int idx64,
                             float* __restrict__ g_out, float* __restrict__ g_lo_out,
                             PrepFlags* __restrict__ flags) {
   const int64_t rows = n * m;
@@ -79,8 +79,9 @@ __global__ void k_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* __
     const double err = fabs(sum - 1.0);
     if (!(err <= tol)) not_stoch = 1;
     if (isfinite(err)) max_err = fmax(max_err, err);
-    const double gv = g_f64 ? static_cast<const double*>(g_in)[r]
-                            : static_cast<double>(static_cast<const float*>(g_in)[r]);
+    const double g_raw = g_f64 ? static_cast<const double*>(g_in)[r]
+                               : static_cast<double>(static_cast<const float*>(g_in)[r]);
+    const double gv = g_neg ? -g_raw : g_raw;  // rewards of a maximisation: g = -r, exact
     if (!isfinite(gv)) nonfinite = 1;
     const float ghi = static_cast<float>(gv);
     g_out[r] = ghi;
@@ -195,11 +196,11 @@ static unsigned grid_of(int64_t work, int num_sms) {
 cudaError_t launch_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* rp_in,
                              const int32_t* col_in, const void* val_in, int val_f64,
                              const uint32_t* pk, const float* pk_lo, const void* g_in, int g_f64,
-                             double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
-                             PrepFlags* flags, int num_sms, cudaStream_t s) {
+                             int g_neg, double tol, void* rp_out, int idx64, float* g_out,
+                             float* g_lo_out, PrepFlags* flags, int num_sms, cudaStream_t s) {
   k_prep_rows<<<grid_of(n * m, num_sms), 256, 0, s>>>(n, m, nnz, rp_in, col_in, val_in, val_f64,
-                                                      pk, pk_lo, g_in, g_f64, tol, rp_out, idx64,
-                                                      g_out, g_lo_out, flags);
+                                                      pk, pk_lo, g_in, g_f64, g_neg, tol, rp_out,
+                                                      idx64, g_out, g_lo_out, flags);
   return cudaGetLastError();
 }
 

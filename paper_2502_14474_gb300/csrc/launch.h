@@ -102,11 +102,15 @@ cudaError_t launch_richardson(const Mat& A, bool lp, const int32_t* pi, const fl
 // V += d (float-float V, FP32 d).
 cudaError_t launch_ff_axpy(int64_t n, float2* V, const float* d, int num_sms, cudaStream_t s);
 
-// Conversions between caller vectors and the float-float iterate.
-cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, float2* dst, int num_sms,
-                         cudaStream_t s);
-cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int num_sms,
-                           cudaStream_t s);
+// Conversions between caller vectors and the float-float iterate; neg = 1
+// negates on the way (a maximising handle keeps -V internally).
+cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, int neg, float2* dst,
+                         int num_sms, cudaStream_t s);
+cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int neg,
+                           int num_sms, cudaStream_t s);
+// dst = -src (FP32 or FP64 vector of n entries); dst may equal src.
+cudaError_t launch_negate(int64_t n, const void* src, void* dst, int f64, int num_sms,
+                          cudaStream_t s);
 
 // Matrix preparation (mdp_create).
 struct PrepFlags {
@@ -141,8 +145,8 @@ cudaError_t launch_build_am(const Mat& A, uint32_t* pk_am, int32_t L, cudaStream
 cudaError_t launch_prep_rows(int64_t n, int32_t m, int64_t nnz, const int64_t* rp_in,
                              const int32_t* col_in, const void* val_in, int val_f64,
                              const uint32_t* pk, const float* pk_lo, const void* g_in, int g_f64,
-                             double tol, void* rp_out, int idx64, float* g_out, float* g_lo_out,
-                             PrepFlags* flags, int num_sms, cudaStream_t s);
+                             int g_neg, double tol, void* rp_out, int idx64, float* g_out,
+                             float* g_lo_out, PrepFlags* flags, int num_sms, cudaStream_t s);
 // Interleave col/val into the packed layout (groups of 4 entries, 32 bytes).
 cudaError_t launch_pack(int64_t nnz, const int32_t* col_in, const void* val_in, int val_f64,
                         uint32_t* pk, float* val_lo_out, int num_sms, cudaStream_t s);

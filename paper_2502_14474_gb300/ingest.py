@@ -1,0 +1,172 @@
+"""Building MDPs for the solver from a simulator, from logged transitions or
+from PETSc binary files (include/mdp_ingest.h; host-side, no GPU needed).
+
+The madupite paper (section "Implementation") creates an MDP by loading
+offline data from earlier experiments or from online simulation, and stores it
+in PETSc matrices.  The functions here return a ``HostMDP`` in the layout that
+``MDP.from_csr`` takes (row r = s*m + a of an (n*m) x n CSR matrix).  The
+arrays are numpy arrays whose memory the library filled through an allocator
+callback; with ``pinned=True`` that memory is page-locked (PyTorch's pinned
+host allocator), so that ``MDP.from_csr(mdp, host_input=True)`` reads it in
+place over the host link.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import capi
+
+
+@dataclasses.dataclass
+class HostMDP:
+    """A CSR MDP in host memory: ``row_ptr`` int64[n*m+1], ``col`` int32[nnz],
+    ``val`` float64[nnz], ``g`` float64[n*m] (costs, or rewards when
+    ``maximize``), discount ``gamma``."""
+
+    n: int
+    m: int
+    gamma: float
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    g: np.ndarray
+    maximize: bool = False
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    @property
+    def rows(self) -> int:
+        return self.n * self.m
+
+
+class _Allocator:
+    """The allocator callback: hands the library numpy buffers (page-locked
+    ones when pinned) and keeps them by address."""
+
+    def __init__(self, pinned: bool = False):
+        self.pinned = pinned
+        self.bufs = {}
+        self.fn = capi.MDP_ALLOC_FN(self._alloc)
+
+    def _alloc(self, nbytes, _user):
+        try:
+            if self.pinned:
+                import torch
+                arr = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True).numpy()
+            else:
+                arr = np.empty(int(nbytes), dtype=np.uint8)
+            self.bufs[arr.ctypes.data] = arr
+            return arr.ctypes.data
+        except Exception:  # noqa: BLE001 -- a NULL return is the library's OOM signal
+            return None
+
+    def array(self, addr, dtype, count):
+        return self.bufs[addr][: count * np.dtype(dtype).itemsize].view(dtype)
+
+
+def _host_mdp(out, al: _Allocator, gamma, maximize) -> HostMDP:
+    n, m, nnz = int(out.n_states), int(out.n_actions), int(out.nnz)
+    return HostMDP(n=n, m=m, gamma=float(gamma),
+                   row_ptr=al.array(out.row_ptr, np.int64, n * m + 1),
+                   col=al.array(out.col, np.int32, nnz), val=al.array(out.val, np.float64, nnz),
+                   g=al.array(out.cost, np.float64, n * m), maximize=bool(maximize))
+
+
+def from_functions(n, m, transitions, cost, gamma, threads=1, maximize=False,
+                   pinned=False) -> HostMDP:
+    """Evaluate ``transitions(s, a) -> (successors, probabilities)`` and
+    ``cost(s, a) -> float`` for every state-action pair (online simulation).
+
+    Repeated successors are summed and each row is sorted by successor.  With
+    threads > 1 the callables are called from several threads (they hold the
+    interpreter lock while they run).  An exception raised by a callable is
+    re-raised here.
+    """
+    errors = []
+
+    def row(s, a, cap, col_p, prob_p, _user):
+        try:
+            succ, prob = transitions(int(s), int(a))
+            c = np.asarray(succ, dtype=np.int64).reshape(-1)
+            p = np.asarray(prob, dtype=np.float64).reshape(-1)
+            if c.shape != p.shape:
+                raise ValueError(f"transitions({s}, {a}): {c.size} successors, "
+                                 f"{p.size} probabilities")
+            k = c.size
+            if 0 < k <= cap:
+                # a successor outside int32 reaches the library as -2^31 (reported there)
+                big = (c < -2**31) | (c > 2**31 - 1)
+                np.ctypeslib.as_array(col_p, (k,))[:] = np.where(big, -2**31, c)
+                np.ctypeslib.as_array(prob_p, (k,))[:] = p
+            return k
+        except BaseException as e:  # noqa: BLE001 -- carried across the C boundary
+            errors.append(e)
+            return -1
+
+    def cst(s, a, _user):
+        try:
+            return float(cost(int(s), int(a)))
+        except BaseException as e:  # noqa: BLE001
+            errors.append(e)
+            return float("nan")
+
+    row_fn, cost_fn = capi.MDP_ROW_FN(row), capi.MDP_COST_FN(cst)
+    al = _Allocator(pinned)
+    try:
+        out = capi.mdp_csr_from_functions(n, m, row_fn, cost_fn, threads=threads, alloc=al.fn)
+    except capi.MDPError:
+        if errors:
+            raise errors[0] from None
+        raise
+    return _host_mdp(out, al, gamma, maximize)
+
+
+def from_samples(n, m, s, a, s_next, cost=None, gamma=0.99, unseen="error", unseen_cost=0.0,
+                 threads=0, maximize=False, pinned=False) -> HostMDP:
+    """The maximum-likelihood MDP of logged transitions (s[i], a[i]) -> s_next[i]
+    with cost cost[i]: P(s'|s,a) = N(s,a,s')/N(s,a), g(s,a) = mean cost.
+    ``unseen``: "error" or "self_loop" (P(s|s,a) = 1 at ``unseen_cost``) for
+    pairs without a sample."""
+    s = np.ascontiguousarray(s, dtype=np.int64)
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    s_next = np.ascontiguousarray(s_next, dtype=np.int64)
+    if not (s.shape == a.shape == s_next.shape) or s.ndim != 1:
+        raise ValueError("s, a and s_next must be 1-D arrays of one length")
+    c = None if cost is None else np.ascontiguousarray(cost, dtype=np.float64)
+    if c is not None and c.shape != s.shape:
+        raise ValueError("cost must have one entry per sample")
+    mode = {"error": capi.MDP_UNSEEN_ERROR, "self_loop": capi.MDP_UNSEEN_SELF_LOOP}[unseen]
+    al = _Allocator(pinned)
+    out = capi.mdp_csr_from_samples(n, m, s, a, s_next, c, unseen=mode, unseen_cost=unseen_cost,
+                                    threads=threads, alloc=al.fn)
+    return _host_mdp(out, al, gamma, maximize)
+
+
+def read_petsc(p_path, g_path=None, gamma=0.99, threads=0, maximize=False,
+               pinned=False) -> HostMDP:
+    """Load P ((n*m) x n sparse) and g (n x m, dense or sparse) from PETSc
+    binary files; g_path None gives zero costs."""
+    al = _Allocator(pinned)
+    out = capi.mdp_csr_read_petsc(p_path, g_path, threads=threads, alloc=al.fn)
+    return _host_mdp(out, al, gamma, maximize)
+
+
+def write_petsc(mdp, p_path, g_path=None) -> None:
+    """Write an object with n, m, row_ptr, col, val, g as PETSc binary files."""
+    rp = np.ascontiguousarray(mdp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(mdp.col, dtype=np.int32)
+    val = np.ascontiguousarray(mdp.val, dtype=np.float64)
+    g = np.ascontiguousarray(mdp.g, dtype=np.float64)
+    if rp.shape != (mdp.n * mdp.m + 1,) or g.shape != (mdp.n * mdp.m,):
+        raise ValueError("row_ptr must have n*m+1 entries and g n*m")
+    if col.shape != val.shape or col.size < int(rp[-1]):
+        raise ValueError("col and val must hold row_ptr[-1] entries")
+    c = capi.mdp_host_csr(n_states=mdp.n, n_actions=mdp.m, nnz=int(rp[-1]),
+                          row_ptr=rp.ctypes.data, col=col.ctypes.data, val=val.ctypes.data,
+                          cost=g.ctypes.data, owned=0)
+    capi.mdp_csr_write_petsc(c, p_path, g_path)

@@ -1,10 +1,11 @@
 """Host-side checks of the C ABI library (no GPU needed).
 
 The library is built for sm_103a with nvcc (cross-compiles here) and loaded
-with ctypes; every function include/mdp.h declares must be exported.  Only
+with ctypes; every function include/*.h declares must be exported.  Only
 calls that do no device work are made.
 """
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -16,10 +17,11 @@ HEADER = os.path.join(ROOT, "include", "mdp.h")
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(mdp_[a-z_0-9]+)\s*\(", src)
-    return sorted(set(names))
+    names = set()
+    for header in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(header).read(), flags=re.S)
+        names.update(re.findall(r"\b(mdp_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
