@@ -67,10 +67,10 @@ def _args():
     p.add_argument("--store", choices=["f32", "bf16", "f16"], default="f32",
                    help="probabilities of the inner GMRES SpMV")
     p.add_argument("--inner-norm", choices=["2", "inf"], default="2")
-    p.add_argument("--inner", choices=["gmres", "richardson"], default="gmres",
-                   help="inner solver of the evaluation step: GMRES (iPI) or Richardson "
+    p.add_argument("--inner", choices=["gmres", "richardson", "bicgstab"], default="gmres",
+                   help="inner solver of the evaluation step: GMRES (iPI), Richardson "
                         "sweeps (modified policy iteration; with --max-inner 1 it is value "
-                        "iteration)")
+                        "iteration) or BiCGStab")
     p.add_argument("--max-inner", type=int, default=None,
                    help="cap on GMRES steps per outer iteration (default 10000; 100 for "
                         "grid4096, whose early policies make the evaluation nearly singular)")
@@ -560,6 +560,7 @@ def main():
                        "gamma": host.gamma, "seed": 2 if args.workload == "banded4m" else 3,
                        "tol": args.tol,
                        "inner": (f"gmres({args.restart})" if args.inner == "gmres"
+                                 else "bicgstab" if args.inner == "bicgstab"
                                  else ("value iteration" if args.max_inner == 1
                                        else "richardson (modified PI)")),
                        "eta": 0.1,

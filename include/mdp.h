@@ -92,7 +92,9 @@ typedef enum {
  * range of inner solvers for the approximate policy evaluation step"). */
 typedef enum {
   MDP_INNER_GMRES = 0,      /* restarted GMRES(restart), the default */
-  MDP_INNER_RICHARDSON = 1  /* v <- g_pi + gamma P_pi v sweeps: modified policy iteration */
+  MDP_INNER_RICHARDSON = 1, /* v <- g_pi + gamma P_pi v sweeps: modified policy iteration */
+  MDP_INNER_BICGSTAB = 2    /* BiCGStab (van der Vorst 1992) on the FP32 probabilities:
+                               two policy SpMVs per iteration, no restart, no basis */
 } mdp_inner;
 
 typedef struct {
@@ -101,10 +103,12 @@ typedef struct {
                            <= eta * ||T V - V||_inf, default 0.1 */
   int32_t restart;      /* GMRES restart length, 1..64, default 30 */
   int32_t max_outer;    /* outer (improvement) iterations, default 1000 */
-  int32_t max_inner;    /* inner iterations (Arnoldi steps or sweeps) per outer, default 10000 */
+  int32_t max_inner;    /* inner iterations (Arnoldi steps, sweeps or BiCGStab
+                           iterations) per outer, default 10000 */
   int32_t inner;        /* mdp_inner, default MDP_INNER_GMRES */
   int32_t cgs2;         /* 1 = re-orthogonalise once (classical Gram-Schmidt twice) */
-  int32_t low_precision_inner; /* 1 = inner SpMV on the BF16/FP16 copy (needs store_t) */
+  int32_t low_precision_inner; /* 1 = inner SpMV on the BF16/FP16 copy (needs store_t;
+                                  GMRES and Richardson; BiCGStab always uses FP32) */
   int32_t inner_norm;   /* 0: stop the inner GMRES on its 2-norm residual estimate
                            <= eta * ||T V - V||_inf (default, conservative);
                            1: additionally stop after any restart cycle whose explicit
@@ -269,6 +273,7 @@ enum {
   MDP_PROF_RICHARDSON = 6,   /* modified-PI sweep */
   MDP_PROF_OTHER = 7,        /* conversions, set-up kernels */
   MDP_PROF_ARNOLDI_DOTS = 8, /* Gram-Schmidt dots <w, v_i> */
+  MDP_PROF_BICGSTAB_SPMV = 9,/* BiCGStab policy SpMV y = x - gamma P_pi x with its dots */
   MDP_PROF_KINDS = 12
 };
 

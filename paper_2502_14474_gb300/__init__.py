@@ -157,12 +157,15 @@ class MDP:
     def solve(self, tol=1e-9, inner_rtol=0.1, restart=30, max_outer=1000, max_inner=10000,
               inner="gmres", cgs2=False, low_precision_inner=None, V_init=None,
               raise_on_not_converged=True, inner_norm="2"):
-        """Inexact policy iteration; returns (V float64, pi int32, stats dict)."""
+        """Inexact policy iteration; returns (V float64, pi int32, stats dict).
+        ``inner``: "gmres" (default), "richardson" (modified policy iteration) or
+        "bicgstab"."""
         torch = _torch()
         o = mdp_default_opts()
         o.tol, o.inner_rtol, o.restart = float(tol), float(inner_rtol), int(restart)
         o.max_outer, o.max_inner = int(max_outer), int(max_inner)
-        o.inner = MDP_INNER_GMRES if inner == "gmres" else MDP_INNER_RICHARDSON
+        o.inner = {"gmres": MDP_INNER_GMRES, "richardson": MDP_INNER_RICHARDSON,
+                   "bicgstab": capi.MDP_INNER_BICGSTAB}[inner]
         o.cgs2 = 1 if cgs2 else 0
         if low_precision_inner is None:
             low_precision_inner = self.store != "f32"

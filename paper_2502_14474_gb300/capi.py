@@ -23,7 +23,7 @@ MDP_FLAG_HOST_INPUT = 0x1
 MDP_FLAG_NO_VALIDATE = 0x2
 MDP_FLAG_AUTOTUNE = 0x4
 MDP_FLAG_MAXIMIZE = 0x8
-MDP_INNER_GMRES, MDP_INNER_RICHARDSON = 0, 1
+MDP_INNER_GMRES, MDP_INNER_RICHARDSON, MDP_INNER_BICGSTAB = 0, 1, 2
 MDP_UNSEEN_ERROR, MDP_UNSEEN_SELF_LOOP = 0, 1
 MDP_HISTORY = 128
 
@@ -36,7 +36,7 @@ EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval"
                    "mdp_csr_write_petsc", "mdp_csr_free"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
-              "gmres_update", "richardson", "other", "arnoldi_dots", "unused9", "unused10",
+              "gmres_update", "richardson", "other", "arnoldi_dots", "bicgstab_spmv", "unused10",
               "unused11"]
 
 

@@ -107,8 +107,9 @@ struct mdp_s {
   float* basis = nullptr;   // (restart_cap + 1) x ld
   int64_t ld = 0;
   int restart_cap = 0;
-  float* d0 = nullptr;      // Richardson vectors
+  float* d0 = nullptr;      // Richardson vectors (BiCGStab: x, r)
   float* d1 = nullptr;
+  float* bt = nullptr;      // BiCGStab t = A s
   double* partials = nullptr;
   DevState* st = nullptr;
   int* flag = nullptr;      // policy range check
@@ -323,7 +324,8 @@ double bytes_richardson(const Mat& A, bool lp) {
 
 void free_all(mdp_s* h) {
   void* ptrs[] = {h->rp, h->pk, h->pk_am, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
-                  h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->partials, h->st, h->flag};
+                  h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->bt, h->partials, h->st,
+                  h->flag};
   cudaStream_t fs = free_stream(h->device);
   if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
   for (void* p : ptrs)
@@ -479,6 +481,22 @@ mdp_status ensure_richardson(mdp_s* h, cudaStream_t s) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(MDP_ERR_OOM, "device allocation of the Richardson vectors failed");
+  }
+  return MDP_OK;
+}
+
+// BiCGStab vectors: x and r in the Richardson pair, p and v in W2 (n float2 =
+// 2n floats, free during a solve), r^ = r0 in W1, and t of its own.
+mdp_status ensure_bicgstab(mdp_s* h, cudaStream_t s) {
+  mdp_status rc = ensure_richardson(h, s);
+  if (rc != MDP_OK || h->bt) return rc;
+  const cudaStream_t home = h->home;
+  h->home = s;
+  cudaError_t e = dalloc(h, &h->bt, static_cast<size_t>(h->A.n) * sizeof(float));
+  h->home = home;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, "device allocation of the BiCGStab vector failed");
   }
   return MDP_OK;
 }
@@ -734,7 +752,7 @@ size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, md
     b += static_cast<size_t>(nnz + nnz / 4 + 4) * 4 + static_cast<size_t>(rows) * 4;
   // action-major policy copy of short rows: at most 1.25 nnz padded entries
   if (nnz < 12 * rows) b += static_cast<size_t>(nnz + nnz / 4 + 4) * 8;
-  b += static_cast<size_t>(n) * (8 * 3 + 4 + 8);  // V, W1, W2, pi; Richardson d0, d1
+  b += static_cast<size_t>(n) * (8 * 3 + 4 + 8 + 4);  // V, W1, W2, pi; d0, d1; BiCGStab t
   b += static_cast<size_t>(restart + 1) * ld * 4;
   b += sizeof(DevState) + (1 << 20);
   return b;
@@ -1184,7 +1202,8 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   if (o.restart < 1 || o.restart > kMaxRestart) return fail(MDP_ERR_ARG, "restart in [1, 64]");
   if (!(o.tol >= 0.0) || !(o.inner_rtol > 0.0)) return fail(MDP_ERR_ARG, "bad tolerances");
   if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_ERR_ARG, "bad iteration limits");
-  if (o.inner != MDP_INNER_GMRES && o.inner != MDP_INNER_RICHARDSON)
+  if (o.inner != MDP_INNER_GMRES && o.inner != MDP_INNER_RICHARDSON &&
+      o.inner != MDP_INNER_BICGSTAB)
     return fail(MDP_ERR_ARG, "unknown inner solver");
   if (o.inner_norm != 0 && o.inner_norm != 1) return fail(MDP_ERR_ARG, "inner_norm is 0 or 1");
   const bool lp = o.low_precision_inner != 0;
@@ -1196,7 +1215,8 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   h->cancel.store(0);
   mdp_status rc = MDP_OK;
   if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart, s);
-  else rc = ensure_richardson(h, s);
+  else if (o.inner == MDP_INNER_RICHARDSON) rc = ensure_richardson(h, s);
+  else rc = ensure_bicgstab(h, s);
   if (rc != MDP_OK) return rc;
   const Mat& A = h->A;
   if (V_init)
@@ -1278,6 +1298,59 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
         rc = set_cycle(h, o.restart, 1, o.inner_rtol, 0.0, 0, s);
         if (rc != MDP_OK) return rc;
       }
+    } else if (o.inner == MDP_INNER_BICGSTAB) {
+      // BiCGStab in correction form: (I - gamma P_pi) x = r from x = 0, then V += x,
+      // stopping at ||r_k||_2 <= eta * ||T V - V||_inf.  Iterations (five launches
+      // each) are enqueued eight at a time; every launch returns at once after the
+      // solve met its target or broke down, so the host reads the status once per
+      // batch.  A breakdown keeps the iterate reached so far.
+      const float* rhat = reinterpret_cast<const float*>(h->W1);
+      float* x = h->d0;
+      float* r = h->d1;
+      float* p = reinterpret_cast<float*>(h->W2);
+      float* v = p + A.n;
+      float* t = h->bt;
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1, [&] {
+           return launch_bicg_begin(A.n, rhat, r, p, x, target, h->partials, h->st, A.num_sms,
+                                    s);
+         }));
+      int executed = 0;
+      while (used < o.max_inner) {
+        const int batch = std::min(8, o.max_inner - used);
+        const size_t first = h->prof.pending.size();
+        for (int i = 0; i < batch; ++i) {
+          const int k = executed + i;
+          CK(h, run(h, s, MDP_PROF_BICGSTAB_SPMV, 1, bytes_richardson(A, false), k, [&] {
+               return launch_bicg_spmv(A, h->pi, p, v, rhat, 0, h->partials, h->st, s);
+             }));
+          CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, k, [&] {
+               return launch_bicg_s(A.n, p, v, r, x, h->partials, h->st, A.num_sms, s);
+             }));
+          CK(h, run(h, s, MDP_PROF_BICGSTAB_SPMV, 1, bytes_richardson(A, false), k, [&] {
+               return launch_bicg_spmv(A, h->pi, r, t, r, 1, h->partials, h->st, s);
+             }));
+          CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, k, [&] {
+               return launch_bicg_r(A.n, rhat, t, r, x, h->partials, h->st, A.num_sms, s);
+             }));
+          CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, k, [&] {
+               return launch_bicg_p(A.n, r, v, p, h->st, A.num_sms, s);
+             }));
+        }
+        rc = read_head(h, s, false);
+        if (rc != MDP_OK) return rc;
+        const int now = h->head->jdone;
+        for (size_t i = first; i < h->prof.pending.size(); ++i)
+          if (h->prof.pending[i].j >= now) h->prof.pending[i].skipped = true;
+        prof_flush(h);
+        ss.policy_sweeps += 2 * (now - executed);
+        transitions += 2.0 * policy_nnz * (now - executed);
+        used += now - executed;
+        executed = now;
+        if (!h->head->active) break;
+        if (h->cancel.load()) break;
+      }
+      CK(h, run(h, s, MDP_PROF_OTHER, 1, 0.0, -1,
+                [&] { return launch_ff_axpy(A.n, h->V, x, A.num_sms, s); }));
     } else {
       // modified policy iteration in correction form: d_1 = r, d_{k+1} = r + gamma P_pi d_k;
       // V + d_k equals T_pi^k V, and ||d_{k+1} - d_k||_2 is the residual of d_k.

@@ -544,6 +544,73 @@ __global__ void __launch_bounds__(NT)
 }
 
 // ---------------------------------------------------------------------------
+// BiCGStab (van der Vorst 1992) on (I - gamma P_pi) d = r: the policy SpMV
+// y = x - gamma P_pi x over the FP32 probabilities (row s*m + pi(s) read from
+// the CSR, or from the action-major copy), with <y, w> and <y, y> reduced in a
+// fixed order; the last block turns them into a recurrence scalar:
+//   mode 0: y = v = A p, w = r^  ->  alpha = rho / <r^, v>
+//   mode 1: y = t = A s, w = s   ->  omega = <t, s> / <t, t>
+// A zero or non-finite quotient ends the inner solve (breakdown).
+// ---------------------------------------------------------------------------
+template <typename IdxT, int VW>
+__global__ void __launch_bounds__(kThreads)
+    k_bicg_spmv(Csr<IdxT> P, Grid G, const int32_t* __restrict__ pi,
+                const float* __restrict__ x, float* __restrict__ y,
+                const float* __restrict__ w, int mode, double* __restrict__ partials,
+                DevState* __restrict__ st) {
+  if (!st->active) return;
+  __shared__ double red[kThreads / 32];
+  constexpr int NV = kThreads / VW;
+  const int lane = threadIdx.x % VW;
+  const int vec = threadIdx.x / VW;
+  const bool vec4 = P.vec4 != 0;
+  double d1 = 0.0, d2 = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s = tile * NV + vec;
+    int64_t b = 0, e = 0;
+    if (s < P.n) row_bounds<IdxT>(P.rp, P.uniform_len, policy_row(P, s, __ldg(pi + s)), b, e);
+    float acc = row_dot_f32<VW, float, GatherF32>(P.col, P.val, GatherF32{x}, b, e, lane, vec4);
+    acc = group_sum<VW>(acc);
+    if (lane == 0 && s < P.n) {
+      const float yv = fmaf(-P.gamma, acc, x[s]);
+      y[s] = yv;
+      const double yd = static_cast<double>(yv);
+      d1 += yd * static_cast<double>(w[s]);
+      d2 += yd * yd;
+    }
+  }
+  const double b1 = block_sum_d(d1, red);
+  const double b2 = block_sum_d(d2, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b1;
+    partials[2 * blockIdx.x + 1] = b2;
+  }
+  if (last_block(&st->counter[kCntBicg])) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += kThreads) {
+      s1 += __ldcg(partials + 2 * i);
+      s2 += __ldcg(partials + 2 * i + 1);
+    }
+    s1 = block_sum_d(s1, red);
+    s2 = block_sum_d(s2, red);
+    if (threadIdx.x == 0) {
+      st->counter[kCntBicg] = 0;
+      const double q = mode == 0 ? st->bicg_rho / s1 : s1 / s2;
+      if (!(q != 0.0 && isfinite(q))) {
+        st->breakdown = 1;
+        st->active = 0;
+      } else if (mode == 0) {
+        st->bicg_alpha = q;
+      } else {
+        st->bicg_omega = q;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename IdxT>
@@ -727,6 +794,43 @@ cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2
                                    double* partials, DevState* st, cudaStream_t s) {
   return A.idx64 ? presid_idx<int64_t>(A, pi, V, r, partials, st, s)
                  : presid_idx<int32_t>(A, pi, V, r, partials, st, s);
+}
+
+template <typename IdxT, int VW>
+static cudaError_t bicg_vw(const Mat& A, const int32_t* pi, const float* x, float* y,
+                           const float* w, int mode, double* partials, DevState* st,
+                           cudaStream_t s) {
+  auto kern = k_bicg_spmv<IdxT, VW>;
+  static int occ = occupancy(kern, 0);
+  constexpr int NV = kThreads / VW;
+  const int64_t n_tiles = (A.n + NV - 1) / NV;
+  const Grid G = make_grid(n_tiles, A.num_sms * occ, NV);
+  Csr<IdxT> P = make_csr<IdxT>(A);
+  use_policy_copy(P, A);
+  kern<<<static_cast<unsigned>(n_blocks(G)), kThreads, 0, s>>>(P, G, pi, x, y, w, mode, partials,
+                                                               st);
+  return cudaGetLastError();
+}
+
+template <typename IdxT>
+static cudaError_t bicg_idx(const Mat& A, const int32_t* pi, const float* x, float* y,
+                            const float* w, int mode, double* partials, DevState* st,
+                            cudaStream_t s) {
+  switch (A.vw) {
+    case 1: return bicg_vw<IdxT, 1>(A, pi, x, y, w, mode, partials, st, s);
+    case 2: return bicg_vw<IdxT, 2>(A, pi, x, y, w, mode, partials, st, s);
+    case 4: return bicg_vw<IdxT, 4>(A, pi, x, y, w, mode, partials, st, s);
+    case 8: return bicg_vw<IdxT, 8>(A, pi, x, y, w, mode, partials, st, s);
+    case 16: return bicg_vw<IdxT, 16>(A, pi, x, y, w, mode, partials, st, s);
+    default: return bicg_vw<IdxT, 32>(A, pi, x, y, w, mode, partials, st, s);
+  }
+}
+
+cudaError_t launch_bicg_spmv(const Mat& A, const int32_t* pi, const float* x, float* y,
+                             const float* w, int mode, double* partials, DevState* st,
+                             cudaStream_t s) {
+  return A.idx64 ? bicg_idx<int64_t>(A, pi, x, y, w, mode, partials, st, s)
+                 : bicg_idx<int32_t>(A, pi, x, y, w, mode, partials, st, s);
 }
 
 }  // namespace mdpk

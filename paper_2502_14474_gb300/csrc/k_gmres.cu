@@ -324,6 +324,136 @@ __global__ void k_negate(int64_t n, const void* src, void* dst, int f64) {
 }
 
 // ---------------------------------------------------------------------------
+// BiCGStab vector updates (van der Vorst 1992).  The policy SpMVs and the
+// scalars alpha and omega come from k_bicg_spmv; each kernel here returns at
+// once when the solve is over (DevState::active), so a batch of iterations can
+// be enqueued without reading the status between them.  Reductions are fixed
+// order (per-thread sums over a fixed grid-stride, block sums, last block).
+// ---------------------------------------------------------------------------
+
+// Shared tail: publish two block sums; the last block sums them in block order
+// and hands the totals to `fin` (thread 0 only).
+template <typename Fin>
+__device__ __forceinline__ void bicg_reduce2(double a, double b, double* partials,
+                                             DevState* st, Fin fin) {
+  __shared__ double red[kThreads / 32];
+  const double ba = block_sum_d(a, red);
+  const double bb = block_sum_d(b, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = ba;
+    partials[2 * blockIdx.x + 1] = bb;
+  }
+  if (last_block(&st->counter[kCntBicg])) {
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += kThreads) {
+      sa += __ldcg(partials + 2 * i);
+      sb += __ldcg(partials + 2 * i + 1);
+    }
+    sa = block_sum_d(sa, red);
+    sb = block_sum_d(sb, red);
+    if (threadIdx.x == 0) {
+      st->counter[kCntBicg] = 0;
+      fin(sa, sb);
+    }
+  }
+}
+
+// r = p = r0, x = 0, rho = <r0, r0>; the solve starts unless ||r0||_2 <= target.
+__global__ void k_bicg_begin(int64_t n, const float* __restrict__ r0, float* __restrict__ r,
+                             float* __restrict__ p, float* __restrict__ x, double target,
+                             double* __restrict__ partials, DevState* __restrict__ st) {
+  double sq = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float v = r0[i];
+    r[i] = v;
+    p[i] = v;
+    x[i] = 0.f;
+    sq += static_cast<double>(v) * static_cast<double>(v);
+  }
+  bicg_reduce2(sq, 0.0, partials, st, [&](double rr, double) {
+    st->bicg_rho = rr;
+    st->res_2 = sqrt(rr);
+    st->target = target;
+    st->jdone = 0;
+    st->breakdown = 0;
+    const bool done = !(sqrt(rr) > target);
+    st->converged = done ? 1 : 0;
+    st->active = done ? 0 : 1;
+  });
+}
+
+// x += alpha p;  s = r - alpha v (in place of r);  stop when ||s||_2 <= target.
+__global__ void k_bicg_s(int64_t n, const float* __restrict__ p, const float* __restrict__ v,
+                         float* __restrict__ r, float* __restrict__ x,
+                         double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
+  const float alpha = static_cast<float>(st->bicg_alpha);
+  double sq = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    const float sv = fmaf(-alpha, v[i], r[i]);
+    r[i] = sv;
+    sq += static_cast<double>(sv) * static_cast<double>(sv);
+  }
+  bicg_reduce2(sq, 0.0, partials, st, [&](double ss, double) {
+    st->res_2 = sqrt(ss);
+    if (!(sqrt(ss) > st->target)) {
+      st->jdone += 1;
+      st->converged = 1;
+      st->active = 0;
+    }
+  });
+}
+
+// x += omega s;  r = s - omega t;  rho' = <r^, r>;  beta = (rho'/rho)(alpha/omega).
+__global__ void k_bicg_r(int64_t n, const float* __restrict__ rhat, const float* __restrict__ t,
+                         float* __restrict__ r, float* __restrict__ x,
+                         double* __restrict__ partials, DevState* __restrict__ st) {
+  if (!st->active) return;
+  const float omega = static_cast<float>(st->bicg_omega);
+  double d = 0.0, sq = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float sv = r[i];
+    x[i] = fmaf(omega, sv, x[i]);
+    const float rv = fmaf(-omega, t[i], sv);
+    r[i] = rv;
+    d += static_cast<double>(rhat[i]) * static_cast<double>(rv);
+    sq += static_cast<double>(rv) * static_cast<double>(rv);
+  }
+  bicg_reduce2(d, sq, partials, st, [&](double rho_new, double rr) {
+    st->res_2 = sqrt(rr);
+    st->jdone += 1;
+    if (!(sqrt(rr) > st->target)) {
+      st->converged = 1;
+      st->active = 0;
+      return;
+    }
+    const double beta = (rho_new / st->bicg_rho) * (st->bicg_alpha / st->bicg_omega);
+    if (!(rho_new != 0.0 && isfinite(beta))) {
+      st->breakdown = 1;
+      st->active = 0;
+      return;
+    }
+    st->bicg_beta = beta;
+    st->bicg_rho = rho_new;
+  });
+}
+
+// p = r + beta (p - omega v).
+__global__ void k_bicg_p(int64_t n, const float* __restrict__ r, const float* __restrict__ v,
+                         float* __restrict__ p, const DevState* __restrict__ st) {
+  if (!st->active) return;
+  const float beta = static_cast<float>(st->bicg_beta);
+  const float omega = static_cast<float>(st->bicg_omega);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = fmaf(beta, fmaf(-omega, v[i], p[i]), r[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
@@ -409,6 +539,31 @@ cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64,
 cudaError_t launch_negate(int64_t n, const void* src, void* dst, int f64, int num_sms,
                           cudaStream_t s) {
   k_negate<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, src, dst, f64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_begin(int64_t n, const float* r0, float* r, float* p, float* x,
+                              double target, double* partials, DevState* st, int num_sms,
+                              cudaStream_t s) {
+  k_bicg_begin<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, r0, r, p, x, target, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_s(int64_t n, const float* p, const float* v, float* r, float* x,
+                          double* partials, DevState* st, int num_sms, cudaStream_t s) {
+  k_bicg_s<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, p, v, r, x, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_r(int64_t n, const float* rhat, const float* t, float* r, float* x,
+                          double* partials, DevState* st, int num_sms, cudaStream_t s) {
+  k_bicg_r<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, rhat, t, r, x, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_p(int64_t n, const float* r, const float* v, float* p,
+                          const DevState* st, int num_sms, cudaStream_t s) {
+  k_bicg_p<<<ew_blocks(n, num_sms), kThreads, 0, s>>>(n, r, v, p, st);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,21 @@ cudaError_t launch_to_ff(int64_t n, const void* src, int src_f64, int neg, float
                          int num_sms, cudaStream_t s);
 cudaError_t launch_from_ff(int64_t n, const float2* src, void* dst, int dst_f64, int neg,
                            int num_sms, cudaStream_t s);
+// BiCGStab on (I - gamma P_pi) x = r0 (FP32 vectors of n entries, scalars and
+// status in DevState).  One iteration: bicg_spmv(mode 0: v = A p), bicg_s,
+// bicg_spmv(mode 1: t = A s, s kept in r), bicg_r, bicg_p.
+cudaError_t launch_bicg_spmv(const Mat& A, const int32_t* pi, const float* x, float* y,
+                             const float* w, int mode, double* partials, DevState* st,
+                             cudaStream_t s);
+cudaError_t launch_bicg_begin(int64_t n, const float* r0, float* r, float* p, float* x,
+                              double target, double* partials, DevState* st, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_bicg_s(int64_t n, const float* p, const float* v, float* r, float* x,
+                          double* partials, DevState* st, int num_sms, cudaStream_t s);
+cudaError_t launch_bicg_r(int64_t n, const float* rhat, const float* t, float* r, float* x,
+                          double* partials, DevState* st, int num_sms, cudaStream_t s);
+cudaError_t launch_bicg_p(int64_t n, const float* r, const float* v, float* p,
+                          const DevState* st, int num_sms, cudaStream_t s);
 // dst = -src (FP32 or FP64 vector of n entries); dst may equal src.
 cudaError_t launch_negate(int64_t n, const void* src, void* dst, int f64, int num_sms,
                           cudaStream_t s);

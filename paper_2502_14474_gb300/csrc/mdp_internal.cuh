@@ -208,6 +208,7 @@ enum : unsigned {
   kCntDots2 = 4,
   kCntOrtho2 = 5,
   kCntMisc = 6,
+  kCntBicg = 7,
   kNumCounters = 8
 };
 
@@ -237,6 +238,8 @@ struct DevState {
   // eight chunk slots within a group (two-level fixed-order reduction)
   unsigned dots_group[kMaxBasis / 8 + 1];
   unsigned dots_run[kMaxBasis / 8 + 1][kDotsMaxRuns];
+  // BiCGStab scalars (rho = <r^, r>, alpha, omega, beta of the recurrences)
+  double bicg_rho, bicg_alpha, bicg_omega, bicg_beta;
 };
 
 // Initialise a GMRES cycle from ||r0||_2 = beta (single thread).
