@@ -2,10 +2,14 @@
 // from user generators (online simulation), from logged transitions (offline
 // data: the maximum-likelihood model), and from/to PETSc binary matrix files.
 // No CUDA call in this file; every entry point runs on a host without a GPU.
+#include <errno.h>
+#include <fcntl.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
@@ -449,23 +453,43 @@ uint64_t bits_of(double d) {
   return b;
 }
 
+// Positional reads (pread) so that several threads fill disjoint slices of an
+// array at once; `pos` is the offset of the next sequential read.
 struct Reader {
-  FILE* f = nullptr;
+  int fd = -1;
   const char* path = "";
   int64_t size = 0;
+  int64_t pos = 0;
   ~Reader() {
-    if (f) fclose(f);
+    if (fd >= 0) close(fd);
   }
   mdp_status open(const char* p) {
     path = p;
-    f = fopen(p, "rb");
-    if (!f) return ifail(MDP_ERR_ARG, "cannot open %s", p);
-    if (fseeko(f, 0, SEEK_END) != 0 || (size = ftello(f)) < 0 || fseeko(f, 0, SEEK_SET) != 0)
-      return ifail(MDP_ERR_ARG, "cannot seek in %s", p);
+    fd = ::open(p, O_RDONLY);
+    if (fd < 0) return ifail(MDP_ERR_ARG, "cannot open %s", p);
+    struct stat sb;
+    if (fstat(fd, &sb) != 0) return ifail(MDP_ERR_ARG, "cannot stat %s", p);
+    size = static_cast<int64_t>(sb.st_size);
     return MDP_OK;
   }
+  // Read bytes at an absolute offset; false on a short read or an error.
+  bool read_at(void* dst, int64_t bytes, int64_t off) const {
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    while (bytes > 0) {
+      const ssize_t got = pread(fd, d, static_cast<size_t>(std::min<int64_t>(bytes, 1 << 30)),
+                                static_cast<off_t>(off));
+      if (got < 0 && errno == EINTR) continue;
+      if (got <= 0) return false;
+      d += got;
+      off += got;
+      bytes -= got;
+    }
+    return true;
+  }
   bool read(void* dst, int64_t bytes) {
-    return fread(dst, 1, static_cast<size_t>(bytes), f) == static_cast<size_t>(bytes);
+    if (!read_at(dst, bytes, pos)) return false;
+    pos += bytes;
+    return true;
   }
   mdp_status truncated() { return ifail(MDP_ERR_ARG, "%s is truncated", path); }
 };
@@ -502,83 +526,117 @@ mdp_status read_header(Reader& rd, MatHeader* h) {
   return MDP_OK;
 }
 
-// Stream `count` big-endian integers of width w; sink(i, value) sees each one
-// (from T threads, disjoint i).  Returns false on a short read.
+// Read `count` big-endian integers of width w from the current position;
+// sink(i, value) sees each one.  T threads each read and decode a contiguous
+// slice (disjoint i).  Returns false on a short read.
 template <class Sink>
 bool read_ints(Reader& rd, int w, int64_t count, int T, Sink&& sink) {
-  const int64_t chunk = kChunkBytes / w;
-  std::vector<unsigned char> buf(static_cast<size_t>(std::min(count, chunk) * w));
-  for (int64_t base = 0; base < count; base += chunk) {
-    const int64_t k = std::min(chunk, count - base);
-    if (!rd.read(buf.data(), k * w)) return false;
-    parallel_blocks(thread_count(T, k / 4096), k, [&](int, int64_t i0, int64_t i1) {
-      for (int64_t i = i0; i < i1; ++i) {
+  const int64_t base_off = rd.pos;
+  std::atomic<int> short_read{0};
+  parallel_blocks(thread_count(T, count / 65536), count, [&](int, int64_t i0, int64_t i1) {
+    const int64_t chunk = kChunkBytes / 8 / w;  // entries per read
+    std::vector<unsigned char> buf(static_cast<size_t>(std::min(chunk, i1 - i0) * w));
+    for (int64_t b = i0; b < i1; b += chunk) {
+      const int64_t k = std::min(chunk, i1 - b);
+      if (!rd.read_at(buf.data(), k * w, base_off + b * w)) {
+        short_read.store(1);
+        return;
+      }
+      for (int64_t i = 0; i < k; ++i) {
         const unsigned char* p = buf.data() + i * w;
         const int64_t v = w == 4 ? static_cast<int64_t>(static_cast<int32_t>(be32(p)))
                                  : static_cast<int64_t>(be64(p));
-        sink(base + i, v);
+        sink(b + i, v);
       }
-    });
-  }
-  return true;
+    }
+  });
+  rd.pos = base_off + count * w;
+  return short_read.load() == 0;
 }
 
-// Read `count` big-endian doubles into dst; returns false on a short read.
-// *bad receives the lowest index of a NaN/Inf (or -1).
+// Read `count` big-endian doubles into dst (each thread reads its slice in
+// place and converts it); returns false on a short read.  *bad receives the
+// lowest index of a NaN/Inf (or -1).
 bool read_doubles(Reader& rd, int64_t count, int T, double* dst, int64_t* bad) {
+  const int64_t base_off = rd.pos;
   std::atomic<int64_t> first{INT64_MAX};
-  for (int64_t base = 0; base < count; base += kChunkBytes / 8) {
-    const int64_t k = std::min(kChunkBytes / 8, count - base);
-    unsigned char* raw = reinterpret_cast<unsigned char*>(dst + base);
-    if (!rd.read(raw, k * 8)) return false;
-    parallel_blocks(thread_count(T, k / 4096), k, [&](int, int64_t i0, int64_t i1) {
-      for (int64_t i = i0; i < i1; ++i) {
-        const double v = as_double(be64(raw + i * 8));
-        dst[base + i] = v;
-        if (!std::isfinite(v)) lower_limit(first, base + i);
-      }
-    });
-  }
+  std::atomic<int> short_read{0};
+  parallel_blocks(thread_count(T, count / 65536), count, [&](int, int64_t i0, int64_t i1) {
+    unsigned char* raw = reinterpret_cast<unsigned char*>(dst + i0);
+    if (!rd.read_at(raw, (i1 - i0) * 8, base_off + i0 * 8)) {
+      short_read.store(1);
+      return;
+    }
+    for (int64_t i = i0; i < i1; ++i) {
+      const double v = as_double(be64(reinterpret_cast<unsigned char*>(dst + i)));
+      dst[i] = v;
+      if (!std::isfinite(v)) lower_limit(first, i);
+    }
+  });
+  rd.pos = base_off + count * 8;
   *bad = first.load() == INT64_MAX ? -1 : first.load();
-  return true;
+  return short_read.load() == 0;
 }
 
+// Positional writes: every array of the file is encoded by T threads, each
+// turning a contiguous slice into big-endian bytes and writing it at its own
+// offset, so the file is the same whatever the thread count.
 struct Writer {
-  FILE* f = nullptr;
+  int fd = -1;
   const char* path = "";
-  std::vector<unsigned char> buf;
-  size_t used = 0;
-  bool ok = true;
+  std::atomic<bool> ok{true};  // cleared by any thread whose write fails
+  int64_t pos = 0;
   ~Writer() {
-    if (f) fclose(f);
+    if (fd >= 0) close(fd);
   }
   mdp_status open(const char* p) {
     path = p;
-    f = fopen(p, "wb");
-    if (!f) return ifail(MDP_ERR_ARG, "cannot create %s", p);
-    buf.resize(size_t(1) << 20);
+    fd = ::open(p, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+    if (fd < 0) return ifail(MDP_ERR_ARG, "cannot create %s", p);
     return MDP_OK;
   }
-  void flush() {
-    if (used && fwrite(buf.data(), 1, used, f) != used) ok = false;
-    used = 0;
+  void write_at(const unsigned char* src, int64_t bytes, int64_t off) {
+    while (bytes > 0) {
+      const ssize_t put = pwrite(fd, src, static_cast<size_t>(std::min<int64_t>(bytes, 1 << 30)),
+                                 static_cast<off_t>(off));
+      if (put < 0 && errno == EINTR) continue;
+      if (put <= 0) {
+        ok.store(false);
+        return;
+      }
+      src += put;
+      off += put;
+      bytes -= put;
+    }
   }
-  unsigned char* room(size_t k) {
-    if (used + k > buf.size()) flush();
-    unsigned char* p = buf.data() + used;
-    used += k;
-    return p;
+  // Append `count` items, item i encoded by enc(i, p) into `width` bytes at p.
+  template <class Enc>
+  void put_array(int64_t count, int width, Enc&& enc) {
+    const int64_t base = pos;
+    parallel_blocks(thread_count(0, count / 65536), count, [&](int, int64_t i0, int64_t i1) {
+      const int64_t chunk = (int64_t(8) << 20) / width;
+      std::vector<unsigned char> buf(static_cast<size_t>(std::min(chunk, i1 - i0) * width));
+      for (int64_t b = i0; b < i1; b += chunk) {
+        const int64_t k = std::min(chunk, i1 - b);
+        for (int64_t i = 0; i < k; ++i) enc(b + i, buf.data() + i * width);
+        write_at(buf.data(), k * width, base + b * width);
+      }
+    });
+    pos = base + count * width;
   }
-  void put_int(int w, int64_t v) {
-    if (w == 4) put_be32(room(4), static_cast<uint32_t>(static_cast<int32_t>(v)));
-    else put_be64(room(8), static_cast<uint64_t>(v));
+  void put_ints(int w, const int64_t* v, int count) {
+    unsigned char b[32];
+    for (int i = 0; i < count; ++i) {
+      if (w == 4) put_be32(b + 4 * i, static_cast<uint32_t>(static_cast<int32_t>(v[i])));
+      else put_be64(b + 8 * i, static_cast<uint64_t>(v[i]));
+    }
+    write_at(b, static_cast<int64_t>(count) * w, pos);
+    pos += static_cast<int64_t>(count) * w;
   }
-  void put_double(double v) { put_be64(room(8), bits_of(v)); }
-  mdp_status close() {
-    flush();
-    if (fclose(f) != 0) ok = false;
-    f = nullptr;
-    return ok ? MDP_OK : ifail(MDP_ERR_ARG, "write to %s failed", path);
+  mdp_status finish() {
+    const int rc = close(fd);
+    fd = -1;
+    return ok.load() && rc == 0 ? MDP_OK : ifail(MDP_ERR_ARG, "write to %s failed", path);
   }
 };
 
@@ -731,30 +789,38 @@ mdp_status mdp_csr_write_petsc(const mdp_host_csr* c, const char* p_path, const 
     return ifail(MDP_ERR_ARG, "NULL csr or array");
   if (c->n_states < 1 || c->n_actions < 1) return ifail(MDP_ERR_ARG, "empty csr");
   const int64_t n = c->n_states, m = c->n_actions, rows = n * m, nnz = c->row_ptr[rows];
-  if (p_path) {
-    const int w = (rows <= 0x7fffffff && nnz <= 0x7fffffff) ? 4 : 8;
-    Writer wr;
-    mdp_status st = wr.open(p_path);
-    if (st != MDP_OK) return st;
-    wr.put_int(w, kMatClassId);
-    wr.put_int(w, rows);
-    wr.put_int(w, n);
-    wr.put_int(w, nnz);
-    for (int64_t r = 0; r < rows; ++r) wr.put_int(w, c->row_ptr[r + 1] - c->row_ptr[r]);
-    for (int64_t e = 0; e < nnz; ++e) wr.put_int(w, c->col[e]);
-    for (int64_t e = 0; e < nnz; ++e) wr.put_double(c->val[e]);
-    if ((st = wr.close()) != MDP_OK) return st;
-  }
-  if (g_path) {
-    Writer wr;
-    mdp_status st = wr.open(g_path);
-    if (st != MDP_OK) return st;
-    wr.put_int(4, kMatClassId);
-    wr.put_int(4, n);
-    wr.put_int(4, m);
-    wr.put_int(4, kDenseFormat);
-    for (int64_t r = 0; r < rows; ++r) wr.put_double(c->cost[r]);
-    if ((st = wr.close()) != MDP_OK) return st;
+  try {
+    if (p_path) {
+      const int w = (rows <= 0x7fffffff && nnz <= 0x7fffffff) ? 4 : 8;
+      Writer wr;
+      mdp_status st = wr.open(p_path);
+      if (st != MDP_OK) return st;
+      const int64_t head[4] = {kMatClassId, rows, n, nnz};
+      wr.put_ints(w, head, 4);
+      auto put_int = [w](int64_t v, unsigned char* p) {
+        if (w == 4) put_be32(p, static_cast<uint32_t>(static_cast<int32_t>(v)));
+        else put_be64(p, static_cast<uint64_t>(v));
+      };
+      wr.put_array(rows, w, [&](int64_t r, unsigned char* p) {
+        put_int(c->row_ptr[r + 1] - c->row_ptr[r], p);
+      });
+      wr.put_array(nnz, w, [&](int64_t e, unsigned char* p) { put_int(c->col[e], p); });
+      wr.put_array(nnz, 8, [&](int64_t e, unsigned char* p) { put_be64(p, bits_of(c->val[e])); });
+      if ((st = wr.finish()) != MDP_OK) return st;
+    }
+    if (g_path) {
+      Writer wr;
+      mdp_status st = wr.open(g_path);
+      if (st != MDP_OK) return st;
+      const int64_t head[4] = {kMatClassId, n, m, kDenseFormat};
+      wr.put_ints(4, head, 4);
+      wr.put_array(rows, 8, [&](int64_t r, unsigned char* p) { put_be64(p, bits_of(c->cost[r])); });
+      if ((st = wr.finish()) != MDP_OK) return st;
+    }
+  } catch (const std::bad_alloc&) {
+    return ifail(MDP_ERR_OOM, "host allocation failed");
+  } catch (const std::system_error& e) {
+    return ifail(MDP_ERR_ARG, "could not start host threads: %s", e.what());
   }
   return MDP_OK;
 }
