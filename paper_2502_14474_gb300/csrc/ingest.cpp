@@ -97,19 +97,38 @@ int64_t canon_row(int32_t* col, double* val, int64_t k,
       break;
     }
   if (ascending) return k;
-  tmp.resize(static_cast<size_t>(k));
-  for (int64_t i = 0; i < k; ++i) tmp[i] = {col[i], val[i]};
-  std::stable_sort(tmp.begin(), tmp.end(),
-                   [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
-                     return x.first < y.first;
-                   });
+  if (k <= 64) {
+    // short rows: stable insertion sort in place (no allocation)
+    for (int64_t i = 1; i < k; ++i) {
+      const int32_t c = col[i];
+      const double v = val[i];
+      int64_t j = i;
+      for (; j > 0 && col[j - 1] > c; --j) {
+        col[j] = col[j - 1];
+        val[j] = val[j - 1];
+      }
+      col[j] = c;
+      val[j] = v;
+    }
+  } else {
+    tmp.resize(static_cast<size_t>(k));
+    for (int64_t i = 0; i < k; ++i) tmp[i] = {col[i], val[i]};
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [](const std::pair<int32_t, double>& x,
+                        const std::pair<int32_t, double>& y) { return x.first < y.first; });
+    for (int64_t i = 0; i < k; ++i) {
+      col[i] = tmp[i].first;
+      val[i] = tmp[i].second;
+    }
+  }
+  // sum repeated columns (now adjacent) in their original order
   int64_t w = 0;
   for (int64_t i = 0; i < k; ++i) {
-    if (w > 0 && tmp[i].first == col[w - 1]) {
-      val[w - 1] += tmp[i].second;
+    if (w > 0 && col[i] == col[w - 1]) {
+      val[w - 1] += val[i];
     } else {
-      col[w] = tmp[i].first;
-      val[w] = tmp[i].second;
+      col[w] = col[i];
+      val[w] = val[i];
       ++w;
     }
   }
