@@ -21,6 +21,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mdp.h"
 #include "launch.h"
 
@@ -42,6 +44,15 @@ mdp_status fail(mdp_status st, const char* fmt, ...) {
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// NVTX range over a scope: the phases of a call appear by name in a profiler's
+// timeline (nsys, ncu --nvtx); without a profiler attached the calls do nothing.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Prefix of DevState that the host reads back after a synchronisation.
 struct StatusHead {
@@ -762,6 +773,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
                       const int32_t* col, const void* val, mdp_dtype val_t, const void* cost,
                       mdp_dtype cost_t, double gamma, mdp_dtype store_t, void* stream,
                       uint64_t flags) {
+  Range nvtx("mdp_create");
   if (!out) return fail(MDP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n <= 0 || m <= 0) return fail(MDP_ERR_ARG, "n_states and n_actions must be >= 1");
@@ -1064,6 +1076,7 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
 
 mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, int32_t* pi_out,
                        float* r_out, double* res_inf, double* res_2, void* stream) {
+  Range nvtx("mdp_bellman");
   if (!h) return fail(MDP_ERR_ARG, "NULL handle");
   if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
   if (!V_in) return fail(MDP_ERR_ARG, "V_in is NULL");
@@ -1114,6 +1127,7 @@ mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, in
 mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype v_t, double tol,
                            int32_t restart, int32_t max_iters, mdp_eval_stats* stats,
                            void* stream) {
+  Range nvtx("mdp_policy_eval");
   if (!h) return fail(MDP_ERR_ARG, "NULL handle");
   if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
   if (!pi || !v_inout) return fail(MDP_ERR_ARG, "NULL argument");
@@ -1192,6 +1206,7 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
 mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
                      mdp_dtype vinit_t, double* V_out, int32_t* pi_out, mdp_solve_stats* stats,
                      void* stream) {
+  Range nvtx("mdp_solve");
   if (!h) return fail(MDP_ERR_ARG, "NULL handle");
   if (h->broken) return fail(MDP_ERR_CUDA, "handle is broken by an earlier CUDA error");
   if (!V_out) return fail(MDP_ERR_ARG, "V_out is NULL");
@@ -1235,6 +1250,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   double transitions = 0.0;
   mdp_status result = MDP_OK;
   for (int k = 0;; ++k) {
+    Range nvtx_outer("outer iteration");
     // improvement + high-precision residual (+ GMRES cycle start from r)
     float* r_dst = o.inner == MDP_INNER_GMRES ? h->basis : reinterpret_cast<float*>(h->W1);
     CK(h, run(h, s, MDP_PROF_BELLMAN_FF, 1, bytes_bellman(A, true, false), -1, [&] {
@@ -1267,6 +1283,9 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
     ss.outer_iters += 1;
     const double target = o.inner_rtol * res;
     int used = 0;
+    Range nvtx_inner(o.inner == MDP_INNER_GMRES      ? "inner: gmres"
+                     : o.inner == MDP_INNER_BICGSTAB ? "inner: bicgstab"
+                                                     : "inner: richardson");
     if (o.inner == MDP_INNER_GMRES) {
       // the Bellman kernel began the first cycle: target = eta * res_inf
       for (;;) {
@@ -1411,6 +1430,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
 mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts* opts,
                            double* const* V_out, int32_t* const* pi_out, mdp_solve_stats* stats,
                            mdp_status* status_out, int32_t n_streams) {
+  Range nvtx("mdp_batch_solve");
   if (count < 0 || (count > 0 && (!hs || !V_out)))
     return fail(MDP_ERR_ARG, "mdp_batch_solve: bad arguments");
   if (n_streams == 0) n_streams = 8;
