@@ -93,15 +93,21 @@ class Server:
 
     def request_bytes(self, req: Request) -> int:
         """Device bytes a request holds while admitted: the handle
-        (mdp_bytes_required) plus the staging copy of its host CSR during create."""
+        (mdp_bytes_required, for the request's probability dtype), the staging
+        copy of its host CSR during create (row pointers, columns, values and
+        costs at their own widths) and the solve's outputs (float64 V, int32 pi)."""
         if self.bytes_fn is not None:
             return int(self.bytes_fn(req))
-        nnz = int(req.mdp.row_ptr[-1])
-        b = capi.mdp_bytes_required(req.mdp.n, req.mdp.m, nnz, capi.MDP_F32,
+        mdp = req.mdp
+        nnz, rows = int(mdp.row_ptr[-1]), mdp.n * mdp.m
+        vsz, gsz = np.dtype(mdp.val.dtype).itemsize, np.dtype(mdp.g.dtype).itemsize
+        b = capi.mdp_bytes_required(mdp.n, mdp.m, nnz,
+                                    capi.MDP_F64 if vsz == 8 else capi.MDP_F32,
                                     {"f32": capi.MDP_F32, "bf16": capi.MDP_BF16,
                                      "f16": capi.MDP_F16}[self.store],
                                     self.solve_opts.get("restart", 30))
-        return b + nnz * 8 + len(req.mdp.row_ptr) * 8 + req.mdp.n * 12
+        staging = (rows + 1) * 8 + nnz * (4 + vsz) + rows * gsz
+        return b + staging + mdp.n * 12
 
     def submit(self, req: Request):
         req.nbytes = self.request_bytes(req)

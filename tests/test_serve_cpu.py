@@ -78,3 +78,24 @@ def test_worker_error_is_isolated():
         srv.submit(r)
     srv.close()
     assert [r.status for r in reqs] == ["MDP_OK", "MDP_OK", "error", "MDP_OK", "MDP_OK"]
+
+
+def test_admission_estimate_follows_the_request_dtypes():
+    """A float64 MDP (as the ingest builders return) needs the FP64 remainders on
+    the device (4 B per nonzero) and a wider staging copy (4 more per nonzero,
+    4 more per cost) than the same MDP in float32."""
+    import dataclasses
+
+    import synth
+    from paper_2502_14474_gb300 import capi
+    m32 = synth.random_sparse(500, 4, 8, 1.0, 0.9, seed=3, dtype=np.float32)
+    m64 = dataclasses.replace(m32, val=m32.val.astype(np.float64), g=m32.g.astype(np.float64))
+    srv = serve.Server(budget_bytes=1e12, workers=1, solver=lambda r, w: None)
+    b32 = srv.request_bytes(serve.Request(rid=0, mdp=m32))
+    b64 = srv.request_bytes(serve.Request(rid=1, mdp=m64))
+    nnz, rows = m32.nnz, m32.n * m32.m
+    assert b64 - b32 == (capi.mdp_bytes_required(m32.n, m32.m, nnz, capi.MDP_F64)
+                         - capi.mdp_bytes_required(m32.n, m32.m, nnz, capi.MDP_F32)
+                         + 4 * nnz + 4 * rows)
+    assert b64 - b32 >= 8 * nnz + 4 * rows
+    assert b32 >= capi.mdp_bytes_required(m32.n, m32.m, nnz) + 8 * nnz + 4 * rows
