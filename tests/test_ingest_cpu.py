@@ -263,3 +263,52 @@ def test_write_read_round_trip(ingest, tmp_path):
     assert struct.unpack(">4i", raw[:16]) == (CLASS_ID, rows, mdp.n, nnz)
     lens = np.frombuffer(raw[16:16 + 4 * rows], dtype=">i4")
     assert np.array_equal(lens, np.diff(mdp.row_ptr))
+
+
+def test_read_petsc_survives_corrupt_files(ingest, tmp_path):
+    """Seeded fuzzing: truncations and byte flips of valid files (header, row
+    lengths, columns, values; 32- and 64-bit; sparse and dense costs).  Each read
+    either raises MDPError or returns a structurally valid CSR -- it never
+    crashes or reads past the file."""
+    from paper_2502_14474_gb300 import MDPError
+    rng = np.random.default_rng(2024)
+    rowlens = [1, 3, 2, 1, 1, 2]
+    colidx = [0, 2, 0, 2, 1, 2, 1, 0, 1, 0]
+    vals = [1.0, 0.25, 0.5, 0.25, 0.5, 0.5, 1.0, 1.0, 0.75, 0.25]
+    bases = [(_aij(6, 3, rowlens, colidx, vals, w), g)
+             for w in (4, 8)
+             for g in (_dense(3, 2, [1.0, 2.0, 3.0, 4.0, 5.0, 6.0], w),
+                       _aij(3, 2, [2, 0, 1], [1, 1, 0], [2.0, 0.5, -1.0], w))]
+    ok = failed = 0
+    for trial in range(400):
+        P, G = bases[trial % len(bases)]
+        P, G = bytearray(P), bytearray(G)
+        target = P if rng.random() < 0.7 else G
+        kind = rng.integers(3)
+        if kind == 0:      # truncate
+            del target[int(rng.integers(0, len(target))):]
+        elif kind == 1:    # flip bytes
+            for _ in range(int(rng.integers(1, 4))):
+                target[int(rng.integers(0, len(target)))] ^= int(rng.integers(1, 256))
+        else:              # overwrite a header integer with an extreme value
+            w = 4 if P[:4] == struct.pack(">i", CLASS_ID) else 8
+            slot = int(rng.integers(1, 4))
+            v = int(rng.choice([-2, -1, 0, 2**31 - 1, 2**30, 7]))
+            fmt = ">i" if w == 4 else ">q"
+            target[slot * w:(slot + 1) * w] = struct.pack(fmt, v)
+        p = _write(tmp_path, "fP.bin", bytes(P))
+        g = _write(tmp_path, "fg.bin", bytes(G))
+        try:
+            h = ingest.read_petsc(p, g)
+        except MDPError:
+            failed += 1
+            continue
+        ok += 1
+        assert h.row_ptr[0] == 0 and np.all(np.diff(h.row_ptr) >= 0)
+        assert h.row_ptr[-1] == h.nnz == h.col.size == h.val.size
+        assert np.all((h.col >= 0) & (h.col < h.n))
+        assert np.all(np.isfinite(h.val)) and np.all(np.isfinite(h.g))
+        for r in range(h.rows):
+            c = h.col[h.row_ptr[r]:h.row_ptr[r + 1]]
+            assert np.all(np.diff(c) > 0)
+    assert failed > 100 and ok > 20
