@@ -170,3 +170,32 @@ def write_petsc(mdp, p_path, g_path=None) -> None:
                           row_ptr=rp.ctypes.data, col=col.ctypes.data, val=val.ctypes.data,
                           cost=g.ctypes.data, owned=0)
     capi.mdp_csr_write_petsc(c, p_path, g_path)
+
+
+def save_npz(mdp, path) -> None:
+    """Save an object with n, m, gamma, row_ptr, col, val, g (and optionally
+    maximize) as a numpy .npz archive, arrays at their own dtypes."""
+    np.savez(path, n=np.int64(mdp.n), m=np.int64(mdp.m), gamma=np.float64(mdp.gamma),
+             maximize=np.bool_(getattr(mdp, "maximize", False)),
+             row_ptr=np.asarray(mdp.row_ptr), col=np.asarray(mdp.col),
+             val=np.asarray(mdp.val), g=np.asarray(mdp.g))
+
+
+def load_npz(path) -> HostMDP:
+    """Load an archive written by save_npz.  The arrays keep their stored dtypes
+    (float32 or float64 probabilities and costs); row_ptr becomes int64 and col
+    int32.  Shapes are checked here; values are checked by mdp_create."""
+    with np.load(path, allow_pickle=False) as z:
+        n, m = int(z["n"]), int(z["m"])
+        row_ptr = np.ascontiguousarray(z["row_ptr"], dtype=np.int64)
+        col = np.ascontiguousarray(z["col"], dtype=np.int32)
+        val, g = np.ascontiguousarray(z["val"]), np.ascontiguousarray(z["g"])
+        mdp = HostMDP(n=n, m=m, gamma=float(z["gamma"]), row_ptr=row_ptr, col=col, val=val,
+                      g=g, maximize=bool(z["maximize"]) if "maximize" in z else False)
+    if row_ptr.shape != (n * m + 1,) or g.shape != (n * m,):
+        raise ValueError(f"{path}: row_ptr must have n*m+1 entries and g n*m")
+    if col.shape != val.shape or col.size != int(row_ptr[-1]):
+        raise ValueError(f"{path}: col and val must hold row_ptr[-1] entries")
+    if val.dtype not in (np.float32, np.float64) or g.dtype not in (np.float32, np.float64):
+        raise ValueError(f"{path}: val and g must be float32 or float64")
+    return mdp

@@ -312,3 +312,22 @@ def test_read_petsc_survives_corrupt_files(ingest, tmp_path):
             c = h.col[h.row_ptr[r]:h.row_ptr[r + 1]]
             assert np.all(np.diff(c) > 0)
     assert failed > 100 and ok > 20
+
+
+def test_npz_round_trip(ingest, tmp_path):
+    mdp = synth.random_sparse(300, 3, 5, 1.0, 0.9, seed=8, dtype=np.float32)
+    p = os.path.join(tmp_path, "mdp.npz")
+    ingest.save_npz(mdp, p)
+    h = ingest.load_npz(p)
+    assert (h.n, h.m, h.gamma, h.maximize) == (mdp.n, mdp.m, mdp.gamma, False)
+    for a, b in ((h.row_ptr, mdp.row_ptr), (h.col, mdp.col), (h.val, mdp.val), (h.g, mdp.g)):
+        assert a.dtype == b.dtype and np.array_equal(a, b)
+    h2 = ingest.HostMDP(n=h.n, m=h.m, gamma=0.5, row_ptr=h.row_ptr, col=h.col,
+                        val=h.val.astype(np.float64), g=-h.g.astype(np.float64), maximize=True)
+    ingest.save_npz(h2, p)
+    h3 = ingest.load_npz(p)
+    assert h3.maximize and h3.gamma == 0.5 and h3.val.dtype == np.float64
+    np.savez(p, n=3, m=1, gamma=0.9, row_ptr=np.arange(3), col=np.zeros(2), val=np.ones(2),
+             g=np.zeros(3))
+    with pytest.raises(ValueError, match="n\\*m\\+1"):
+        ingest.load_npz(p)
