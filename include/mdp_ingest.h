@@ -75,6 +75,20 @@ mdp_status mdp_csr_from_functions(int64_t n, int32_t m, mdp_row_fn row, mdp_cost
                                   void* user, int32_t threads, mdp_alloc_fn alloc,
                                   void* alloc_user, mdp_host_csr* out);
 
+/*
+ * mdp_csr_from_rows -- assemble the CSR from raw rows: the entries of row
+ * r = s*m + a are col/prob[offsets[r] .. offsets[r+1]), in any order and with
+ * repeated successors; cost[r] is g(s, a).  Rows are sorted and repeats summed
+ * in entry order, so the result is bitwise that of mdp_csr_from_functions on a
+ * generator returning the same rows.  Checks and errors as there (the lowest
+ * failing row is reported); offsets must start at 0 and never decrease
+ * (MDP_ERR_BAD_CSR otherwise).  The inputs are only read.
+ *   offsets  int64[n*m + 1];  col int32[offsets[n*m]];  prob, cost doubles.
+ */
+mdp_status mdp_csr_from_rows(int64_t n, int32_t m, const int64_t* offsets, const int32_t* col,
+                             const double* prob, const double* cost, int32_t threads,
+                             mdp_alloc_fn alloc, void* alloc_user, mdp_host_csr* out);
+
 /* Handling of state-action pairs without a sample in mdp_csr_from_samples. */
 typedef enum {
   MDP_UNSEEN_ERROR = 0,     /* fail with MDP_ERR_ARG, naming the first such (s, a) */

@@ -32,7 +32,8 @@ EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval"
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
                    "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim",
-                   "mdp_csr_from_functions", "mdp_csr_from_samples", "mdp_csr_read_petsc",
+                   "mdp_csr_from_functions", "mdp_csr_from_rows", "mdp_csr_from_samples",
+                   "mdp_csr_read_petsc",
                    "mdp_csr_write_petsc", "mdp_csr_free"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
@@ -188,6 +189,8 @@ def load(build_if_missing: bool = True):
         lib.mdp_csr_from_functions.argtypes = [I64, I32, MDP_ROW_FN, MDP_COST_FN, P, I32,
                                                MDP_ALLOC_FN, P, HP]
         lib.mdp_csr_from_functions.restype = ctypes.c_int
+        lib.mdp_csr_from_rows.argtypes = [I64, I32, P, P, P, P, I32, MDP_ALLOC_FN, P, HP]
+        lib.mdp_csr_from_rows.restype = ctypes.c_int
         lib.mdp_csr_from_samples.argtypes = [I64, I32, I64, P, P, P, P, I32, D, I32,
                                              MDP_ALLOC_FN, P, HP]
         lib.mdp_csr_from_samples.restype = ctypes.c_int
@@ -376,6 +379,15 @@ def mdp_csr_from_functions(n_states, n_actions, row_fn, cost_fn, threads=1, allo
     out = mdp_host_csr()
     _check(load().mdp_csr_from_functions(int(n_states), int(n_actions), row_fn, cost_fn, None,
                                          int(threads), _alloc_fn(alloc), None, ctypes.byref(out)))
+    return out
+
+
+def mdp_csr_from_rows(n_states, n_actions, offsets, col, prob, cost, threads=0, alloc=None):
+    """offsets int64[n*m+1], col int32, prob and cost float64 arrays."""
+    out = mdp_host_csr()
+    _check(load().mdp_csr_from_rows(int(n_states), int(n_actions), _ptr(offsets), _ptr(col),
+                                    _ptr(prob), _ptr(cost), int(threads), _alloc_fn(alloc), None,
+                                    ctypes.byref(out)))
     return out
 
 

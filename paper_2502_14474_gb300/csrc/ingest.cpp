@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <exception>
 #include <new>
 #include <string>
 #include <system_error>
@@ -49,20 +50,36 @@ int thread_count(int32_t threads, int64_t work) {
 }
 
 // f(block, begin, end) over t contiguous blocks of [0, count), one thread each.
+// An exception thrown in a block (an allocation failure) is caught in its
+// thread and the first one rethrown here after every thread has joined.
 template <class F>
 void parallel_blocks(int t, int64_t count, F&& f) {
   if (t <= 1) {
     f(0, int64_t(0), count);
     return;
   }
+  std::vector<std::exception_ptr> thrown(static_cast<size_t>(t));
   std::vector<std::thread> ws;
   ws.reserve(t);
-  for (int i = 0; i < t; ++i) {
-    const int64_t b = count / t * i + std::min<int64_t>(i, count % t);
-    const int64_t e = b + count / t + (i < count % t ? 1 : 0);
-    ws.emplace_back([&f, i, b, e] { f(i, b, e); });
+  try {
+    for (int i = 0; i < t; ++i) {
+      const int64_t b = count / t * i + std::min<int64_t>(i, count % t);
+      const int64_t e = b + count / t + (i < count % t ? 1 : 0);
+      ws.emplace_back([&f, &thrown, i, b, e] {
+        try {
+          f(i, b, e);
+        } catch (...) {
+          thrown[static_cast<size_t>(i)] = std::current_exception();
+        }
+      });
+    }
+  } catch (...) {  // a thread could not start: finish the ones that did, then report
+    for (auto& w : ws) w.join();
+    throw;
   }
   for (auto& w : ws) w.join();
+  for (auto& x : thrown)
+    if (x) std::rethrow_exception(x);
 }
 
 // Output arrays from the caller's allocator, or malloc (released on failure).
@@ -169,6 +186,39 @@ std::string fmt(const char* f, ...) {
   return buf;
 }
 
+// Checks of one raw row of state s, action a (before sorting): non-empty,
+// successors in [0, n), probabilities finite and non-negative.  Returns MDP_OK,
+// or the status with its message in *msg.
+mdp_status check_row(int64_t n, int64_t s, int32_t a, const int32_t* col, const double* val,
+                     int64_t k, std::string* msg) {
+  const long long sl = static_cast<long long>(s);
+  if (k == 0) {
+    *msg = fmt("row (s, a) = (%lld, %d) has no successor", sl, a);
+    return MDP_ERR_NOT_STOCHASTIC;
+  }
+  for (int64_t i = 0; i < k; ++i) {
+    if (col[i] < 0 || col[i] >= n) {
+      *msg = fmt("successor %d of (s, a) = (%lld, %d) is outside [0, n)", col[i], sl, a);
+      return MDP_ERR_BAD_CSR;
+    }
+    if (!std::isfinite(val[i])) {
+      *msg = fmt("probability of (s, a) = (%lld, %d) is not finite", sl, a);
+      return MDP_ERR_NONFINITE;
+    }
+    if (val[i] < 0.0) {
+      *msg = fmt("negative probability in (s, a) = (%lld, %d)", sl, a);
+      return MDP_ERR_NOT_STOCHASTIC;
+    }
+  }
+  return MDP_OK;
+}
+
+mdp_status check_cost(int64_t s, int32_t a, double g, std::string* msg) {
+  if (std::isfinite(g)) return MDP_OK;
+  *msg = fmt("cost of (s, a) = (%lld, %d) is not finite", static_cast<long long>(s), a);
+  return MDP_ERR_NONFINITE;
+}
+
 // row_ptr[1..rows] holds row lengths; turn it into offsets.  Returns nnz.
 int64_t prefix_sum(int64_t* row_ptr, int64_t rows) {
   row_ptr[0] = 0;
@@ -255,30 +305,12 @@ mdp_status mdp_csr_from_functions(int64_t n, int32_t m, mdp_row_fn row, mdp_cost
               return stop(r, MDP_ERR_ARG,
                            fmt("row generator aborted at (s, a) = (%lld, %d) with %d",
                                static_cast<long long>(s), a, k));
-            if (k == 0)
-              return stop(r, MDP_ERR_NOT_STOCHASTIC,
-                           fmt("row (s, a) = (%lld, %d) has no successor",
-                               static_cast<long long>(s), a));
-            for (int32_t i = 0; i < k; ++i) {
-              if (cb[i] < 0 || cb[i] >= n)
-                return stop(r, MDP_ERR_BAD_CSR,
-                             fmt("successor %d of (s, a) = (%lld, %d) is outside [0, n)", cb[i],
-                                 static_cast<long long>(s), a));
-              if (!std::isfinite(vb[i]))
-                return stop(r, MDP_ERR_NONFINITE,
-                             fmt("probability of (s, a) = (%lld, %d) is not finite",
-                                 static_cast<long long>(s), a));
-              if (vb[i] < 0.0)
-                return stop(r, MDP_ERR_NOT_STOCHASTIC,
-                             fmt("negative probability in (s, a) = (%lld, %d)",
-                                 static_cast<long long>(s), a));
-            }
+            std::string msg;
+            mdp_status cs = check_row(n, s, a, cb.data(), vb.data(), k, &msg);
+            if (cs != MDP_OK) return stop(r, cs, std::move(msg));
             const int64_t kk = canon_row(cb.data(), vb.data(), k, tmp);
             const double g = cost(s, a, user);
-            if (!std::isfinite(g))
-              return stop(r, MDP_ERR_NONFINITE,
-                           fmt("cost of (s, a) = (%lld, %d) is not finite",
-                               static_cast<long long>(s), a));
+            if ((cs = check_cost(s, a, g, &msg)) != MDP_OK) return stop(r, cs, std::move(msg));
             o.c.cost[r] = g;
             o.c.row_ptr[r + 1] = kk;
             p.col.insert(p.col.end(), cb.begin(), cb.begin() + kk);
@@ -308,6 +340,105 @@ mdp_status mdp_csr_from_functions(int64_t n, int32_t m, mdp_row_fn row, mdp_cost
         const int64_t off = o.c.row_ptr[first_state[t] * m];
         std::copy(parts[t].col.begin(), parts[t].col.end(), o.c.col + off);
         std::copy(parts[t].val.begin(), parts[t].val.end(), o.c.val + off);
+      }
+    });
+  } catch (const std::bad_alloc&) {
+    o.release();
+    return ifail(MDP_ERR_OOM, "host allocation failed");
+  } catch (const std::system_error& e) {
+    o.release();
+    return ifail(MDP_ERR_ARG, "could not start host threads: %s", e.what());
+  }
+  *out = o.c;
+  return MDP_OK;
+}
+
+mdp_status mdp_csr_from_rows(int64_t n, int32_t m, const int64_t* offsets, const int32_t* col,
+                             const double* prob, const double* cost, int32_t threads,
+                             mdp_alloc_fn alloc, void* alloc_user, mdp_host_csr* out) {
+  if (!out) return ifail(MDP_ERR_ARG, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  if (n < 1 || n > kMaxStates || m < 1)
+    return ifail(MDP_ERR_ARG, "need 1 <= n_states < 2^31 and n_actions >= 1");
+  if (!offsets || !col || !prob || !cost) return ifail(MDP_ERR_ARG, "NULL array argument");
+  const int64_t rows = n * m;
+  if (offsets[0] != 0) return ifail(MDP_ERR_BAD_CSR, "offsets[0] must be 0");
+  for (int64_t r = 0; r < rows; ++r)
+    if (offsets[r + 1] < offsets[r])
+      return ifail(MDP_ERR_BAD_CSR, "offsets decrease at row %lld", static_cast<long long>(r));
+  Outputs o{alloc, alloc_user};
+  o.c.n_states = n;
+  o.c.n_actions = m;
+  o.c.owned = alloc ? 0 : 1;
+  try {
+    o.c.row_ptr = static_cast<int64_t*>(o.get(static_cast<size_t>(rows + 1) * sizeof(int64_t)));
+    o.c.cost = static_cast<double*>(o.get(static_cast<size_t>(rows) * sizeof(double)));
+    if (!o.c.row_ptr || !o.c.cost) {
+      o.release();
+      return ifail(MDP_ERR_OOM, "host allocation of %lld rows failed",
+                   static_cast<long long>(rows));
+    }
+    const int T = thread_count(threads, rows / 1024 + 1);
+    // the canonical form of row r, in the caller's scratch vectors; returns its length
+    auto canon = [&](int64_t r, std::vector<int32_t>& cb, std::vector<double>& vb,
+                     std::vector<std::pair<int32_t, double>>& tmp) {
+      const int64_t b = offsets[r], k = offsets[r + 1] - b;
+      cb.assign(col + b, col + b + k);
+      vb.assign(prob + b, prob + b + k);
+      return canon_row(cb.data(), vb.data(), k, tmp);
+    };
+    // pass 1: checks and canonical lengths
+    std::vector<RowError> errs(T);
+    std::atomic<int64_t> limit{INT64_MAX};
+    parallel_blocks(T, rows, [&](int t, int64_t r0, int64_t r1) {
+      std::vector<int32_t> cb;
+      std::vector<double> vb;
+      std::vector<std::pair<int32_t, double>> tmp;
+      try {
+        for (int64_t r = r0; r < r1; ++r) {
+          if (r > limit.load(std::memory_order_relaxed)) return;
+          const int64_t s = r / m;
+          const int32_t a = static_cast<int32_t>(r % m);
+          std::string msg;
+          mdp_status cs = check_row(n, s, a, col + offsets[r], prob + offsets[r],
+                                    offsets[r + 1] - offsets[r], &msg);
+          if (cs == MDP_OK) cs = check_cost(s, a, cost[r], &msg);
+          if (cs != MDP_OK) {
+            errs[t] = RowError{r, cs, std::move(msg)};
+            lower_limit(limit, r);
+            return;
+          }
+          o.c.row_ptr[r + 1] = canon(r, cb, vb, tmp);
+          o.c.cost[r] = cost[r];
+        }
+      } catch (const std::bad_alloc&) {
+        errs[t] = RowError{r0, MDP_ERR_OOM, "host allocation failed while sorting rows"};
+        lower_limit(limit, r0);
+      }
+    });
+    mdp_status st = first_error(errs);
+    if (st != MDP_OK) {
+      o.release();
+      return st;
+    }
+    const int64_t nnz = prefix_sum(o.c.row_ptr, rows);
+    o.c.nnz = nnz;
+    o.c.col = static_cast<int32_t*>(o.get(static_cast<size_t>(nnz) * sizeof(int32_t)));
+    o.c.val = static_cast<double*>(o.get(static_cast<size_t>(nnz) * sizeof(double)));
+    if (!o.c.col || !o.c.val) {
+      o.release();
+      return ifail(MDP_ERR_OOM, "host allocation of %lld entries failed",
+                   static_cast<long long>(nnz));
+    }
+    // pass 2: the canonical rows into place
+    parallel_blocks(T, rows, [&](int, int64_t r0, int64_t r1) {
+      std::vector<int32_t> cb;
+      std::vector<double> vb;
+      std::vector<std::pair<int32_t, double>> tmp;
+      for (int64_t r = r0; r < r1; ++r) {
+        const int64_t kk = canon(r, cb, vb, tmp);
+        std::copy(cb.begin(), cb.begin() + kk, o.c.col + o.c.row_ptr[r]);
+        std::copy(vb.begin(), vb.begin() + kk, o.c.val + o.c.row_ptr[r]);
       }
     });
   } catch (const std::bad_alloc&) {

@@ -77,16 +77,83 @@ def _host_mdp(out, al: _Allocator, gamma, maximize) -> HostMDP:
                    g=al.array(out.cost, np.float64, n * m), maximize=bool(maximize))
 
 
+def _int32_cols(c):
+    """Successors as int32; one outside int32 becomes -2^31 (reported by the library)."""
+    return np.where((c < -2**31) | (c > 2**31 - 1), -2**31, c).astype(np.int32)
+
+
+def _simulate_states(transitions, cost, s0, s1, m):
+    """The raw rows of states [s0, s1): row lengths, successors, probabilities
+    and costs in row order (runs in a worker process of from_functions)."""
+    rows = (s1 - s0) * m
+    lens = np.empty(rows, dtype=np.int64)
+    g = np.empty(rows, dtype=np.float64)
+    cols, probs = [], []
+    r = 0
+    for s in range(s0, s1):
+        for a in range(m):
+            succ, prob = transitions(s, a)
+            c = np.asarray(succ, dtype=np.int64).reshape(-1)
+            p = np.asarray(prob, dtype=np.float64).reshape(-1)
+            if c.shape != p.shape:
+                raise ValueError(f"transitions({s}, {a}): {c.size} successors, "
+                                 f"{p.size} probabilities")
+            lens[r] = c.size
+            cols.append(c)
+            probs.append(p)
+            g[r] = float(cost(s, a))
+            r += 1
+    empty = np.empty(0, dtype=np.int64)
+    return (lens, np.concatenate(cols) if cols else empty,
+            np.concatenate(probs) if probs else empty.astype(np.float64), g)
+
+
+def from_rows(n, m, offsets, col, prob, cost, gamma, threads=0, maximize=False,
+              pinned=False) -> HostMDP:
+    """Assemble the CSR from raw rows: row r = s*m + a holds the entries
+    col/prob[offsets[r]:offsets[r+1]] in any order, repeats allowed (summed);
+    cost[r] = g(s, a).  Same result and checks as from_functions."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    col = _int32_cols(np.asarray(col, dtype=np.int64))
+    prob = np.ascontiguousarray(prob, dtype=np.float64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    if offsets.shape != (n * m + 1,) or cost.shape != (n * m,):
+        raise ValueError("offsets must have n*m+1 entries and cost n*m")
+    if col.shape != prob.shape or col.size < int(offsets[-1]):
+        raise ValueError("col and prob must hold offsets[-1] entries")
+    al = _Allocator(pinned)
+    out = capi.mdp_csr_from_rows(n, m, offsets, col, prob, cost, threads=threads, alloc=al.fn)
+    return _host_mdp(out, al, gamma, maximize)
+
+
 def from_functions(n, m, transitions, cost, gamma, threads=1, maximize=False,
-                   pinned=False) -> HostMDP:
+                   pinned=False, processes=1) -> HostMDP:
     """Evaluate ``transitions(s, a) -> (successors, probabilities)`` and
     ``cost(s, a) -> float`` for every state-action pair (online simulation).
 
     Repeated successors are summed and each row is sorted by successor.  With
     threads > 1 the callables are called from several threads (they hold the
-    interpreter lock while they run).  An exception raised by a callable is
-    re-raised here.
+    interpreter lock while they run).  With processes > 1 they run in that many
+    spawned worker processes over contiguous state ranges instead (they must
+    then be picklable: module-level functions), and the rows are assembled by
+    the library (from_rows); the result is the same.  An exception raised by a
+    callable is re-raised here.
     """
+    if processes > 1:
+        import multiprocessing as mp
+        chunks = max(1, min(n, 4 * processes))
+        bounds = [n * i // chunks for i in range(chunks + 1)]
+        with mp.get_context("spawn").Pool(processes) as pool:
+            parts = pool.starmap(_simulate_states,
+                                 [(transitions, cost, bounds[i], bounds[i + 1], m)
+                                  for i in range(chunks)])
+        lens = np.concatenate([p[0] for p in parts])
+        offsets = np.zeros(n * m + 1, dtype=np.int64)
+        np.cumsum(lens, out=offsets[1:])
+        return from_rows(n, m, offsets, np.concatenate([p[1] for p in parts]),
+                         np.concatenate([p[2] for p in parts]),
+                         np.concatenate([p[3] for p in parts]), gamma, threads=threads,
+                         maximize=maximize, pinned=pinned)
     errors = []
 
     def row(s, a, cap, col_p, prob_p, _user):
@@ -99,9 +166,7 @@ def from_functions(n, m, transitions, cost, gamma, threads=1, maximize=False,
                                  f"{p.size} probabilities")
             k = c.size
             if 0 < k <= cap:
-                # a successor outside int32 reaches the library as -2^31 (reported there)
-                big = (c < -2**31) | (c > 2**31 - 1)
-                np.ctypeslib.as_array(col_p, (k,))[:] = np.where(big, -2**31, c)
+                np.ctypeslib.as_array(col_p, (k,))[:] = _int32_cols(c)
                 np.ctypeslib.as_array(prob_p, (k,))[:] = p
             return k
         except BaseException as e:  # noqa: BLE001 -- carried across the C boundary

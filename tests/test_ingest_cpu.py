@@ -331,3 +331,73 @@ def test_npz_round_trip(ingest, tmp_path):
              g=np.zeros(3))
     with pytest.raises(ValueError, match="n\\*m\\+1"):
         ingest.load_npz(p)
+
+
+# module-level generators: picklable for the worker processes of from_functions
+def _sim_transitions(s, a):
+    rng = np.random.default_rng(7_000_003 + s * 31 + a)
+    k = 1 + (s + 2 * a) % 6
+    succ = rng.integers(0, 60, size=k)
+    w = rng.random(k) + 0.05
+    return succ.tolist(), (w / w.sum()).tolist()
+
+
+def _sim_cost(s, a):
+    return float(np.cos(0.3 * s + a))
+
+
+def _sim_fails(s, a):
+    if s == 37:
+        raise RuntimeError("simulator failed at state 37")
+    return [s], [1.0]
+
+
+def _raw_rows(n, m, transitions, cost):
+    offsets, col, prob, g = [0], [], [], []
+    for s in range(n):
+        for a in range(m):
+            succ, p = transitions(s, a)
+            col += list(succ)
+            prob += list(p)
+            offsets.append(len(col))
+            g.append(cost(s, a))
+    return np.array(offsets), np.array(col), np.array(prob), np.array(g)
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_from_rows_equals_from_functions(ingest, threads):
+    n, m = 60, 3
+    ref = ingest.from_functions(n, m, _sim_transitions, _sim_cost, gamma=0.9)
+    h = ingest.from_rows(n, m, *_raw_rows(n, m, _sim_transitions, _sim_cost), gamma=0.9,
+                         threads=threads)
+    _same(h, (ref.row_ptr, ref.col, ref.val, ref.g))
+    _same(h, _by_hand(n, m, _sim_transitions, _sim_cost))
+
+
+def test_from_rows_errors(ingest):
+    from paper_2502_14474_gb300 import MDPError
+    off, col, prob, g = _raw_rows(60, 3, _sim_transitions, _sim_cost)
+    bad = off.copy()
+    bad[5] = bad[6] + 1
+    with pytest.raises(MDPError, match="BAD_CSR.*offsets decrease at row 5"):
+        ingest.from_rows(60, 3, bad, col, prob, g, 0.9)
+    c2 = col.copy()
+    c2[off[100]] = 60
+    c2[off[7]] = -3
+    with pytest.raises(MDPError, match=r"successor -3 of \(s, a\) = \(2, 1\)"):
+        ingest.from_rows(60, 3, off, c2, prob, g, 0.9, threads=8)
+    g2 = g.copy()
+    g2[11] = np.inf
+    with pytest.raises(MDPError, match=r"NONFINITE.*cost of \(s, a\) = \(3, 2\)"):
+        ingest.from_rows(60, 3, off, col, prob, g2, 0.9)
+    with pytest.raises(ValueError, match="offsets"):
+        ingest.from_rows(60, 3, off[:-1], col, prob, g, 0.9)
+
+
+def test_from_functions_in_worker_processes(ingest):
+    n, m = 60, 3
+    ref = ingest.from_functions(n, m, _sim_transitions, _sim_cost, gamma=0.9)
+    h = ingest.from_functions(n, m, _sim_transitions, _sim_cost, gamma=0.9, processes=2)
+    _same(h, (ref.row_ptr, ref.col, ref.val, ref.g))
+    with pytest.raises(RuntimeError, match="state 37"):
+        ingest.from_functions(n, m, _sim_fails, _sim_cost, gamma=0.9, processes=2)
