@@ -49,6 +49,11 @@ class _Allocator:
     ones when pinned) and keeps them by address."""
 
     def __init__(self, pinned: bool = False):
+        if pinned:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("pinned=True needs a CUDA device: page-locked host memory "
+                                   "comes from the CUDA driver")
         self.pinned = pinned
         self.bufs = {}
         self.fn = capi.MDP_ALLOC_FN(self._alloc)

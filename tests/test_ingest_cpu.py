@@ -401,3 +401,11 @@ def test_from_functions_in_worker_processes(ingest):
     _same(h, (ref.row_ptr, ref.col, ref.val, ref.g))
     with pytest.raises(RuntimeError, match="state 37"):
         ingest.from_functions(n, m, _sim_fails, _sim_cost, gamma=0.9, processes=2)
+
+
+def test_pinned_needs_a_device(ingest):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present (the GPU tests cover pinned outputs)")
+    with pytest.raises(RuntimeError, match="needs a CUDA device"):
+        ingest.from_samples(2, 1, [0, 1], [0, 0], [1, 0], None, pinned=True)
