@@ -40,6 +40,8 @@ class Request:
     status: str = "pending"
     error: str = ""
     nbytes: int = 0
+    cancel_requested: bool = False
+    handle: int | None = dataclasses.field(default=None, repr=False)  # while solving
 
     @property
     def latency(self) -> float:
@@ -123,6 +125,28 @@ class Server:
             self.queue.append(req)
             self.cv.notify_all()
 
+    def cancel(self, req: Request) -> bool:
+        """Cancel a request.  A queued one leaves the queue at once with status
+        MDP_ERR_CANCELLED; a running one is asked to stop at its solve's next
+        host check (mdp_cancel), and ends with that status unless its solve
+        finished first.  Returns False when the request had already finished."""
+        with self.cv:
+            for i, q in enumerate(self.queue):
+                if q is req:
+                    del self.queue[i]
+                    req.cancel_requested = True
+                    req.status = "MDP_ERR_CANCELLED"
+                    req.t_done = time.perf_counter()
+                    self.done.append(req)
+                    self.cv.notify_all()
+                    return True
+            if req.t_done or req.status not in ("pending",):
+                return False
+            req.cancel_requested = True
+            if req.handle is not None:
+                capi.mdp_cancel(req.handle)
+            return True
+
     # -- worker --------------------------------------------------------------------
     def _take(self):
         with self.cv:
@@ -172,14 +196,24 @@ class Server:
                     h = MDP.from_csr(req.mdp, store=self.store, host_input=True,
                                      device=f"cuda:{self.device}", stream=stream)
                     try:
+                        with self.cv:  # from here on cancel() reaches the solve
+                            req.handle = h.h
+                            stop = req.cancel_requested
+                        if stop:
+                            raise capi.MDPError(7, "cancelled before the solve started")
                         V, pi, st = h.solve(raise_on_not_converged=False, **self.solve_opts)
                         Vh = V.cpu()
                         pih = pi.cpu()
                         stream.synchronize()
                     finally:
+                        with self.cv:
+                            req.handle = None
                         h.close()
                 req.V, req.pi, req.stats = Vh.numpy(), pih.numpy(), st
                 req.status = st["status"]
+            except capi.MDPError as e:
+                req.status = e.status_name
+                req.error = str(e)
             except Exception as e:  # keep serving the other requests
                 req.status = "error"
                 req.error = repr(e)

@@ -99,3 +99,36 @@ def test_admission_estimate_follows_the_request_dtypes():
                          + 4 * nnz + 4 * rows)
     assert b64 - b32 >= 8 * nnz + 4 * rows
     assert b32 >= capi.mdp_bytes_required(m32.n, m32.m, nnz) + 8 * nnz + 4 * rows
+
+
+def test_cancel_queued_and_running_requests():
+    """cancel() drops a queued request at once and asks a running one to stop;
+    the others are served as usual and the budget is released."""
+    started = threading.Event()
+
+    def solver(req, w):
+        if req.rid == 0:  # a long solve that watches for cancellation
+            started.set()
+            t0 = time.perf_counter()
+            while not req.cancel_requested and time.perf_counter() - t0 < 10:
+                time.sleep(0.001)
+            return None, None, {"status": "MDP_ERR_CANCELLED" if req.cancel_requested
+                                else "MDP_OK", "transitions": 0.0}
+        return np.zeros(req.mdp.n), None, {"status": "MDP_OK", "transitions": 1.0}
+
+    srv = serve.Server(budget_bytes=100, workers=1, solver=solver,
+                       bytes_fn=lambda r: r.mdp.n).start()
+    reqs = [serve.Request(rid=i, mdp=_FakeMDP(60)) for i in range(4)]
+    for r in reqs:
+        srv.submit(r)
+    assert started.wait(5)
+    assert srv.cancel(reqs[2])           # still queued: leaves the queue
+    assert reqs[2].status == "MDP_ERR_CANCELLED"
+    assert srv.cancel(reqs[0])           # running: asked to stop
+    srv.close()
+    assert [r.status for r in reqs] == ["MDP_ERR_CANCELLED", "MDP_OK",
+                                        "MDP_ERR_CANCELLED", "MDP_OK"]
+    assert not srv.cancel(reqs[1])       # already finished
+    assert srv.used == 0 and srv.active == 0
+    summ = serve.summarize(reqs, 1.0)
+    assert summ["completed"] == 2 and summ["failed"] == 2
