@@ -61,7 +61,11 @@ def _args():
                         "continuous-batching loop")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--streams", type=int, default=16)
-    p.add_argument("--requests", type=int, default=2000)
+    p.add_argument("--requests", type=int, default=10000)
+    p.add_argument("--pool", type=int, default=512,
+                   help="serve: distinct MDPs drawn from the uneven-batch distribution")
+    p.add_argument("--saturation-rate", type=float, default=2000.0)
+    p.add_argument("--saturation-requests", type=int, default=3000)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--budget-gb", type=float, default=100.0)
     p.add_argument("--store", choices=["f32", "bf16", "f16"], default="f32",
@@ -250,6 +254,63 @@ def _cpu_sample_bellman(n, seconds, s1=1 << 18):
                         f"{el:.1f} s"))
 
 
+def _oracle_error_blocks(n_total, V, pi, tol, block=4096):
+    """The FP64 oracle's certificate of a GPU result on three sampled blocks of
+    states (both ends of the state range and one in the middle), run on the host
+    after the timed region: ||T V - V||_inf in FP64 over the blocks, the bound
+    ||V - V*||_inf <= res / (1 - gamma) it implies for the whole vector when the
+    whole residual is that small, and the greedy actions that differ from the
+    oracle's on states whose oracle Q-gap exceeds 2 tol."""
+    import oracle
+    res, mism, checked, gamma = 0.0, 0, 0, None
+    starts = (0, n_total // 3, max(0, n_total - block))
+    for s0 in starts:
+        s1 = min(n_total, s0 + block)
+        blk = _workload(n=n_total, s0=s0, s1=s1)
+        cert = oracle.certificate(blk, V)
+        gamma = float(blk.gamma)
+        res = max(res, cert["res_inf"])
+        clear = cert["gap"] > 2 * tol + 1e-12
+        mism += int(np.count_nonzero(pi[s0:s1][clear] != cert["pi"][clear]))
+        checked += s1 - s0
+    vmax = float(np.max(np.abs(V))) if len(V) else 0.0
+    bound = res / (1.0 - gamma)
+    return {"kind": "FP64 oracle certificate on sampled blocks",
+            "blocks": [[s0, min(n_total, s0 + block)] for s0 in starts],
+            "states_checked": checked, "res_inf_fp64": res, "bound_inf": bound,
+            "bound_rel": bound / vmax if vmax > 0 else None,
+            "pi_mismatch_on_clear_gap": mism}
+
+
+def _oracle_error_whole(items, tol):
+    """The FP64 oracle's certificate of whole GPU results (small MDPs): the largest
+    ||T V - V||_inf, the largest bound res / (1 - gamma) on ||V - V*||_inf, and the
+    greedy actions that differ from the oracle's on clear-gap states.  ``items``
+    holds (mdp, V, pi) triples."""
+    import oracle
+    res, bound, mism, states = 0.0, 0.0, 0, 0
+    for mdp, V, pi in items:
+        cert = oracle.certificate(mdp, V)
+        res = max(res, cert["res_inf"])
+        bound = max(bound, cert["bound"])
+        clear = cert["gap"] > 2 * tol + 1e-12
+        mism += int(np.count_nonzero(np.asarray(pi)[clear] != cert["pi"][clear]))
+        states += mdp.n
+    return {"kind": "FP64 oracle certificate of whole solves", "solves": len(items),
+            "states_checked": states, "res_inf_fp64": res, "bound_inf": bound,
+            "pi_mismatch_on_clear_gap": mism}
+
+
+def _timed_oracle(fn):
+    """Run fn() and return (result, seconds, host threads available)."""
+    t0 = time.perf_counter()
+    r = fn()
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return r, el, int(omp) if omp else cores
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -316,10 +377,28 @@ def run_batch(args):
     seq_el, _, _ = go(1)
     trans = sum(st["transitions"] for st in stats)
     el = float(np.median(times))
-    # the float-float Bellman residual each solve ends on (the oracle certifies
-    # batch results in the GPU tests, not here)
-    sample = list(range(0, len(mdps), max(1, len(mdps) // 5)))
+    sample = list(range(0, len(mdps), 100))
     res = [stats[i]["residual_inf"] for i in sample]
+    # CPU leg, after the timed runs: the FP64 oracle certifies the 1% sample of
+    # results (every 100th MDP) and is timed on Bellman sweeps over the same MDPs
+    oracle_error = cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        items = [(mdps[i], Vs[i].cpu().numpy(), pis[i].cpu().numpy()) for i in sample]
+        oracle_error = _oracle_error_whole(items, 1e-9)
+
+        def sweeps():
+            reps, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < args.cpu_seconds:
+                for mdp, V, _ in items:
+                    oracle.bellman(mdp, V)
+                reps += 1
+            return reps
+        reps, cpu_s, cores = _timed_oracle(sweeps)
+        cnnz = sum(mdp.nnz for mdp, _, _ in items)
+        cpu = {"value": cnnz * reps / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 oracle Bellman sweeps over the {len(items)} sampled MDPs "
+                          f"({cnnz} nnz), {reps} rounds, {cpu_s:.1f} s")}
     line = {"metric": METRIC, "value": trans / el, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -330,7 +409,7 @@ def run_batch(args):
                        "generation_s": gen_s},
             "converged": sum(1 for x in status if x == "MDP_OK"),
             "sequential_ms": seq_el * 1e3, "speedup_vs_one_stream": seq_el / el,
-            "solve_residual_sample": res}
+            "solve_residual_sample": res, "oracle_error": oracle_error, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     for h in hs:
         h.close()
@@ -338,56 +417,92 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Poisson request stream through the continuous-batching loop (one JSON line)."""
+    """Poisson request stream through the continuous-batching loop (one JSON line).
+
+    Requests are drawn from the uneven-batch distribution (n log-uniform in
+    [2e3, 2e5], m in {2..16}, 4..32 successors per row, gamma in [0.9, 0.999]):
+    a pool of ``--pool`` independent draws (distinct seeds), plus 1% large
+    requests (n = 2^20, m = 8, 16 successors) from four distinct large MDPs.
+    The trace runs at the offered rate, then a shorter trace at
+    ``--saturation-rate`` measures the loop's throughput and latency when it
+    cannot keep up."""
     import torch
     import synth
     from paper_2502_14474_gb300 import serve
+    t0 = time.perf_counter()
     rng = np.random.default_rng(5)
-    pool = [synth.uneven_mdp(p) for p in synth.uneven_batch_params(48, seed=5)]
+    pool = [synth.uneven_mdp(p) for p in synth.uneven_batch_params(args.pool, seed=5)]
     large = [synth.random_sparse(1 << 20, 8, 16, 1.0, 0.99, seed=5_000_000 + i,
                                  dtype=np.float32, name="random_n1048576_m8_k16")
-             for i in range(2)]
+             for i in range(4)]
     # request payloads live in pinned host memory (as a front end that receives
     # them into registered buffers would hold them): host-to-device copies are
     # then asynchronous DMA instead of staged pageable copies
     for mdp in pool + large:
         for k in ("row_ptr", "col", "val", "g"):
             setattr(mdp, k, torch.from_numpy(getattr(mdp, k)).pin_memory().numpy())
-    arrivals = serve.poisson_arrivals(args.requests, args.rate, seed=5)
-    reqs = []
-    for i, a in enumerate(arrivals):
-        mdp = large[int(rng.integers(2))] if rng.random() < 0.01 else pool[int(rng.integers(48))]
-        reqs.append(serve.Request(rid=i, mdp=mdp, arrival=float(a)))
+    gen_s = time.perf_counter() - t0
+
+    def trace(count, rate, seed, rid0):
+        arrivals = serve.poisson_arrivals(count, rate, seed=seed)
+        out = []
+        for i, a in enumerate(arrivals):
+            if rng.random() < 0.01:
+                mdp = large[int(rng.integers(len(large)))]
+            else:
+                mdp = pool[int(rng.integers(len(pool)))]
+            out.append(serve.Request(rid=rid0 + i, mdp=mdp, arrival=float(a)))
+        return out
+
     srv = serve.Server(budget_bytes=args.budget_gb * 1e9, workers=args.streams,
                        solve_opts={"max_inner": args.max_inner}).start()
     # warm the library, the kernels of both request classes and the memory pool
     # on a few requests outside the trace (a server warms up before it takes traffic)
-    warm = [serve.Request(rid=-1 - i, mdp=m) for i, m in enumerate(pool[:4] + large)]
+    warm = [serve.Request(rid=-1 - i, mdp=m) for i, m in enumerate(pool[:4] + large[:1])]
     for r in warm:
         srv.submit(r)
     with srv.cv:
         while len(srv.done) < len(warm):
             srv.cv.wait(timeout=1.0)
         srv.done.clear()
+    reqs = trace(args.requests, args.rate, 5, 0)
     wall = srv.run_trace(reqs)
-    srv.close()
     summ = serve.summarize(reqs, wall)
-    # 1% of the requests: the float-float Bellman residual their solves end on
-    # (the oracle certifies served results in the GPU tests, not here)
+    peak_active, peak_used = srv.peak_active, srv.peak_used
+    sat = None
+    if args.saturation_requests > 0:
+        with srv.cv:
+            srv.done.clear()
+        sreqs = trace(args.saturation_requests, args.saturation_rate, 6, 10**7)
+        swall = srv.run_trace(sreqs)
+        sat = serve.summarize(sreqs, swall)
+        sat["offered_rate_per_s"] = args.saturation_rate
+    srv.close()
+    # 1% of the requests: the float-float Bellman residual their solves end on,
+    # and (CPU leg, after the traces) the FP64 oracle's certificate of their results
     sample = [r for r in reqs if r.rid % 100 == 0 and r.status == "MDP_OK"]
+    oracle_error = None
+    if not args.no_cpu_baseline:
+        oracle_error, cpu_s, cores = _timed_oracle(
+            lambda: _oracle_error_whole([(r.mdp, r.V, r.pi) for r in sample], 1e-9))
+        oracle_error["oracle_s"] = cpu_s
+        oracle_error["cores"] = cores
     line = {"metric": "solves/s (with p50/p99 latency)", "value": summ["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "poisson_request_stream", "requests": args.requests,
                        "rate_per_s": args.rate, "budget_gb": args.budget_gb,
-                       "workers": args.streams, "pool_mdps": 48, "large_fraction": 0.01,
-                       "large": "n=2^20, m=8, 16 successors"},
-            "serving": summ, "peak_active": srv.peak_active,
-            "peak_budget_gb": srv.peak_used / 1e9,
+                       "workers": args.streams, "pool_mdps": len(pool),
+                       "pool": "independent draws of the uneven-batch distribution",
+                       "large_fraction": 0.01, "large_mdps": len(large),
+                       "large": "n=2^20, m=8, 16 successors", "generation_s": gen_s},
+            "serving": summ, "saturation": sat, "peak_active": peak_active,
+            "peak_budget_gb": peak_used / 1e9,
             "residual_sample": {"requests": len(sample),
                                 "max_residual_inf": max((r.stats["residual_inf"] for r in sample),
-                                                        default=None)}}
+                                                        default=None)},
+            "oracle_error": oracle_error}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -456,7 +571,9 @@ def main():
         e0.record(stream)
         out = []
         for _ in range(args.steps):
-            out.append(h.solve(**opts)[2])
+            V_last, pi_last, st_ = h.solve(**opts)
+            out.append(st_)
+            last[:] = [V_last, pi_last]
         e1.record(stream)
         torch.cuda.synchronize()
         if ws > 1:
@@ -466,9 +583,12 @@ def main():
         h.profile(False)
         return elapsed, out, prof_
 
+    last = []
     sampler.start()
     time.sleep(0.3)
     ms, stats, prof_plain = timed(False)
+    V_res = last[0].cpu().numpy()
+    pi_res = last[1].cpu().numpy()
     clocks = sampler.stop()
     trans = sum(s["transitions"] for s in stats)
     ms_max, value = aggregate(ms, trans, dist if ws > 1 else None, dev)
@@ -546,9 +666,12 @@ def main():
     if h is not None:
         h.close()
 
-    cpu = None
+    # ---- CPU leg: the FP64 oracle timed on the host, and its certificate of the
+    # result of the last timed solve (after the timed regions)
+    cpu, oracle_error = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_sample_bellman(args.n, args.cpu_seconds)
+        oracle_error = _oracle_error_blocks(host.n, V_res, pi_res, args.tol)
 
     if rank == 0:
         st0 = stats[-1]
@@ -585,6 +708,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "oracle_error": oracle_error,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -251,6 +251,30 @@ mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts*
 /* Handle properties (layout chosen at create, memory held). */
 mdp_status mdp_info(mdp_t h, mdp_info_t* info);
 
+#define MDP_MAX_RESTART 64
+
+/* The last finished GMRES restart cycle of a handle (the least-squares step of
+ * GMRES, Saad 2003, 6.5.3: minimise ||beta e_1 - H y||_2 over y, H the
+ * (J+1) x J upper Hessenberg matrix of the Arnoldi process, which the inner
+ * policy evaluation of the paper's "Problem Setting and Solution Methods" runs
+ * on (I - gamma P_pi)). */
+typedef struct {
+  int32_t J;        /* Arnoldi steps of the cycle (0 when no cycle has finished) */
+  int32_t pad;
+  double beta;      /* ||r_0||_2 of the cycle */
+  double est;       /* |g_{J}|: the Givens residual estimate ||beta e_1 - H y||_2 */
+  double H[(MDP_MAX_RESTART + 1) * MDP_MAX_RESTART]; /* H as built by the Arnoldi
+                       process, before the rotations: entry (i, j) at H[j * 65 + i],
+                       i <= j + 1 < J + 1; other entries unspecified */
+  double y[MDP_MAX_RESTART];  /* the back-solved least-squares solution, y[0..J) */
+} mdp_gmres_cycle_t;
+
+/* Copy the last finished GMRES cycle of h (mdp_solve with the GMRES inner solver,
+ * or mdp_policy_eval) into *out.  Synchronises the handle's last stream.  The
+ * record is the one of the cycle that finished last: later cycles overwrite
+ * it.  Returns MDP_ERR_ARG for a NULL argument, MDP_ERR_CUDA if the copy fails. */
+mdp_status mdp_last_cycle(mdp_t h, mdp_gmres_cycle_t* out);
+
 /*
  * Device bytes a handle of this shape needs (CSR copy, low-precision copy,
  * GMRES basis of `restart`+1 vectors, work vectors); used for admission control.
@@ -258,8 +282,14 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info);
 size_t mdp_bytes_required(int64_t n_states, int32_t n_actions, int64_t nnz, mdp_dtype val_t,
                           mdp_dtype store_t, int32_t restart);
 
-/* Request that a running mdp_solve / mdp_policy_eval on h stop at its next
- * host check; it then returns MDP_ERR_CANCELLED.  Thread-safe. */
+/* Request that the mdp_solve / mdp_policy_eval running on h stop at its next
+ * host check (at most one GMRES restart cycle or one batch of eight inner
+ * iterations later); it then returns MDP_ERR_CANCELLED with the iterate
+ * reached so far in its outputs.  A request made while no call runs on h stays
+ * pending: the next mdp_solve / mdp_policy_eval on h returns MDP_ERR_CANCELLED
+ * at once, before it enqueues anything or writes its outputs.  Each request is consumed by the call that returns
+ * MDP_ERR_CANCELLED for it; a request that arrives after a call's last check
+ * therefore cancels the next call on h.  Thread-safe. */
 void mdp_cancel(mdp_t h);
 
 /* ---- per-kernel profiling (CUDA events on the launching stream) ---------- */
@@ -314,9 +344,11 @@ mdp_status mdp_profile_read(mdp_t h, mdp_profile_t* out);
  * Scratch: a file-scope device array of 262,400 bytes per device that loads
  * the library (held until exit), enough for n_states <= 4,194,304; larger
  * problems are rejected with MDP_ERR_ARG.  The first call on a device looks
- * the array up with cudaGetSymbolAddress, so it should come before any stream
- * capture.  All calls on a device share the array: calls whose kernels overlap
- * on the GPU race and must be serialised by the caller.
+ * the array up with cudaGetSymbolAddress.  The call reads its results back
+ * through host memory and synchronises `stream`, so it must never be made on a
+ * stream that is capturing a CUDA graph; such a call returns MDP_ERR_ARG
+ * before it enqueues anything.  All calls on a device share the array: calls
+ * whose kernels overlap on the GPU race and must be serialised by the caller.
  */
 mdp_status mdp_bellman_noalloc(int64_t n_states, int32_t n_actions, const int64_t* row_ptr,
                                const int32_t* col, const float* val, const float* cost,

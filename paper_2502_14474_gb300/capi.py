@@ -31,7 +31,7 @@ MDP_HISTORY = 128
 EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval",
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
-                   "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim",
+                   "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim", "mdp_last_cycle",
                    "mdp_csr_from_functions", "mdp_csr_from_rows", "mdp_csr_from_samples",
                    "mdp_csr_read_petsc",
                    "mdp_csr_write_petsc", "mdp_csr_free"])
@@ -94,6 +94,23 @@ class mdp_info_t(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+MDP_MAX_RESTART = 64
+
+
+class mdp_gmres_cycle_t(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int32), ("pad", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("est", ctypes.c_double),
+                ("H", ctypes.c_double * ((MDP_MAX_RESTART + 1) * MDP_MAX_RESTART)),
+                ("y", ctypes.c_double * MDP_MAX_RESTART)]
+
+    def as_dict(self):
+        import numpy as np
+        J = self.J
+        H = np.ctypeslib.as_array(self.H).reshape(MDP_MAX_RESTART, MDP_MAX_RESTART + 1).T
+        return {"J": J, "beta": self.beta, "est": self.est,
+                "H": np.triu(np.array(H[:J + 1, :J]), -1), "y": np.array(self.y[:J])}
 
 
 class mdp_profile_t(ctypes.Structure):
@@ -169,6 +186,8 @@ def load(build_if_missing: bool = True):
         lib.mdp_solve.restype = ctypes.c_int
         lib.mdp_info.argtypes = [P, ctypes.POINTER(mdp_info_t)]
         lib.mdp_info.restype = ctypes.c_int
+        lib.mdp_last_cycle.argtypes = [P, ctypes.POINTER(mdp_gmres_cycle_t)]
+        lib.mdp_last_cycle.restype = ctypes.c_int
         lib.mdp_bytes_required.argtypes = [I64, I32, I64, ctypes.c_int, ctypes.c_int, I32]
         lib.mdp_bytes_required.restype = ctypes.c_size_t
         lib.mdp_cancel.argtypes = [P]
@@ -306,6 +325,14 @@ def mdp_info(h) -> dict:
     info = mdp_info_t()
     _check(load().mdp_info(h, ctypes.byref(info)))
     return info.as_dict()
+
+
+def mdp_last_cycle(h) -> dict:
+    """The last finished GMRES cycle: J, beta, est, H ((J+1) x J, before the Givens
+    rotations) and the least-squares solution y."""
+    c = mdp_gmres_cycle_t()
+    _check(load().mdp_last_cycle(h, ctypes.byref(c)))
+    return c.as_dict()
 
 
 def mdp_bytes_required(n_states, n_actions, nnz, val_t=MDP_F32, store_t=MDP_F32, restart=30):

@@ -1074,6 +1074,31 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
   return MDP_OK;
 }
 
+mdp_status mdp_last_cycle(mdp_t h, mdp_gmres_cycle_t* out) {
+  static_assert(MDP_MAX_RESTART == kMaxRestart, "ABI restart cap");
+  if (!h || !out) return fail(MDP_ERR_ARG, "NULL argument");
+  DeviceGuard dg(h->device);
+  memset(out, 0, sizeof(*out));
+  const char* base = reinterpret_cast<const char*>(h->st);
+  int J = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&J, base + offsetof(DevState, last_J), sizeof(int), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(&out->beta, base + offsetof(DevState, last_beta), sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&out->est, base + offsetof(DevState, last_est), sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(out->H, base + offsetof(DevState, Hraw), sizeof(out->H),
+                 cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(out->y, base + offsetof(DevState, y), sizeof(out->y), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_CUDA, "mdp_last_cycle: reading the cycle record failed");
+  }
+  out->J = J;
+  return MDP_OK;
+}
+
 mdp_status mdp_bellman(mdp_t h, const void* V_in, mdp_dtype v_t, void* V_out, int32_t* pi_out,
                        float* r_out, double* res_inf, double* res_2, void* stream) {
   Range nvtx("mdp_bellman");
@@ -1137,8 +1162,10 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
   if (max_iters < 0) return fail(MDP_ERR_ARG, "max_iters must be >= 0");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // a cancel request made before this call started (a server may publish the
+  // handle to its cancel path before it calls in) is honoured here, not dropped
+  if (h->cancel.exchange(0)) return fail(MDP_ERR_CANCELLED, "cancelled before the call started");
   DoneMark dm{h, s};
-  h->cancel.store(0);
   mdp_status rc = check_policy(h, pi, s);
   if (rc != MDP_OK) return rc;
   rc = ensure_basis(h, restart, s);
@@ -1164,7 +1191,7 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
                     max_iters, res);
       break;
     }
-    if (h->cancel.load()) {
+    if (h->cancel.exchange(0)) {  // the request is consumed by this call
       result = fail(MDP_ERR_CANCELLED, "cancelled");
       break;
     }
@@ -1226,8 +1253,8 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
     return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
   DeviceGuard dg(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->cancel.exchange(0)) return fail(MDP_ERR_CANCELLED, "cancelled before the call started");
   DoneMark dm{h, s};
-  h->cancel.store(0);
   mdp_status rc = MDP_OK;
   if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart, s);
   else if (o.inner == MDP_INNER_RICHARDSON) rc = ensure_richardson(h, s);
@@ -1276,7 +1303,7 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
       result = fail(MDP_ERR_NOT_CONVERGED, "max_outer=%d reached (residual %.3e)", o.max_outer, res);
       break;
     }
-    if (h->cancel.load()) {
+    if (h->cancel.exchange(0)) {  // the request is consumed by this call
       result = fail(MDP_ERR_CANCELLED, "cancelled");
       break;
     }

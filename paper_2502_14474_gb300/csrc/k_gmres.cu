@@ -63,6 +63,8 @@ __device__ void givens_step(DevState* st, int j, double nrm) {
   for (int i = 0; i <= j; ++i) colmax = fmax(colmax, fabs(h[i]));
   const bool breakdown = !(nrm > 1e-14 * colmax) || !(nrm > 1e-300);
   h[j + 1] = nrm;
+  double* hr = st->Hraw + static_cast<int64_t>(j) * kMaxBasis;
+  for (int i = 0; i <= j + 1; ++i) hr[i] = h[i];
   st->scale[j + 1] = breakdown ? 0.0 : 1.0 / nrm;
   for (int i = 0; i < j; ++i) {
     const double t = st->cs[i] * h[i] + st->sn[i] * h[i + 1];
@@ -97,6 +99,9 @@ __device__ void givens_step(DevState* st, int j, double nrm) {
       const double d = st->H[static_cast<int64_t>(i) * kMaxBasis + i];
       st->y[i] = d != 0.0 ? t / d : 0.0;
     }
+    st->last_J = J;
+    st->last_beta = st->beta;
+    st->last_est = est;
   }
 }
 

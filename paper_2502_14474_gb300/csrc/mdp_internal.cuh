@@ -240,6 +240,13 @@ struct DevState {
   unsigned dots_run[kMaxBasis / 8 + 1][kDotsMaxRuns];
   // BiCGStab scalars (rho = <r^, r>, alpha, omega, beta of the recurrences)
   double bicg_rho, bicg_alpha, bicg_omega, bicg_beta;
+  // the last finished GMRES cycle, kept for inspection: the Hessenberg matrix
+  // as built (before the Givens rotations; column-major, leading dimension
+  // kMaxBasis), its beta = ||r0||_2, step count and final residual estimate
+  // (y above holds its least-squares solution until the next cycle ends)
+  double Hraw[kMaxBasis * kMaxRestart];
+  double last_beta, last_est;
+  int last_J;
 };
 
 // Initialise a GMRES cycle from ||r0||_2 = beta (single thread).

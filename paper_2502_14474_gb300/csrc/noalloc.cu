@@ -14,11 +14,15 @@
 //
 // The scratch array is resolved once per device with cudaGetSymbolAddress (the
 // array's name in host code is only a host-side stand-in, not a device
-// address).  That happens on the first call on each device, so the first call
-// on a device should come before any stream capture.  Every call on a device
-// shares the one array: concurrent calls whose kernels overlap on the GPU race
-// on it and must be serialised by the caller (one stream, or events).
+// address).  That happens on the first call on each device.  No call may be
+// made on a stream that is being captured into a CUDA graph: every call reads
+// its results back with a copy into host memory and a stream synchronisation,
+// which capture does not allow, so a call on a capturing stream is rejected
+// with MDP_ERR_ARG before anything is enqueued.  Every call on a device shares
+// the one array: concurrent calls whose kernels overlap on the GPU race on it
+// and must be serialised by the caller (one stream, or events).
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <mutex>
@@ -44,6 +48,10 @@ struct Head {
 };
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// The kernel's reduction helpers (mdpk::block_max_d / block_sum_d) reduce over
+// mdpk::kThreads / 32 warps into `red`; the tile width must match them.
+static_assert(kTileStates == mdpk::kThreads, "tile width must equal the reduction width");
 
 __global__ void __launch_bounds__(kTileStates)
     k_bellman_plain(int64_t n, int32_t m, const int64_t* __restrict__ rp,
@@ -144,6 +152,13 @@ extern "C" mdp_status mdp_bellman_noalloc(int64_t n_states, int32_t n_actions,
                 "mdp_bellman_noalloc: n_states exceeds the static scratch limit of 4194304 states");
   if (n_states > INT64_MAX / n_actions)
     return fail(MDP_ERR_ARG, "mdp_bellman_noalloc: n_states * n_actions overflows");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess)
+    return fail(MDP_ERR_CUDA, "mdp_bellman_noalloc: cudaStreamIsCapturing failed");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(MDP_ERR_ARG, "mdp_bellman_noalloc: the stream is capturing a graph; this call "
+                             "synchronises and cannot be captured");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(MDP_ERR_CUDA, "mdp_bellman_noalloc: no usable current device");
@@ -160,15 +175,21 @@ extern "C" mdp_status mdp_bellman_noalloc(int64_t n_states, int32_t n_actions,
     }
     scratch = g_dev_ptr[dev];
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the ticket and the error flag must start at zero; results are rewritten
   if (cudaMemsetAsync(scratch, 0, kHeadBytes, s) != cudaSuccess)
     return fail(MDP_ERR_CUDA, "mdp_bellman_noalloc: clearing the scratch head failed");
   k_bellman_plain<<<static_cast<unsigned>(tiles), kTileStates, 0, s>>>(
       n_states, n_actions, row_ptr, col, val, cost, static_cast<float>(gamma), V_in, V_out,
       pi_out, r_out, static_cast<unsigned char*>(scratch));
-  if (cudaGetLastError() != cudaSuccess)
-    return fail(MDP_ERR_CUDA, "mdp_bellman_noalloc: kernel launch failed");
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    // the message names the error, so a failure left pending by an earlier
+    // unrelated call on this thread can be told apart from this launch failing
+    static thread_local char msg[192];
+    snprintf(msg, sizeof(msg), "mdp_bellman_noalloc: kernel launch reported %s (%s)",
+             cudaGetErrorName(le), cudaGetErrorString(le));
+    return fail(MDP_ERR_CUDA, msg);
+  }
   Head head;
   if (cudaMemcpyAsync(&head, scratch, sizeof(Head), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -144,7 +144,7 @@ class Server:
                 return False
             req.cancel_requested = True
             if req.handle is not None:
-                capi.mdp_cancel(req.handle)
+                self._cancel_handle(req.handle)
             return True
 
     # -- worker --------------------------------------------------------------------
@@ -184,33 +184,13 @@ class Server:
                     req.error = repr(e)
                 req.t_done = time.perf_counter()
                 self._release(req)
-        import torch
-        torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(device=self.device)
+        stream = self._worker_stream()
         while True:
             req = self._take()
             if req is None:
                 return
             try:
-                with torch.cuda.stream(stream):
-                    h = MDP.from_csr(req.mdp, store=self.store, host_input=True,
-                                     device=f"cuda:{self.device}", stream=stream)
-                    try:
-                        with self.cv:  # from here on cancel() reaches the solve
-                            req.handle = h.h
-                            stop = req.cancel_requested
-                        if stop:
-                            raise capi.MDPError(7, "cancelled before the solve started")
-                        V, pi, st = h.solve(raise_on_not_converged=False, **self.solve_opts)
-                        Vh = V.cpu()
-                        pih = pi.cpu()
-                        stream.synchronize()
-                    finally:
-                        with self.cv:
-                            req.handle = None
-                        h.close()
-                req.V, req.pi, req.stats = Vh.numpy(), pih.numpy(), st
-                req.status = st["status"]
+                self._serve_one(req, stream)
             except capi.MDPError as e:
                 req.status = e.status_name
                 req.error = str(e)
@@ -219,6 +199,45 @@ class Server:
                 req.error = repr(e)
             req.t_done = time.perf_counter()
             self._release(req)
+
+    def _worker_stream(self):
+        import torch
+        torch.cuda.set_device(self.device)
+        return torch.cuda.Stream(device=self.device)
+
+    def _open(self, req, stream):
+        """The request's handle, created from its host CSR on the worker's stream."""
+        return MDP.from_csr(req.mdp, store=self.store, host_input=True,
+                            device=f"cuda:{self.device}", stream=stream)
+
+    def _cancel_handle(self, handle):
+        capi.mdp_cancel(handle)
+
+    def _serve_one(self, req, stream):
+        import contextlib
+        import torch
+        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+            h = self._open(req, stream)
+            try:
+                with self.cv:  # from here on cancel() reaches the solve
+                    req.handle = h.h
+                    stop = req.cancel_requested
+                if stop:
+                    raise capi.MDPError(7, "cancelled before the solve started")
+                # a cancel() that lands between the lines above and the solve's
+                # first check stays pending on the handle, and the library
+                # honours it when the solve starts
+                V, pi, st = h.solve(raise_on_not_converged=False, **self.solve_opts)
+                Vh = V.cpu()
+                pih = pi.cpu()
+                if stream is not None:
+                    stream.synchronize()
+            finally:
+                with self.cv:
+                    req.handle = None
+                h.close()
+        req.V, req.pi, req.stats = Vh.numpy(), pih.numpy(), st
+        req.status = st["status"]
 
     # -- trace replay ---------------------------------------------------------------
     def run_trace(self, requests, time_scale: float = 1.0):

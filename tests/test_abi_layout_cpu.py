@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ENUMS = ["MDP_F32", "MDP_F64", "MDP_BF16", "MDP_F16", "MDP_OK", "MDP_FLAG_HOST_INPUT",
          "MDP_FLAG_NO_VALIDATE", "MDP_FLAG_AUTOTUNE", "MDP_FLAG_MAXIMIZE", "MDP_INNER_GMRES",
          "MDP_INNER_RICHARDSON", "MDP_INNER_BICGSTAB", "MDP_HISTORY", "MDP_UNSEEN_ERROR",
-         "MDP_UNSEEN_SELF_LOOP"]
+         "MDP_UNSEEN_SELF_LOOP", "MDP_MAX_RESTART"]
 STATUSES = ["MDP_OK", "MDP_ERR_ARG", "MDP_ERR_NOT_STOCHASTIC", "MDP_ERR_OOM", "MDP_ERR_CUDA",
             "MDP_ERR_NOT_CONVERGED", "MDP_ERR_TIMEOUT", "MDP_ERR_CANCELLED", "MDP_ERR_BAD_CSR",
             "MDP_ERR_NONFINITE"]
@@ -26,7 +26,8 @@ def _structs():
     from paper_2502_14474_gb300 import capi
     return {"mdp_solve_opts": capi.mdp_solve_opts, "mdp_solve_stats": capi.mdp_solve_stats,
             "mdp_eval_stats": capi.mdp_eval_stats, "mdp_info_t": capi.mdp_info_t,
-            "mdp_profile_t": capi.mdp_profile_t, "mdp_host_csr": capi.mdp_host_csr}
+            "mdp_profile_t": capi.mdp_profile_t, "mdp_host_csr": capi.mdp_host_csr,
+            "mdp_gmres_cycle_t": capi.mdp_gmres_cycle_t}
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +65,8 @@ def c_layout(tmp_path_factory):
 
 
 @pytest.mark.parametrize("name", ["mdp_solve_opts", "mdp_solve_stats", "mdp_eval_stats",
-                                  "mdp_info_t", "mdp_profile_t", "mdp_host_csr"])
+                                  "mdp_info_t", "mdp_profile_t", "mdp_host_csr",
+                                  "mdp_gmres_cycle_t"])
 def test_struct_layout_matches_the_header(c_layout, name):
     import ctypes
     layout, _ = c_layout

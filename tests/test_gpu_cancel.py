@@ -70,3 +70,28 @@ def test_serving_cancels_running_and_queued_requests():
     srv.close()
     assert a.status == "MDP_ERR_CANCELLED", a.error
     assert srv.used == 0 and srv.active == 0
+
+
+def test_cancel_before_the_call_is_honoured_once():
+    """A cancel request made while no call runs stays pending: the next solve (or
+    policy evaluation) returns MDP_ERR_CANCELLED at once, which consumes it, and
+    the call after that runs normally."""
+    import torch
+    from paper_2502_14474_gb300 import MDP, MDPError, capi
+    mdp = synth.random_sparse(5000, 4, 8, 1.0, 0.95, seed=73, dtype=np.float32)
+    h = MDP.from_csr(mdp)
+    capi.mdp_cancel(h.h)
+    with pytest.raises(MDPError) as ei:
+        h.solve(tol=1e-9)
+    assert ei.value.status_name == "MDP_ERR_CANCELLED"
+    V, pi, st = h.solve(tol=1e-9)
+    assert st["converged"]
+    assert oracle.certificate(mdp, V.cpu().numpy())["res_inf"] <= 1.01e-9
+    capi.mdp_cancel(h.h)
+    v = torch.zeros(mdp.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(MDPError) as ei:
+        h.policy_eval(pi, v, tol=1e-8)
+    assert ei.value.status_name == "MDP_ERR_CANCELLED"
+    st2 = h.policy_eval(pi, v, tol=1e-8)
+    assert st2["converged"]
+    h.close()

@@ -132,3 +132,66 @@ def test_cancel_queued_and_running_requests():
     assert srv.used == 0 and srv.active == 0
     summ = serve.summarize(reqs, 1.0)
     assert summ["completed"] == 2 and summ["failed"] == 2
+
+
+class _PendingCancelHandle:
+    """Stands in for a library handle with the C ABI's cancel rule: a cancel
+    request made before the solve starts stays pending and the solve returns
+    MDP_ERR_CANCELLED at once."""
+
+    def __init__(self, gate, entered):
+        self.h = object()
+        self.pending = False
+        self.gate, self.entered = gate, entered
+        self.solved = False
+
+    def solve(self, **kw):
+        import torch
+        from paper_2502_14474_gb300 import capi
+        self.entered.set()
+        self.gate.wait(5)          # the test cancels in this window
+        if self.pending:
+            self.pending = False
+            raise capi.MDPError(7, "cancelled before the call started")
+        self.solved = True
+        return torch.zeros(3), torch.zeros(3, dtype=torch.int32), {"status": "MDP_OK"}
+
+    def close(self):
+        pass
+
+
+def test_cancel_between_publish_and_solve_start_is_not_lost():
+    """A cancel() that lands after the worker published the request's handle but
+    before the solve's first check reaches the handle and ends the request as
+    cancelled (the solve must not run to the end with cancel() having said True)."""
+    gate, entered = threading.Event(), threading.Event()
+    handles = []
+
+    class Srv(serve.Server):
+        def _worker_stream(self):
+            return None
+
+        def _open(self, req, stream):
+            handles.append(_PendingCancelHandle(gate, entered))
+            return handles[-1]
+
+        def _cancel_handle(self, handle):
+            for fh in handles:
+                if fh.h is handle:
+                    fh.pending = True
+
+    srv = Srv(budget_bytes=100, workers=1, bytes_fn=lambda r: 1)
+    srv.solver = None
+    for w in range(srv.workers):
+        t = threading.Thread(target=srv._worker, args=(w,), daemon=True)
+        t.start()
+        srv.threads.append(t)
+    req = serve.Request(rid=0, mdp=_FakeMDP(3))
+    srv.submit(req)
+    assert entered.wait(5) and req.handle is not None
+    assert srv.cancel(req)
+    gate.set()
+    srv.close()
+    assert req.status == "MDP_ERR_CANCELLED", req.status
+    assert not handles[0].solved
+    assert srv.used == 0 and srv.active == 0

@@ -73,3 +73,55 @@ def test_noalloc_rejects_oversize_and_bad_columns():
     # the shared scratch is usable again right after a failed call
     ri, _ = capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, 0.9, V)
     assert abs(ri - float(np.min(mdp.g.reshape(mdp.n, mdp.m), axis=1).max())) <= 1e-6
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The property that defines the entry point: after a first call on the device
+    (which may load the kernel's module), further calls change neither torch's
+    allocator, nor the library's memory pool, nor the device's free memory."""
+    from paper_2502_14474_gb300 import capi
+    mdp = synth.random_sparse(20000, 4, 8, 1.0, 0.95, seed=80, dtype=np.float32)
+    rp, col, val, g = _inputs(mdp)
+    V = torch.rand(mdp.n, device="cuda")
+    V_out = torch.empty_like(V)
+    pi_out = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+    r_out = torch.empty_like(V)
+    s = torch.cuda.current_stream()
+    capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, mdp.gamma, V, V_out, pi_out, r_out,
+                             stream=s)
+    torch.cuda.synchronize()
+    dev_i = torch.cuda.current_device()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
+              capi.mdp_pool_trim(dev_i, 1 << 62), torch.cuda.mem_get_info()[0])
+    for _ in range(3):
+        capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, mdp.gamma, V, V_out, pi_out,
+                                 r_out, stream=s)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
+             capi.mdp_pool_trim(dev_i, 1 << 62), torch.cuda.mem_get_info()[0])
+    assert after == before
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises, so it refuses a stream that is capturing a graph
+    (before it enqueues anything) instead of invalidating the caller's capture."""
+    from paper_2502_14474_gb300 import capi
+    from paper_2502_14474_gb300.capi import MDPError
+    mdp = synth.random_sparse(1000, 2, 4, 1.0, 0.9, seed=81, dtype=np.float32)
+    rp, col, val, g = _inputs(mdp)
+    V = torch.zeros(mdp.n, device="cuda")
+    capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, 0.9, V)  # device set-up first
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        V2 = V + 1.0
+        torch.cuda.synchronize()
+        with pytest.raises(MDPError) as ei:
+            with torch.cuda.graph(graph, stream=s):
+                V2.add_(1.0)
+                capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, 0.9, V, stream=s)
+    assert ei.value.status_name == "MDP_ERR_ARG"
+    # the stream and the entry point are usable afterwards
+    torch.cuda.synchronize()
+    ri, _ = capi.mdp_bellman_noalloc(mdp.n, mdp.m, rp, col, val, g, 0.9, V)
+    assert abs(ri - float(np.min(mdp.g.reshape(mdp.n, mdp.m), axis=1).max())) <= 1e-6
