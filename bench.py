@@ -75,6 +75,8 @@ def _args():
                    help="inner solver of the evaluation step: GMRES (iPI), Richardson "
                         "sweeps (modified policy iteration; with --max-inner 1 it is value "
                         "iteration) or BiCGStab")
+    p.add_argument("--s-step", type=int, default=None,
+                   help="GMRES block size (0 = classical Arnoldi; default: the library's)")
     p.add_argument("--max-inner", type=int, default=None,
                    help="cap on GMRES steps per outer iteration (default 10000; 100 for "
                         "grid4096, whose early policies make the evaluation nearly singular)")
@@ -536,7 +538,7 @@ def main():
     solve_stream = torch.cuda.Stream(device=dev)
     h = MDP.from_csr(host, store=args.store, stream=solve_stream)
     opts = dict(tol=args.tol, inner_rtol=0.1, restart=args.restart, inner_norm=args.inner_norm,
-                max_inner=args.max_inner, inner=args.inner, max_outer=100000)
+                max_inner=args.max_inner, inner=args.inner, max_outer=100000, s_step=args.s_step)
 
     if args.profile_bellman:
         V = torch.zeros(host.n, dtype=torch.float64, device=dev)
@@ -682,6 +684,8 @@ def main():
             "config": {"workload": host.name, "n_states": host.n, "m": host.m, "nnz": nnz,
                        "gamma": host.gamma, "seed": 2 if args.workload == "banded4m" else 3,
                        "tol": args.tol,
+                       "s_step": (args.s_step if args.s_step is not None
+                                  else capi.mdp_default_opts().s_step),
                        "inner": (f"gmres({args.restart})" if args.inner == "gmres"
                                  else "bicgstab" if args.inner == "bicgstab"
                                  else ("value iteration" if args.max_inner == 1

@@ -113,6 +113,11 @@ typedef struct {
                            <= eta * ||T V - V||_inf (default, conservative);
                            1: additionally stop after any restart cycle whose explicit
                            policy residual has ||.||_inf <= eta * ||T V - V||_inf */
+  int32_t s_step;       /* GMRES in s-step form: 0 = classical Gram-Schmidt Arnoldi
+                           (one orthogonalisation per step); 1..8 = blocks of s_step
+                           Krylov vectors (monomial basis of A - I) orthogonalised
+                           together, with the solution update fused into the last
+                           block's pass; not combinable with cgs2 */
 } mdp_solve_opts;
 
 #define MDP_HISTORY 128
@@ -304,6 +309,8 @@ enum {
   MDP_PROF_OTHER = 7,        /* conversions, set-up kernels */
   MDP_PROF_ARNOLDI_DOTS = 8, /* Gram-Schmidt dots <w, v_i> */
   MDP_PROF_BICGSTAB_SPMV = 9,/* BiCGStab policy SpMV y = x - gamma P_pi x with its dots */
+  MDP_PROF_BLOCK_GRAM = 10,  /* s-step GMRES: Gram pass of a block + its least squares */
+  MDP_PROF_BLOCK_UPDATE = 11,/* s-step GMRES: block orthonormalisation (+ V update) */
   MDP_PROF_KINDS = 12
 };
 

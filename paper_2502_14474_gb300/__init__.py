@@ -156,10 +156,11 @@ class MDP:
 
     def solve(self, tol=1e-9, inner_rtol=0.1, restart=30, max_outer=1000, max_inner=10000,
               inner="gmres", cgs2=False, low_precision_inner=None, V_init=None,
-              raise_on_not_converged=True, inner_norm="2"):
+              raise_on_not_converged=True, inner_norm="2", s_step=None):
         """Inexact policy iteration; returns (V float64, pi int32, stats dict).
         ``inner``: "gmres" (default), "richardson" (modified policy iteration) or
-        "bicgstab"."""
+        "bicgstab".  ``s_step``: GMRES in blocks of s Krylov vectors (0 =
+        classical Arnoldi; None = the library default)."""
         torch = _torch()
         o = mdp_default_opts()
         o.tol, o.inner_rtol, o.restart = float(tol), float(inner_rtol), int(restart)
@@ -171,6 +172,10 @@ class MDP:
             low_precision_inner = self.store != "f32"
         o.low_precision_inner = 1 if low_precision_inner else 0
         o.inner_norm = 1 if str(inner_norm) in ("inf", "1") else 0
+        if s_step is not None:
+            o.s_step = int(s_step)
+        if cgs2:
+            o.s_step = 0
         V = torch.empty(self.n, dtype=torch.float64, device=self.device)
         pi = torch.empty(self.n, dtype=torch.int32, device=self.device)
         vt = _dtype_code(V_init) if V_init is not None else MDP_F64

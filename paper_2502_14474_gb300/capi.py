@@ -37,8 +37,8 @@ EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval"
                    "mdp_csr_write_petsc", "mdp_csr_free"])
 
 PROF_KINDS = ["bellman_f32", "bellman_ff", "policy_residual", "arnoldi_spmv", "arnoldi_ortho",
-              "gmres_update", "richardson", "other", "arnoldi_dots", "bicgstab_spmv", "unused10",
-              "unused11"]
+              "gmres_update", "richardson", "other", "arnoldi_dots", "bicgstab_spmv", "block_gram",
+              "block_update"]
 
 
 class MDPError(RuntimeError):
@@ -53,7 +53,7 @@ class mdp_solve_opts(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_inner", ctypes.c_int32), ("inner", ctypes.c_int32),
                 ("cgs2", ctypes.c_int32), ("low_precision_inner", ctypes.c_int32),
-                ("inner_norm", ctypes.c_int32)]
+                ("inner_norm", ctypes.c_int32), ("s_step", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):

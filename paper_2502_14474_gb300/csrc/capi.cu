@@ -61,8 +61,10 @@ struct StatusHead {
   double res_2;
   int active, jdone, converged, breakdown, restart, target_rel;
   double eta, target, beta, est;
+  int nspmv, bfin_k;
 };
 static_assert(offsetof(StatusHead, est) == offsetof(DevState, est), "DevState prefix layout");
+static_assert(offsetof(StatusHead, bfin_k) == offsetof(DevState, bfin_k), "DevState prefix layout");
 constexpr size_t kHeadBytes = sizeof(StatusHead);
 
 struct ProfRec {
@@ -122,6 +124,7 @@ struct mdp_s {
   float* d1 = nullptr;
   float* bt = nullptr;      // BiCGStab t = A s
   double* partials = nullptr;
+  double* bpart = nullptr;  // s-step Gram pass partials (allocated on first use)
   DevState* st = nullptr;
   int* flag = nullptr;      // policy range check
   StatusHead* head = nullptr;  // pinned host mirror
@@ -142,6 +145,7 @@ struct mdp_s {
     int steps;
     bool lp;
     int cgs2;
+    int sblk;
     const int32_t* pi;
     cudaGraphExec_t exec;
   };
@@ -327,6 +331,13 @@ double bytes_ortho(const Mat& A, int j, int cgs2) {
   return cgs2 ? 2.0 * one + 4.0 * (j + 2) * n : one;
 }
 double bytes_update(const Mat& A, int J) { return 4.0 * J * A.n + 16.0 * A.n; }
+// s-step block at step k with sb vectors: the Gram pass reads u_0..u_k and
+// w_1..w_sb once; the update pass reads them again and writes the sb new
+// vectors (plus 16 bytes per state of V read and written on the last block).
+double bytes_block_gram(const Mat& A, int k, int sb) { return 4.0 * A.n * (k + 1 + sb); }
+double bytes_block_update(const Mat& A, int k, int sb, bool fin) {
+  return 4.0 * A.n * (k + 1 + 2 * sb) + (fin ? 16.0 * A.n : 0.0);
+}
 double bytes_richardson(const Mat& A, bool lp) {
   const double n = A.n;
   return n * (4.0 + 2.0 * prp_bytes(A) + ppolicy_len(A) * (4.0 + (lp ? 2.0 : 4.0)) +
@@ -335,8 +346,8 @@ double bytes_richardson(const Mat& A, bool lp) {
 
 void free_all(mdp_s* h) {
   void* ptrs[] = {h->rp, h->pk, h->pk_am, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
-                  h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->bt, h->partials, h->st,
-                  h->flag};
+                  h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->bt, h->partials, h->bpart,
+                  h->st, h->flag};
   cudaStream_t fs = free_stream(h->device);
   if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
   for (void* p : ptrs)
@@ -512,6 +523,21 @@ mdp_status ensure_bicgstab(mdp_s* h, cudaStream_t s) {
   return MDP_OK;
 }
 
+// The s-step Gram pass's partial sums: one slot of kBlkMaxV x kSMax doubles
+// per chunk slot (at most one slot per 1024 states).
+mdp_status ensure_sstep(mdp_s* h, cudaStream_t s) {
+  if (h->bpart) return MDP_OK;
+  const cudaStream_t home = h->home;
+  h->home = s;
+  cudaError_t e = dalloc(h, &h->bpart, block_partials_len(h->A.num_sms, h->A.n) * sizeof(double));
+  h->home = home;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, "device allocation of the s-step partials failed");
+  }
+  return MDP_OK;
+}
+
 // Read the status prefix of the device state (synchronises the stream).
 mdp_status read_head(mdp_s* h, cudaStream_t s, bool flush = true) {
   CK(h, cudaMemcpyAsync(h->head, h->st, kHeadBytes, cudaMemcpyDeviceToHost, s));
@@ -566,7 +592,7 @@ cudaError_t enqueue_steps(mdp_s* h, const int32_t* pi, int j0, int j1, int steps
                           int cgs2, cudaStream_t s) {
   for (int j = j0; j < j1; ++j) {
     cudaError_t e = run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), j, [&] {
-      return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, steps, h->partials, h->st, s);
+      return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, j, 1.f, h->partials, h->st, s);
     });
     if (e != cudaSuccess) return e;
     e = run(h, s, MDP_PROF_ARNOLDI_DOTS, 1, bytes_dots(h->A, j), j, [&] {
@@ -587,10 +613,47 @@ cudaError_t enqueue_update(mdp_s* h, cudaStream_t s) {
   });
 }
 
-cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+// Blocks b0 .. b1-1 of an s-step cycle of `steps` steps with blocks of sblk
+// vectors (k_sstep.cu): per block sb policy-row SpMVs of the monomial basis,
+// the Gram pass (with the block's least-squares steps) and the update pass
+// (which adds the solution update on the block that ends the cycle).
+cudaError_t enqueue_blocks(mdp_s* h, const int32_t* pi, int b0, int b1, int steps, bool lp,
+                           int sblk, cudaStream_t s) {
+  for (int b = b0; b < b1; ++b) {
+    const int k = b * sblk;
+    if (k >= steps) break;
+    const int sb = std::min(sblk, steps - k);
+    for (int i = 0; i < sb; ++i) {
+      cudaError_t e = run(h, s, MDP_PROF_ARNOLDI_SPMV, 1, bytes_spmv(h->A, lp), k + i, [&] {
+        return launch_arnoldi_spmv(h->A, lp, pi, h->basis, h->ld, k + i, 0.f, h->partials, h->st,
+                                   s);
+      });
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = run(h, s, MDP_PROF_BLOCK_GRAM, 1, bytes_block_gram(h->A, k, sb), k, [&] {
+      return launch_block_dots(h->A, h->basis, h->ld, k, sb, sblk, steps, h->bpart, h->st, s);
+    });
+    if (e != cudaSuccess) return e;
+    e = run(h, s, MDP_PROF_BLOCK_UPDATE, 1, bytes_block_update(h->A, k, sb, false), k, [&] {
+      return launch_block_update(h->A, h->basis, h->ld, k, sb, sblk, h->V, h->st, s);
+    });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int n_blocks(int steps, int sblk) { return (steps + sblk - 1) / sblk; }
+
+cudaError_t enqueue_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2, int sblk,
                           cudaStream_t s) {
+  if (sblk > 0) return enqueue_blocks(h, pi, 0, n_blocks(steps, sblk), steps, lp, sblk, s);
   const cudaError_t e = enqueue_steps(h, pi, 0, steps, steps, lp, cgs2, s);
   return e != cudaSuccess ? e : enqueue_update(h, s);
+}
+
+int64_t cycle_launches(int steps, int cgs2, int sblk) {
+  if (sblk > 0) return static_cast<int64_t>(steps) + 2 * n_blocks(steps, sblk);
+  return static_cast<int64_t>(steps) * (cgs2 ? 5 : 3) + 1;
 }
 
 // Below this many states a GMRES step takes a few microseconds and the launches
@@ -603,14 +666,15 @@ constexpr int kChunkSteps = 8;
 // The captured graph of a cycle configuration (captured once the handle has
 // run four eager cycles, which also initialised every launcher); nullptr when
 // capture is not possible (legacy default stream, profiling, or a capture error).
-cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
+cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2, int sblk,
                             cudaStream_t s) {
   // capture pays off for handles that run many cycles (long or repeated
   // solves); short-lived handles stay eager (instantiation costs ~a cycle)
   if (h->prof.on || s == nullptr || h->eager_cycles < 4 || getenv("MDP_NO_GRAPHS"))
     return nullptr;
   for (auto& g : h->graphs)
-    if (g.steps == steps && g.lp == lp && g.cgs2 == cgs2 && g.pi == pi) return g.exec;
+    if (g.steps == steps && g.lp == lp && g.cgs2 == cgs2 && g.sblk == sblk && g.pi == pi)
+      return g.exec;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
@@ -621,7 +685,7 @@ cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int
     return nullptr;
   }
   const int64_t launches = h->launches;
-  cudaError_t e = enqueue_cycle(h, pi, steps, lp, cgs2, s);
+  cudaError_t e = enqueue_cycle(h, pi, steps, lp, cgs2, sblk, s);
   h->launches = launches;
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &graph);
@@ -632,7 +696,7 @@ cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int
       cudaGraphExecDestroy(h->graphs.front().exec);
       h->graphs.erase(h->graphs.begin());
     }
-    h->graphs.push_back({steps, lp, cgs2, pi, exec});
+    h->graphs.push_back({steps, lp, cgs2, sblk, pi, exec});
   } else {
     exec = nullptr;
     cudaGetLastError();
@@ -644,14 +708,26 @@ cudaGraphExec_t cycle_graph(mdp_s* h, const int32_t* pi, int steps, bool lp, int
 // One GMRES restart cycle on the current device residual (already in u_0 with
 // the cycle begun by the kernel that produced it): `steps` Arnoldi steps and
 // the solution update, replayed from a captured graph when possible; then the
-// cycle's outcome is read back.
-mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2,
-                       cudaStream_t s, int* jdone, int* converged) {
+// cycle's outcome is read back.  sblk > 0 runs the cycle in s-step blocks of
+// sblk vectors.  *jdone: the steps the solution update used; *nspmv: the
+// policy-row SpMVs the cycle ran (s-step: up to sblk - 1 more than *jdone).
+mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2, int sblk,
+                       cudaStream_t s, int* jdone, int* converged, int* nspmv) {
   const size_t first = h->prof.pending.size();
   const bool chunked =
       h->A.n < kChunkedBelow && steps > kChunkSteps && !getenv("MDP_NO_CYCLE_CHUNKS");
-  cudaGraphExec_t g = chunked ? nullptr : cycle_graph(h, pi, steps, lp, cgs2, s);
-  if (chunked) {
+  cudaGraphExec_t g = chunked ? nullptr : cycle_graph(h, pi, steps, lp, cgs2, sblk, s);
+  if (chunked && sblk > 0) {
+    const int per = std::max(1, kChunkSteps / sblk), nb = n_blocks(steps, sblk);
+    for (int b0 = 0; b0 < nb; b0 += per) {
+      const int b1 = std::min(nb, b0 + per);
+      CK(h, enqueue_blocks(h, pi, b0, b1, steps, lp, sblk, s));
+      if (b1 == nb) break;
+      mdp_status rc = read_head(h, s, false);
+      if (rc != MDP_OK) return rc;
+      if (!h->head->active) break;
+    }
+  } else if (chunked) {
     for (int j0 = 0; j0 < steps; j0 += kChunkSteps) {
       const int j1 = std::min(steps, j0 + kChunkSteps);
       CK(h, enqueue_steps(h, pi, j0, j1, steps, lp, cgs2, s));
@@ -663,9 +739,9 @@ mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2
     CK(h, enqueue_update(h, s));
   } else if (g) {
     CK(h, cudaGraphLaunch(g, s));
-    h->launches += static_cast<int64_t>(steps) * (cgs2 ? 5 : 3) + 1;
+    h->launches += cycle_launches(steps, cgs2, sblk);
   } else {
-    CK(h, enqueue_cycle(h, pi, steps, lp, cgs2, s));
+    CK(h, enqueue_cycle(h, pi, steps, lp, cgs2, sblk, s));
     h->eager_cycles += 1;
   }
   const size_t upd = h->prof.pending.empty() ? 0 : h->prof.pending.size() - 1;
@@ -673,11 +749,20 @@ mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2
   if (rc != MDP_OK) return rc;
   *jdone = h->head->jdone;
   *converged = h->head->converged;
+  *nspmv = h->head->nspmv;
   // launches of steps past the end of the cycle returned at once
+  const int fin_k = h->head->bfin_k;
   for (size_t i = first; i < h->prof.pending.size(); ++i) {
     ProfRec& r = h->prof.pending[i];
-    if (r.j >= *jdone) r.skipped = true;
-    if (i == upd && r.kind == MDP_PROF_GMRES_UPDATE) {
+    if (r.kind == MDP_PROF_BLOCK_GRAM || r.kind == MDP_PROF_BLOCK_UPDATE) {
+      r.skipped = r.j > fin_k;
+      if (r.kind == MDP_PROF_BLOCK_UPDATE && r.j == fin_k) r.bytes += 16.0 * h->A.n;
+    } else if (sblk > 0 && r.kind == MDP_PROF_ARNOLDI_SPMV) {
+      r.skipped = r.j >= *nspmv;
+    } else if (r.j >= *jdone) {
+      r.skipped = true;
+    }
+    if (sblk == 0 && i == upd && r.kind == MDP_PROF_GMRES_UPDATE) {
       r.bytes = bytes_update(h->A, *jdone);
       r.skipped = *jdone == 0;
     }
@@ -1198,8 +1283,8 @@ mdp_status mdp_policy_eval(mdp_t h, const int32_t* pi, void* v_inout, mdp_dtype 
     const int steps = std::min(restart, max_iters - es.iters);
     rc = set_cycle(h, steps, 0, 0.0, tol, 1, s);
     if (rc != MDP_OK) return rc;
-    int jdone = 0, conv = 0;
-    rc = gmres_cycle(h, pi, steps, false, 0, s, &jdone, &conv);
+    int jdone = 0, conv = 0, nspmv = 0;
+    rc = gmres_cycle(h, pi, steps, false, 0, 0, s, &jdone, &conv, &nspmv);
     if (rc != MDP_OK) return rc;
     es.iters += jdone;
     es.cycles += 1;
@@ -1248,6 +1333,8 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
       o.inner != MDP_INNER_BICGSTAB)
     return fail(MDP_ERR_ARG, "unknown inner solver");
   if (o.inner_norm != 0 && o.inner_norm != 1) return fail(MDP_ERR_ARG, "inner_norm is 0 or 1");
+  if (o.s_step < 0 || o.s_step > kSMax) return fail(MDP_ERR_ARG, "s_step in [0, %d]", kSMax);
+  if (o.s_step > 0 && o.cgs2) return fail(MDP_ERR_ARG, "cgs2 applies to s_step = 0 only");
   const bool lp = o.low_precision_inner != 0;
   if (lp && !h->val16 && !h->lpk)
     return fail(MDP_ERR_ARG, "low_precision_inner needs store_t BF16/F16");
@@ -1256,9 +1343,14 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
   if (h->cancel.exchange(0)) return fail(MDP_ERR_CANCELLED, "cancelled before the call started");
   DoneMark dm{h, s};
   mdp_status rc = MDP_OK;
-  if (o.inner == MDP_INNER_GMRES) rc = ensure_basis(h, o.restart, s);
-  else if (o.inner == MDP_INNER_RICHARDSON) rc = ensure_richardson(h, s);
-  else rc = ensure_bicgstab(h, s);
+  if (o.inner == MDP_INNER_GMRES) {
+    rc = ensure_basis(h, o.restart, s);
+    if (rc == MDP_OK && o.s_step > 0) rc = ensure_sstep(h, s);
+  } else if (o.inner == MDP_INNER_RICHARDSON) {
+    rc = ensure_richardson(h, s);
+  } else {
+    rc = ensure_bicgstab(h, s);
+  }
   if (rc != MDP_OK) return rc;
   const Mat& A = h->A;
   if (V_init)
@@ -1321,12 +1413,14 @@ mdp_status mdp_solve(mdp_t h, const mdp_solve_opts* opts_in, const void* V_init,
           rc = set_cycle(h, steps, 1, o.inner_rtol, 0.0, 0, s);
           if (rc != MDP_OK) return rc;
         }
-        int jdone = 0, conv = 0;
-        rc = gmres_cycle(h, h->pi, steps, lp, o.cgs2, s, &jdone, &conv);
+        int jdone = 0, conv = 0, nspmv = 0;
+        rc = gmres_cycle(h, h->pi, steps, lp, o.cgs2, o.s_step, s, &jdone, &conv, &nspmv);
         if (rc != MDP_OK) return rc;
-        used += jdone;
-        ss.policy_sweeps += jdone;
-        transitions += policy_nnz * jdone;
+        // work counts every policy SpMV the cycle ran (an s-step cycle that
+        // ends inside a block ran the whole block's SpMVs)
+        used += nspmv;
+        ss.policy_sweeps += nspmv;
+        transitions += policy_nnz * nspmv;
         if (conv || used >= o.max_inner || jdone == 0) break;
         if (h->cancel.load()) break;
         // refinement residual of the policy system, next cycle from it

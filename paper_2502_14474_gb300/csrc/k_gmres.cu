@@ -87,6 +87,7 @@ __device__ void givens_step(DevState* st, int j, double nrm) {
   const double est = fabs(st->gv[j + 1]);
   st->est = est;
   st->jdone = j + 1;
+  st->nspmv = j + 1;
   const bool conv = breakdown || est <= st->target;
   if (conv || j + 1 >= st->restart) {
     st->active = 0;
@@ -462,11 +463,11 @@ __global__ void k_bicg_p(int64_t n, const float* __restrict__ r, const float* __
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
-                                int64_t ld, int j, int restart, double* partials, DevState* st,
+                                int64_t ld, int j, float cdiag, double* partials, DevState* st,
                                 cudaStream_t s) {
-  if (!lp) return launch_arnoldi_spmv_f32(A, pi, basis, ld, j, restart, partials, st, s);
-  if (A.store_t == 3) return launch_arnoldi_spmv_f16(A, pi, basis, ld, j, restart, partials, st, s);
-  return launch_arnoldi_spmv_bf16(A, pi, basis, ld, j, restart, partials, st, s);
+  if (!lp) return launch_arnoldi_spmv_f32(A, pi, basis, ld, j, cdiag, partials, st, s);
+  if (A.store_t == 3) return launch_arnoldi_spmv_f16(A, pi, basis, ld, j, cdiag, partials, st, s);
+  return launch_arnoldi_spmv_bf16(A, pi, basis, ld, j, cdiag, partials, st, s);
 }
 
 // Grid over thread-quads (4 states per thread) for the basis streams.

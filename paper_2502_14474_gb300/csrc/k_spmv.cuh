@@ -32,12 +32,14 @@ __device__ __forceinline__ void ring_fill_f32(float* ring, int mask, const float
 // ||xout - xin||_2 reduced in a fixed order into st->res_2 by the last block,
 // st->jdone counting the sweeps that ran and st->active cleared once the
 // residual meets st->target (later sweeps of the batch return at once).
-// Otherwise xin = u_j, xout = u_{j+1} = scale_j (u_j - gamma P_pi u_j).
+// Otherwise xin = u_j, xout = scale_j (cdiag u_j - gamma P_pi u_j): with
+// cdiag = 1 that is u_{j+1} = A v_j of the Arnoldi process, with cdiag = 0 the
+// next vector (A - I) v_j = -gamma P_pi v_j of an s-step block's monomial basis.
 template <typename IdxT, int VW, typename PV, int NT, bool WIN, bool RICH>
 __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
     k_arnoldi_spmv(Csr<IdxT> P, int64_t states_per_block, int64_t band, int ring_log2,
                    const int32_t* __restrict__ pi, const float* __restrict__ xin,
-                   float* __restrict__ xout, int j, const float* __restrict__ rvec,
+                   float* __restrict__ xout, int j, float cdiag, const float* __restrict__ rvec,
                    double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int TS = 4 * NT;  // states per tile (four passes of NT states)
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 ? 2 : 1))
       const double df = static_cast<double>(v - xv);
       racc += df * df;
     } else {
-      uw[s] = sj * fmaf(-P.gamma, d, xv);
+      uw[s] = sj * fmaf(-P.gamma, d, cdiag * xv);
     }
   };
   const PV* val = sizeof(PV) == 4 ? reinterpret_cast<const PV*>(P.val)
@@ -342,6 +344,7 @@ struct SpmvArgs {
   int j;
   const float* rvec;
   double* partials;
+  float cdiag;
 };
 
 template <typename IdxT, int VW, typename PV, int NT, bool WIN, bool RICH>
@@ -364,7 +367,8 @@ cudaError_t spmv_launch(const Mat& A, const int32_t* pi, const SpmvArgs& a, int 
   if (per < NT) per = NT;
   const int64_t blocks = (A.n + per - 1) / per;
   kern<<<static_cast<unsigned>(blocks < 1 ? 1 : blocks), NT, smem, s>>>(
-      csr_view<IdxT>(A), per, A.band, lg, pi, a.xin, a.xout, a.j, a.rvec, a.partials, st);
+      csr_view<IdxT>(A), per, A.band, lg, pi, a.xin, a.xout, a.j, a.cdiag, a.rvec, a.partials,
+      st);
   return cudaGetLastError();
 }
 
@@ -404,16 +408,16 @@ cudaError_t spmv_entry(const Mat& A, const int32_t* pi, const SpmvArgs& a, DevSt
 // The two entry points every probability type's translation unit instantiates.
 template <typename PV>
 cudaError_t arnoldi_spmv_tu(const Mat& A, const int32_t* pi, float* basis, int64_t ld, int j,
-                            DevState* st, cudaStream_t s) {
+                            float cdiag, DevState* st, cudaStream_t s) {
   const SpmvArgs a{basis + static_cast<int64_t>(j) * ld, basis + static_cast<int64_t>(j + 1) * ld,
-                   j, nullptr, nullptr};
+                   j, nullptr, nullptr, cdiag};
   return spmv_entry<PV, false>(A, pi, a, st, s);
 }
 
 template <typename PV>
 cudaError_t richardson_tu(const Mat& A, const int32_t* pi, const float* r, const float* d_in,
                           float* d_out, double* partials, DevState* st, cudaStream_t s) {
-  const SpmvArgs a{d_in, d_out, 0, r, partials};
+  const SpmvArgs a{d_in, d_out, 0, r, partials, 1.f};
   return spmv_entry<PV, true>(A, pi, a, st, s);
 }
 

@@ -6,11 +6,10 @@
 namespace mdpk {
 
 cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
-                                    int j, int restart, double* partials, DevState* st,
+                                    int j, float cdiag, double* partials, DevState* st,
                                     cudaStream_t s) {
-  (void)restart;
   (void)partials;
-  return arnoldi_spmv_tu<float>(A, pi, basis, ld, j, st, s);
+  return arnoldi_spmv_tu<float>(A, pi, basis, ld, j, cdiag, st, s);
 }
 
 cudaError_t launch_richardson_f32(const Mat& A, const int32_t* pi, const float* r,

@@ -1,0 +1,557 @@
+// s-step GMRES for the policy-evaluation system (I - gamma P_pi) d = r.
+//
+// Classical Gram-Schmidt Arnoldi streams the whole basis twice per step (the
+// dots, then the subtraction).  The s-step form (Chronopoulos & Gear 1989;
+// Hoemmen 2010, "Communication-avoiding Krylov subspace methods", ch. 3)
+// builds a block of sb Krylov vectors with sb policy-row SpMVs first and
+// orthogonalises the whole block against the basis at once, so the basis is
+// streamed twice per block instead of twice per step.
+//
+// Block starting at step k (orthonormal q_0..q_k in basis columns 0..k, q_v =
+// u_v * scale_v):
+//   SpMVs   w_1 = (A - I) q_k, w_{i+1} = (A - I) w_i  (= -gamma P_pi w_i; the
+//           monomial basis of A - I), w_i stored in column k+i (k_spmv.cuh,
+//           cdiag = 0).
+//   Gram    one pass over [Q W]: G = [Q W]^T W, C = Q^T W, and the block's own
+//           Gram matrix W^T W; products are summed in FP32 over 32 entries per
+//           lane, then in float-float, so that the Pythagorean form below keeps
+//           its digits (k_block_dots).  Its last block runs the small FP64
+//           steps (block_ls): R^T R = W^T W - C^T C (Cholesky; "BCGS-PIP",
+//           Carson, Lund, Rozloznik & Thomas 2021), the new Hessenberg columns
+//           from A [q_k, W] = [q_k, W] B (B: ones on the diagonal and the
+//           subdiagonal), the Givens rotations and the convergence test of each
+//           new column, and at the end of the cycle the back-solve R y = g.
+//   Update  one pass: q_{k+1+i} = ((W - Q C) R^{-1})_i written over w_{i+1};
+//           on the block that ends the cycle the same pass also adds the
+//           solution update V += sum_v y_v q_v (it reads every q_v anyway),
+//           so no separate update kernel runs (k_block_update).
+// A pivot of the Cholesky factor below a relative 1e-9 of its column's norm
+// is an exact dependence of the block (an invariant subspace): its Hessenberg
+// column gets a zero subdiagonal and the cycle ends there, as an Arnoldi
+// breakdown does.
+#include "k_rows.cuh"
+#include "launch.h"
+
+namespace mdpk {
+
+constexpr int kBlkThreads = 256;
+constexpr int kBlkChunk = 1024;             // states of the W block staged per chunk
+constexpr int kBlkVPW = 2;                  // streamed vectors per warp
+constexpr int kBlkVPG = (kBlkThreads / 32) * kBlkVPW;  // vectors per group (16)
+constexpr int kBlkStride = kBlkMaxV * kSMax;           // doubles per partial slot
+constexpr int kBlkRun = 8;                  // chunk slots per first-level reduction
+constexpr double kPivotRel = 1e-9;          // dependence threshold on R_ii^2 / ||w_i||^2
+
+// ---------------------------------------------------------------------------
+// The small steps of a block (run by the whole last block of the Gram pass;
+// FP64).  k: first step of the block, sb: block vectors, restart: cycle length.
+// ---------------------------------------------------------------------------
+__device__ void block_ls(DevState* st, int k, int sb, int restart) {
+  __shared__ double C[kMaxBasis * kSMax];  // C[v * kSMax + i] = <q_v, w_{i+1}>
+  __shared__ double Sm[kSMax * kSMax];     // W^T W - C^T C, then R (upper)
+  __shared__ double Ri[kSMax * kSMax];     // R^{-1}
+  __shared__ double hc[kSMax][kBlkMaxV];   // new Hessenberg columns
+  __shared__ int s_ncol, s_nnew;
+  const int tid = threadIdx.x;
+  const int nq = k + 1;
+  // C from the Gram block: dots with the raw columns times their scales
+  for (int t = tid; t < nq * kSMax; t += blockDim.x) {
+    const int v = t / kSMax, i = t % kSMax;
+    C[t] = i < sb ? st->G[v * kSMax + i] * st->scale[v] : 0.0;
+  }
+  __syncthreads();
+  for (int t = tid; t < kSMax * kSMax; t += blockDim.x) {
+    const int i = t / kSMax, j = t % kSMax;
+    double sij = 0.0;
+    if (i < sb && j < sb) {
+      sij = st->G[(nq + i) * kSMax + j];
+      for (int v = 0; v < nq; ++v) sij -= C[v * kSMax + i] * C[v * kSMax + j];
+    }
+    Sm[t] = sij;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // Cholesky Sm = R^T R in place (upper triangle); stop at the first
+    // dependent column c: R_cc = 0, the columns after it are dropped
+    int nnew = sb, ncol = sb;
+    for (int j = 0; j < sb; ++j) {
+      for (int i = 0; i < j; ++i) {
+        double t = Sm[i * kSMax + j];
+        for (int l = 0; l < i; ++l) t -= Sm[l * kSMax + i] * Sm[l * kSMax + j];
+        Sm[i * kSMax + j] = t / Sm[i * kSMax + i];
+      }
+      double d = Sm[j * kSMax + j];
+      for (int l = 0; l < j; ++l) d -= Sm[l * kSMax + j] * Sm[l * kSMax + j];
+      const double wn = st->G[(nq + j) * kSMax + j];  // ||w_{j+1}||^2
+      if (!(d > kPivotRel * wn) || !(wn > 0.0)) {
+        Sm[j * kSMax + j] = 0.0;
+        nnew = j;
+        ncol = j + 1;
+        break;
+      }
+      Sm[j * kSMax + j] = sqrt(d);
+    }
+    for (int t = 0; t < kSMax * kSMax; ++t) {  // R: upper triangle of the kept columns
+      const int i = t / kSMax, j = t % kSMax;
+      if (i > j || j >= ncol) Sm[t] = 0.0;
+    }
+    // R^{-1} of the leading nnew x nnew factor (upper triangular)
+    for (int t = 0; t < kSMax * kSMax; ++t) Ri[t] = 0.0;
+    for (int j = 0; j < nnew; ++j) {
+      Ri[j * kSMax + j] = 1.0 / Sm[j * kSMax + j];
+      for (int i = j - 1; i >= 0; --i) {
+        double t = 0.0;
+        for (int l = i + 1; l <= j; ++l) t += Sm[i * kSMax + l] * Ri[l * kSMax + j];
+        Ri[i * kSMax + j] = -t / Sm[i * kSMax + i];
+      }
+    }
+    s_ncol = ncol;
+    s_nnew = nnew;
+  }
+  __syncthreads();
+  const int ncol = s_ncol, nnew = s_nnew;
+  // New Hessenberg columns, one row per thread.  With z_0 = q_k and
+  // z_j = w_j = sum_v C[v][j-1] q_v + sum_{l<j} R[l][j-1] q_{k+1+l}, the
+  // basis relation A z_i = z_{i+1} + z_i gives
+  //   A q_k     = z_1 + z_0
+  //   A q_{k+i} = (z_{i+1} + z_i - sum_{v<k} C[v][i-1] A q_v - C[k][i-1] A q_k
+  //                - sum_{l<i-1} R[l][i-1] A q_{k+1+l}) / R[i-1][i-1],
+  // with A q_v (v < k) the earlier columns of the cycle (Hraw, unrotated).
+  const int rows = k + ncol + 1;
+  for (int m = tid; m < rows; m += blockDim.x) {
+    auto coefz = [&](int j) -> double {  // row m of z_j (j >= 1)
+      if (m <= k) return C[m * kSMax + (j - 1)];
+      const int l = m - k - 1;
+      return l < j ? Sm[l * kSMax + (j - 1)] : 0.0;
+    };
+    double h0 = coefz(1) + (m == k ? 1.0 : 0.0);
+    hc[0][m] = h0;
+    for (int i = 1; i < ncol; ++i) {
+      double t = coefz(i + 1) + coefz(i);
+      for (int v = (m > 0 ? m - 1 : 0); v < k; ++v)
+        t -= C[v * kSMax + (i - 1)] * st->Hraw[static_cast<int64_t>(v) * kMaxBasis + m];
+      t -= C[k * kSMax + (i - 1)] * hc[0][m];
+      for (int l = 0; l < i - 1; ++l) t -= Sm[l * kSMax + (i - 1)] * hc[l + 1][m];
+      hc[i][m] = t / Sm[(i - 1) * kSMax + (i - 1)];
+    }
+  }
+  __syncthreads();
+  // store the raw columns (rows beyond the subdiagonal are zero by construction)
+  for (int t = tid; t < ncol * kMaxBasis; t += blockDim.x) {
+    const int i = t / kMaxBasis, m = t % kMaxBasis;
+    const int j = k + i;
+    const double v = m <= j + 1 ? hc[i][m] : 0.0;
+    st->Hraw[static_cast<int64_t>(j) * kMaxBasis + m] = v;
+    st->H[static_cast<int64_t>(j) * kMaxBasis + m] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // update coefficients on the raw columns, the new vectors' scales
+    for (int v = 0; v < nq; ++v)
+      for (int i = 0; i < kSMax; ++i)
+        st->bC[v * kSMax + i] = static_cast<float>(C[v * kSMax + i] * st->scale[v]);
+    for (int t = 0; t < kSMax * kSMax; ++t) st->bRinv[t] = static_cast<float>(Ri[t]);
+    for (int i = 0; i < nnew; ++i) st->scale[k + 1 + i] = 1.0;
+    st->bsb = nnew;
+    st->nspmv = k + sb;
+    // Givens rotations of the new columns in order, convergence per column
+    bool end = false, conv = false, brk = false;
+    int J = k + ncol;
+    for (int i = 0; i < ncol && !end; ++i) {
+      const int j = k + i;
+      double* h = st->H + static_cast<int64_t>(j) * kMaxBasis;
+      for (int l = 0; l < j; ++l) {
+        const double t = st->cs[l] * h[l] + st->sn[l] * h[l + 1];
+        h[l + 1] = -st->sn[l] * h[l] + st->cs[l] * h[l + 1];
+        h[l] = t;
+      }
+      const double a = h[j], b = h[j + 1];
+      const bool breakdown = !(b != 0.0);
+      const double den = hypot(a, b);
+      double c = 1.0, sn = 0.0;
+      if (den > 0.0) {
+        c = a / den;
+        sn = b / den;
+      }
+      st->cs[j] = c;
+      st->sn[j] = sn;
+      h[j] = den > 0.0 ? den : a;
+      h[j + 1] = 0.0;
+      st->gv[j + 1] = -sn * st->gv[j];
+      st->gv[j] = c * st->gv[j];
+      const double est = fabs(st->gv[j + 1]);
+      st->est = est;
+      if (breakdown || est <= st->target) {
+        end = true;
+        conv = true;
+        brk = breakdown;
+        J = j + 1;
+      }
+    }
+    if (!end && k + ncol >= restart) end = true;
+    st->jdone = J;
+    if (end) {
+      st->active = 0;
+      st->converged = conv ? 1 : 0;
+      st->breakdown = brk ? 1 : 0;
+      st->bfin_k = k;
+      for (int i = J - 1; i >= 0; --i) {
+        double t = st->gv[i];
+        for (int l = i + 1; l < J; ++l) t -= st->H[static_cast<int64_t>(l) * kMaxBasis + i] * st->y[l];
+        const double d = st->H[static_cast<int64_t>(i) * kMaxBasis + i];
+        st->y[i] = d != 0.0 ? t / d : 0.0;
+      }
+      for (int v = 0; v < kBlkMaxV; ++v)
+        st->bY[v] = v < J ? static_cast<float>(st->y[v] * (v <= k ? st->scale[v] : 1.0)) : 0.f;
+      st->last_J = J;
+      st->last_beta = st->beta;
+      st->last_est = st->est;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram pass: G[v][i] = <x_v, w_{i+1}> for x = [u_0..u_k, w_1..w_sb] (raw
+// columns 0..k+sb), i < sb.  Block (group gx, slot y): the warps stream the
+// group's vectors (kBlkVPW each) over the slot's chunks, with the chunk of W
+// staged in shared memory.  Partials: one FP64 value per (slot, v, i), reduced
+// in two fixed-order levels as in k_gs_dots (runs of eight slots, then the
+// runs of a group), then the last group runs block_ls.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kBlkThreads)
+    k_block_dots(int64_t n, int64_t n_chunks, int vg, const float* __restrict__ basis,
+                 int64_t ld, int k, int sb, int restart, double* __restrict__ partials,
+                 DevState* __restrict__ st) {
+  if (!st->active) return;
+  constexpr int CQ = kBlkChunk / 4;  // quads per staged vector
+  __shared__ __align__(16) float4 wsm[S * CQ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gx = static_cast<int>(blockIdx.x % vg);
+  const int64_t slot = blockIdx.x / vg, slots = gridDim.x / vg;
+  const int nv = k + 1 + sb;
+  int vid[kBlkVPW];
+  bool vok[kBlkVPW];
+#pragma unroll
+  for (int u = 0; u < kBlkVPW; ++u) {
+    vid[u] = gx * kBlkVPG + warp * kBlkVPW + u;
+    vok[u] = vid[u] < nv;
+  }
+  float hi[kBlkVPW][S], lo[kBlkVPW][S];
+#pragma unroll
+  for (int u = 0; u < kBlkVPW; ++u)
+#pragma unroll
+    for (int i = 0; i < S; ++i) hi[u][i] = lo[u][i] = 0.f;
+  for (int64_t c = slot; c < n_chunks; c += slots) {
+    const int64_t c0 = c * kBlkChunk;
+    const int len = static_cast<int>(n - c0 < kBlkChunk ? n - c0 : kBlkChunk);
+    __syncthreads();  // the previous chunk's readers are done with wsm
+    for (int q = threadIdx.x; q < S * CQ; q += kBlkThreads) {
+      const int i = q / CQ, e = 4 * (q % CQ);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < sb) {
+        const float* src = basis + static_cast<int64_t>(k + 1 + i) * ld + c0;
+        if (e + 3 < len) {
+          v = __ldcg(reinterpret_cast<const float4*>(src + e));
+        } else if (e < len) {
+          v.x = src[e];
+          if (e + 1 < len) v.y = src[e + 1];
+          if (e + 2 < len) v.z = src[e + 2];
+        }
+      }
+      wsm[q] = v;
+    }
+    __syncthreads();
+    if (!vok[0]) continue;
+    float acc[kBlkVPW][S];
+#pragma unroll
+    for (int u = 0; u < kBlkVPW; ++u)
+#pragma unroll
+      for (int i = 0; i < S; ++i) acc[u][i] = 0.f;
+    const int nq4 = len >> 2;
+    for (int qd = lane; qd < nq4; qd += 32) {
+      float4 x[kBlkVPW];
+#pragma unroll
+      for (int u = 0; u < kBlkVPW; ++u)
+        x[u] = vok[u] ? __ldcs(reinterpret_cast<const float4*>(
+                            basis + static_cast<int64_t>(vid[u]) * ld + c0) + qd)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const float4 w = wsm[i * CQ + qd];
+#pragma unroll
+        for (int u = 0; u < kBlkVPW; ++u)
+          acc[u][i] = fmaf(x[u].x, w.x, fmaf(x[u].y, w.y, fmaf(x[u].z, w.z,
+                                                                fmaf(x[u].w, w.w, acc[u][i]))));
+      }
+    }
+    if (lane == 0) {  // ragged end of the last chunk, entry by entry
+      const float* ws = reinterpret_cast<const float*>(wsm);
+      for (int e = 4 * nq4; e < len; ++e)
+#pragma unroll
+        for (int u = 0; u < kBlkVPW; ++u) {
+          const float xe = vok[u] ? basis[static_cast<int64_t>(vid[u]) * ld + c0 + e] : 0.f;
+#pragma unroll
+          for (int i = 0; i < S; ++i) acc[u][i] = fmaf(xe, ws[i * kBlkChunk + e], acc[u][i]);
+        }
+    }
+    // fold this chunk's FP32 runs into the float-float sums
+#pragma unroll
+    for (int u = 0; u < kBlkVPW; ++u)
+#pragma unroll
+      for (int i = 0; i < S; ++i) ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
+  }
+  // warp sums (float-float) and the slot's partials
+#pragma unroll
+  for (int u = 0; u < kBlkVPW; ++u)
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        ff_merge(hi[u][i], lo[u][i], __shfl_xor_sync(0xffffffffu, hi[u][i], o),
+                 __shfl_xor_sync(0xffffffffu, lo[u][i], o));
+    }
+  if (lane == 0) {
+#pragma unroll
+    for (int u = 0; u < kBlkVPW; ++u)
+      if (vok[u])
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+          if (i < sb)
+            partials[slot * kBlkStride + vid[u] * kSMax + i] =
+                static_cast<double>(hi[u][i]) + static_cast<double>(lo[u][i]);
+  }
+  __shared__ bool s_last;
+  // the group's (vector, column) values, one per thread
+  const int t = threadIdx.x;
+  const int tv = gx * kBlkVPG + t / kSMax, ti = t % kSMax;
+  const bool tok = t < kBlkVPG * kSMax && tv < nv && ti < sb;
+  // level 1: the last block of this run of slots sums the run in slot order
+  const int64_t run = slot / kBlkRun, runs = (slots + kBlkRun - 1) / kBlkRun;
+  const int64_t run_len = min(static_cast<int64_t>(kBlkRun), slots - run * kBlkRun);
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->dots_run[gx][run], 1u) == run_len - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tok) {
+    const double* pr = partials + run * kBlkRun * kBlkStride + tv * kSMax + ti;
+    double sum = 0.0;
+    for (int r = 0; r < run_len; ++r) sum += __ldcg(pr + r * kBlkStride);
+    partials[run * kBlkRun * kBlkStride + tv * kSMax + ti] = sum;
+  }
+  if (t == 0) st->dots_run[gx][run] = 0;
+  // level 2: the last run of this group sums the runs in order
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->dots_group[gx], 1u) == runs - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tok) {
+    double sum = 0.0;
+    for (int64_t r = 0; r < runs; ++r)
+      sum += __ldcg(partials + r * kBlkRun * kBlkStride + tv * kSMax + ti);
+    st->G[tv * kSMax + ti] = sum;
+  }
+  if (t == 0) st->dots_group[gx] = 0;
+  // level 3: the last group runs the block's small steps
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->blk_groups, 1u) == static_cast<unsigned>(vg) - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (t == 0) st->blk_groups = 0;
+  block_ls(st, k, sb, restart);
+}
+
+// ---------------------------------------------------------------------------
+// Update pass: q_{k+1+i} = sum_{l <= i} (w_{l+1} - sum_v C[v][l] u_v) Rinv[l][i]
+// over basis columns k+1.., in place; on the block that ends the cycle also
+// V += sum_{v < J} y_v q_v (float-float V).  Warp tiles of 128 states: lane l
+// owns the quad at 128 t + 4 l, so each warp reads one contiguous 512-byte run
+// of every column per tile.
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void block_update_quad(const float* __restrict__ basis, int64_t ld,
+                                                  int k, int nnew, int J, bool fin,
+                                                  const float* cf, const float* ri,
+                                                  const float* yc, int64_t s, float4* w,
+                                                  float4& vacc) {
+  auto fma4 = [](float4& a, float c, const float4& b) {
+    a.x = fmaf(c, b.x, a.x);
+    a.y = fmaf(c, b.y, a.y);
+    a.z = fmaf(c, b.z, a.z);
+    a.w = fmaf(c, b.w, a.w);
+  };
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+    w[i] = i < nnew ? *reinterpret_cast<const float4*>(basis + static_cast<int64_t>(k + 1 + i) * ld + s)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int v = 0; v <= k; ++v) {
+    const float4 u = __ldcs(reinterpret_cast<const float4*>(basis + static_cast<int64_t>(v) * ld + s));
+#pragma unroll
+    for (int i = 0; i < S; ++i) fma4(w[i], -cf[v * kSMax + i], u);
+    if (fin && v < J) fma4(vacc, yc[v], u);
+  }
+  // in place, last column first: q_i needs w_0..w_i only
+#pragma unroll
+  for (int i = S - 1; i >= 0; --i) {
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int l = 0; l <= i; ++l) fma4(q, ri[l * kSMax + i], w[l]);
+    w[i] = q;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlkThreads)
+    k_block_update(int64_t n, float* __restrict__ basis, int64_t ld, int k, int sb,
+                   float2* __restrict__ V, const DevState* __restrict__ st) {
+  const bool fin = st->bfin_k == k;
+  if (!st->active && !fin) return;
+  __shared__ float cf[kMaxBasis * kSMax];
+  __shared__ float ri[kSMax * kSMax];
+  __shared__ float yc[kBlkMaxV];
+  const int nnew = st->bsb;
+  const int J = fin ? st->jdone : 0;
+  for (int t = threadIdx.x; t < (k + 1) * kSMax; t += blockDim.x) cf[t] = st->bC[t];
+  for (int t = threadIdx.x; t < kSMax * kSMax; t += blockDim.x) ri[t] = st->bRinv[t];
+  for (int t = threadIdx.x; t < kBlkMaxV; t += blockDim.x) yc[t] = fin ? st->bY[t] : 0.f;
+  __syncthreads();
+  (void)sb;
+  const int64_t n_wt = (n + 127) / 128;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kBlkThreads / 32);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * (kBlkThreads / 32) + (threadIdx.x >> 5);
+       t < n_wt; t += nw) {
+    const int64_t s = t * 128 + 4 * (threadIdx.x & 31);
+    if (s >= n) continue;
+    if (s + 3 < n) {
+      float4 w[S];
+      float4 vacc = make_float4(0.f, 0.f, 0.f, 0.f);
+      block_update_quad<S>(basis, ld, k, nnew, J, fin, cf, ri, yc, s, w, vacc);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        if (i < nnew) {
+          *reinterpret_cast<float4*>(basis + static_cast<int64_t>(k + 1 + i) * ld + s) = w[i];
+          if (fin && k + 1 + i < J) {
+            const float c = yc[k + 1 + i];
+            vacc.x = fmaf(c, w[i].x, vacc.x);
+            vacc.y = fmaf(c, w[i].y, vacc.y);
+            vacc.z = fmaf(c, w[i].z, vacc.z);
+            vacc.w = fmaf(c, w[i].w, vacc.w);
+          }
+        }
+      }
+      if (fin) {
+        float4* v4 = reinterpret_cast<float4*>(V + s);  // two float2 per float4
+        const float4 va = v4[0], vb = v4[1];
+        const ff r0 = ff_add_f(ff{va.x, va.y}, vacc.x), r1 = ff_add_f(ff{va.z, va.w}, vacc.y);
+        const ff r2 = ff_add_f(ff{vb.x, vb.y}, vacc.z), r3 = ff_add_f(ff{vb.z, vb.w}, vacc.w);
+        v4[0] = make_float4(r0.hi, r0.lo, r1.hi, r1.lo);
+        v4[1] = make_float4(r2.hi, r2.lo, r3.hi, r3.lo);
+      }
+    } else {
+      // ragged end of the vector: state by state, same order of operations
+      for (int64_t e = s; e < n; ++e) {
+        float w[S];
+        float va = 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+          w[i] = i < nnew ? basis[static_cast<int64_t>(k + 1 + i) * ld + e] : 0.f;
+        for (int v = 0; v <= k; ++v) {
+          const float u = basis[static_cast<int64_t>(v) * ld + e];
+#pragma unroll
+          for (int i = 0; i < S; ++i) w[i] = fmaf(-cf[v * kSMax + i], u, w[i]);
+          if (fin && v < J) va = fmaf(yc[v], u, va);
+        }
+#pragma unroll
+        for (int i = S - 1; i >= 0; --i) {
+          float q = 0.f;
+#pragma unroll
+          for (int l = 0; l <= i; ++l) q = fmaf(ri[l * kSMax + i], w[l], q);
+          w[i] = q;
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+          if (i < nnew) {
+            basis[static_cast<int64_t>(k + 1 + i) * ld + e] = w[i];
+            if (fin && k + 1 + i < J) va = fmaf(yc[k + 1 + i], w[i], va);
+          }
+        if (fin) {
+          const float2 v = V[e];
+          const ff r = ff_add_f(ff{v.x, v.y}, va);
+          V[e] = make_float2(r.hi, r.lo);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int64_t block_slots(int num_sms, int64_t n);
+
+template <int S>
+cudaError_t block_dots_launch(const Mat& A, const float* basis, int64_t ld, int k, int sb,
+                              int restart, double* partials, DevState* st, cudaStream_t s) {
+  const int nv = k + 1 + sb;
+  const int vg = (nv + kBlkVPG - 1) / kBlkVPG;
+  const int64_t n_chunks = (A.n + kBlkChunk - 1) / kBlkChunk;
+  const int64_t slots = block_slots(A.num_sms, A.n);
+  k_block_dots<S><<<static_cast<unsigned>(slots * vg), kBlkThreads, 0, s>>>(
+      A.n, n_chunks, vg, basis, ld, k, sb, restart, partials, st);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t block_update_launch(const Mat& A, float* basis, int64_t ld, int k, int sb, float2* V,
+                                DevState* st, cudaStream_t s) {
+  static int occ = [] {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_block_update<S>, kBlkThreads, 0) !=
+            cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    return nb;
+  }();
+  const int64_t warp_tiles = (A.n + 127) / 128;
+  const int64_t want = (warp_tiles + kBlkThreads / 32 - 1) / (kBlkThreads / 32);
+  const int64_t cap = static_cast<int64_t>(A.num_sms) * occ;
+  const unsigned nb = static_cast<unsigned>(want < cap ? (want < 1 ? 1 : want) : cap);
+  k_block_update<S><<<nb, kBlkThreads, 0, s>>>(A.n, basis, ld, k, sb, V, st);
+  return cudaGetLastError();
+}
+
+// Chunk slots of the Gram pass: one per chunk, at most eight per SM (and
+// kDotsMaxRuns runs of kBlkRun slots, the tickets of the two-level reduction).
+int64_t block_slots(int num_sms, int64_t n) {
+  const int64_t n_chunks = (n + kBlkChunk - 1) / kBlkChunk;
+  const int64_t max_slots =
+      static_cast<int64_t>(num_sms < kDotsMaxRuns ? num_sms : kDotsMaxRuns) * kBlkRun;
+  return n_chunks < max_slots ? n_chunks : max_slots;
+}
+
+size_t block_partials_len(int num_sms, int64_t n) {
+  return static_cast<size_t>(block_slots(num_sms, n)) * kBlkStride;
+}
+
+cudaError_t launch_block_dots(const Mat& A, const float* basis, int64_t ld, int k, int sb,
+                              int s_blk, int restart, double* partials, DevState* st,
+                              cudaStream_t s) {
+  if (s_blk <= 4) return block_dots_launch<4>(A, basis, ld, k, sb, restart, partials, st, s);
+  if (s_blk <= 6) return block_dots_launch<6>(A, basis, ld, k, sb, restart, partials, st, s);
+  return block_dots_launch<8>(A, basis, ld, k, sb, restart, partials, st, s);
+}
+
+cudaError_t launch_block_update(const Mat& A, float* basis, int64_t ld, int k, int sb, int s_blk,
+                                float2* V, DevState* st, cudaStream_t s) {
+  if (s_blk <= 4) return block_update_launch<4>(A, basis, ld, k, sb, V, st, s);
+  if (s_blk <= 6) return block_update_launch<6>(A, basis, ld, k, sb, V, st, s);
+  return block_update_launch<8>(A, basis, ld, k, sb, V, st, s);
+}
+
+}  // namespace mdpk

@@ -52,10 +52,11 @@ cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, in
 cudaError_t launch_policy_residual(const Mat& A, const int32_t* pi, const float2* V, float* r,
                                    double* partials, DevState* st, cudaStream_t s);
 
-// Arnoldi step j, SpMV half (K2): w = v_j - gamma P_pi v_j into u_{j+1}.
+// Arnoldi step j, SpMV half (K2): u_{j+1} = cdiag v_j - gamma P_pi v_j
+// (cdiag = 1: w = A v_j; cdiag = 0: the s-step monomial basis (A - I) v_j).
 // lp: use the 16-bit probabilities with row renormalisation.
 cudaError_t launch_arnoldi_spmv(const Mat& A, bool lp, const int32_t* pi, float* basis,
-                                int64_t ld, int j, int restart, double* partials, DevState* st,
+                                int64_t ld, int j, float cdiag, double* partials, DevState* st,
                                 cudaStream_t s);
 
 // Richardson sweeps through the policy-row kernel (one per probability type).
@@ -69,13 +70,13 @@ cudaError_t launch_richardson_f16(const Mat& A, const int32_t* pi, const float* 
                                   const float* d_in, float* d_out, double* partials,
                                   DevState* st, cudaStream_t s);
 cudaError_t launch_arnoldi_spmv_f32(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
-                                    int j, int restart, double* partials, DevState* st,
+                                    int j, float cdiag, double* partials, DevState* st,
                                     cudaStream_t s);
 cudaError_t launch_arnoldi_spmv_bf16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
-                                     int j, int restart, double* partials, DevState* st,
+                                    int j, float cdiag, double* partials, DevState* st,
                                      cudaStream_t s);
 cudaError_t launch_arnoldi_spmv_f16(const Mat& A, const int32_t* pi, float* basis, int64_t ld,
-                                    int j, int restart, double* partials, DevState* st,
+                                    int j, float cdiag, double* partials, DevState* st,
                                     cudaStream_t s);
 // Gram-Schmidt dots of u_{j+1} against v_0..v_j: into H(:, j) (out_h2 == 0)
 // or st->h2 (second pass of CGS2).
@@ -85,6 +86,19 @@ cudaError_t launch_arnoldi_dots(const Mat& A, float* basis, int64_t ld, int j, i
 // K3 (+K4 in its last block): w -= sum h_i v_i, ||w||, Givens, convergence.
 cudaError_t launch_arnoldi_ortho(const Mat& A, float* basis, int64_t ld, int j, int restart,
                                  int cgs2, double* partials, DevState* st, cudaStream_t s);
+
+// s-step GMRES (k_sstep.cu): the Gram pass of the block starting at step k
+// (sb vectors in columns k+1..k+sb; its last block runs the block's FP64
+// least-squares steps), and the update pass that orthonormalises the block in
+// place and, on the block that ends the cycle, adds the solution update to V.
+// s_blk is the cycle's block size (selects the kernel instantiation).
+cudaError_t launch_block_dots(const Mat& A, const float* basis, int64_t ld, int k, int sb,
+                              int s_blk, int restart, double* partials, DevState* st,
+                              cudaStream_t s);
+cudaError_t launch_block_update(const Mat& A, float* basis, int64_t ld, int k, int sb, int s_blk,
+                                float2* V, DevState* st, cudaStream_t s);
+// Doubles of the Gram pass's partials buffer for n states.
+size_t block_partials_len(int num_sms, int64_t n);
 
 // K5: V += sum_i y_i v_i over the completed steps (float-float V).
 cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* V,

@@ -15,6 +15,8 @@ constexpr int kThreads = 256;     // threads per CTA for every streaming kernel
 constexpr int kDotsMaxRuns = 256;  // dots kernel: at most 8 * 256 chunk slots
 constexpr int kMaxRestart = 64;   // GMRES restart cap (basis holds restart+1 vectors)
 constexpr int kMaxBasis = kMaxRestart + 1;
+constexpr int kSMax = 8;                     // s-step GMRES: Krylov vectors per block
+constexpr int kBlkMaxV = kMaxBasis + kSMax;  // vectors of one block Gram pass ([Q W])
 
 // ---------------------------------------------------------------------------
 // Float-float ("double-single") arithmetic: a value is the unevaluated sum
@@ -228,6 +230,8 @@ struct DevState {
   double target;      // absolute 2-norm target of the cycle
   double beta;        // ||r0||_2 of the cycle
   double est;         // current residual estimate |g_{j+1}|
+  int nspmv;          // policy-row SpMVs the cycle ran (s-step: may exceed jdone)
+  int bfin_k;         // s-step: first step of the block that ends the cycle, -1 before
   double H[kMaxBasis * kMaxRestart];
   double cs[kMaxRestart], sn[kMaxRestart];
   double gv[kMaxBasis];
@@ -247,16 +251,30 @@ struct DevState {
   double Hraw[kMaxBasis * kMaxRestart];
   double last_beta, last_est;
   int last_J;
+  // s-step GMRES block (k = first step of the block, sb its vectors w_1..w_sb
+  // in basis columns k+1..k+sb): Gram pass results and the coefficients the
+  // update pass applies
+  unsigned blk_groups;           // ticket over the Gram pass's vector groups
+  int bsb;                       // block columns kept (<= sb; fewer after a breakdown)
+  double G[kBlkMaxV * kSMax];    // G[v * kSMax + i] = <x_v, w_{i+1}>, x = [u_0..u_k, W]
+  float bC[kMaxBasis * kSMax];   // coefficient of raw column v in w_{i+1}'s projection
+  float bRinv[kSMax * kSMax];    // R^{-1} (upper triangular), R^T R = W^T W - C^T C
+  float bY[kBlkMaxV];            // coefficient of column v in the solution update
 };
 
 // Initialise a GMRES cycle from ||r0||_2 = beta (single thread).
 __device__ __forceinline__ void gmres_begin(DevState* st, double beta) {
   st->beta = beta;
   st->jdone = 0;
+  st->nspmv = 0;
+  st->bfin_k = -1;
   st->breakdown = 0;
   st->est = beta;
   for (int i = 0; i < kMaxBasis; ++i) st->gv[i] = 0.0;
   st->gv[0] = beta;
+  // v_0 = u_0 / beta; later columns start unscaled (the s-step SpMVs read
+  // their block's vectors w_i with scale 1; Arnoldi sets its own scales)
+  for (int i = 1; i < kMaxBasis; ++i) st->scale[i] = 1.0;
   st->scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
   const bool done = !(beta > st->target);
   st->converged = done ? 1 : 0;
