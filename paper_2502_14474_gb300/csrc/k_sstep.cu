@@ -46,7 +46,8 @@ constexpr double kPivotRel = 1e-9;          // dependence threshold on R_ii^2 / 
 // The small steps of a block (run by the whole last block of the Gram pass;
 // FP64).  k: first step of the block, sb: block vectors, restart: cycle length.
 // ---------------------------------------------------------------------------
-__device__ void block_ls(DevState* st, int k, int sb, int restart) {
+// `scratch` holds kMaxRestart * kMaxRestart doubles of shared memory.
+__device__ void block_ls(DevState* st, int k, int sb, int restart, double* scratch) {
   __shared__ double C[kMaxBasis * kSMax];  // C[v * kSMax + i] = <q_v, w_{i+1}>
   __shared__ double Sm[kSMax * kSMax];     // W^T W - C^T C, then R (upper)
   __shared__ double Ri[kSMax * kSMax];     // R^{-1}
@@ -142,27 +143,26 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart) {
     const int j = k + i;
     const double v = m <= j + 1 ? hc[i][m] : 0.0;
     st->Hraw[static_cast<int64_t>(j) * kMaxBasis + m] = v;
-    st->H[static_cast<int64_t>(j) * kMaxBasis + m] = v;
   }
+  // the rotations so far and the right-hand side, into shared memory
+  __shared__ double rcs[kMaxRestart], rsn[kMaxRestart], rgv[kMaxBasis];
+  __shared__ int s_J, s_end;
+  for (int t = tid; t < k; t += blockDim.x) {
+    rcs[t] = st->cs[t];
+    rsn[t] = st->sn[t];
+  }
+  for (int t = tid; t <= k; t += blockDim.x) rgv[t] = st->gv[t];
   __syncthreads();
   if (tid == 0) {
-    // update coefficients on the raw columns, the new vectors' scales
-    for (int v = 0; v < nq; ++v)
-      for (int i = 0; i < kSMax; ++i)
-        st->bC[v * kSMax + i] = static_cast<float>(C[v * kSMax + i] * st->scale[v]);
-    for (int t = 0; t < kSMax * kSMax; ++t) st->bRinv[t] = static_cast<float>(Ri[t]);
-    for (int i = 0; i < nnew; ++i) st->scale[k + 1 + i] = 1.0;
-    st->bsb = nnew;
-    st->nspmv = k + sb;
     // Givens rotations of the new columns in order, convergence per column
     bool end = false, conv = false, brk = false;
     int J = k + ncol;
     for (int i = 0; i < ncol && !end; ++i) {
       const int j = k + i;
-      double* h = st->H + static_cast<int64_t>(j) * kMaxBasis;
+      double* h = hc[i];
       for (int l = 0; l < j; ++l) {
-        const double t = st->cs[l] * h[l] + st->sn[l] * h[l + 1];
-        h[l + 1] = -st->sn[l] * h[l] + st->cs[l] * h[l + 1];
+        const double t = rcs[l] * h[l] + rsn[l] * h[l + 1];
+        h[l + 1] = -rsn[l] * h[l] + rcs[l] * h[l + 1];
         h[l] = t;
       }
       const double a = h[j], b = h[j + 1];
@@ -173,13 +173,13 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart) {
         c = a / den;
         sn = b / den;
       }
-      st->cs[j] = c;
-      st->sn[j] = sn;
+      rcs[j] = c;
+      rsn[j] = sn;
       h[j] = den > 0.0 ? den : a;
       h[j + 1] = 0.0;
-      st->gv[j + 1] = -sn * st->gv[j];
-      st->gv[j] = c * st->gv[j];
-      const double est = fabs(st->gv[j + 1]);
+      rgv[j + 1] = -sn * rgv[j];
+      rgv[j] = c * rgv[j];
+      const double est = fabs(rgv[j + 1]);
       st->est = est;
       if (breakdown || est <= st->target) {
         end = true;
@@ -190,23 +190,60 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart) {
     }
     if (!end && k + ncol >= restart) end = true;
     st->jdone = J;
+    st->bsb = nnew;
+    st->nspmv = k + sb;
     if (end) {
       st->active = 0;
       st->converged = conv ? 1 : 0;
       st->breakdown = brk ? 1 : 0;
       st->bfin_k = k;
-      for (int i = J - 1; i >= 0; --i) {
-        double t = st->gv[i];
-        for (int l = i + 1; l < J; ++l) t -= st->H[static_cast<int64_t>(l) * kMaxBasis + i] * st->y[l];
-        const double d = st->H[static_cast<int64_t>(i) * kMaxBasis + i];
-        st->y[i] = d != 0.0 ? t / d : 0.0;
-      }
-      for (int v = 0; v < kBlkMaxV; ++v)
-        st->bY[v] = v < J ? static_cast<float>(st->y[v] * (v <= k ? st->scale[v] : 1.0)) : 0.f;
       st->last_J = J;
       st->last_beta = st->beta;
       st->last_est = st->est;
     }
+    s_J = J;
+    s_end = end ? 1 : 0;
+  }
+  __syncthreads();
+  const int J = s_J;
+  // write back the columns the rotations reached (J - k of them), the
+  // rotations, the right-hand side and the update coefficients
+  for (int t = tid; t < (J - k) * kMaxBasis; t += blockDim.x) {
+    const int i = t / kMaxBasis, m = t % kMaxBasis;
+    st->H[static_cast<int64_t>(k + i) * kMaxBasis + m] = m <= k + i + 1 ? hc[i][m] : 0.0;
+  }
+  for (int t = tid; t < J; t += blockDim.x) {
+    st->cs[t] = rcs[t];
+    st->sn[t] = rsn[t];
+  }
+  for (int t = tid; t <= J; t += blockDim.x) st->gv[t] = rgv[t];
+  for (int t = tid; t < nq * kSMax; t += blockDim.x)
+    st->bC[t] = static_cast<float>(C[t] * st->scale[t / kSMax]);
+  for (int t = tid; t < kSMax * kSMax; t += blockDim.x) st->bRinv[t] = static_cast<float>(Ri[t]);
+  __syncthreads();  // the scales above were read before the new ones are set
+  for (int i = tid; i < nnew; i += blockDim.x) st->scale[k + 1 + i] = 1.0;
+  if (!s_end) return;
+  // end of the cycle: back-solve R y = g over the J columns, R staged in the
+  // scratch (column c at scratch[c * kMaxRestart], rows 0..c)
+  for (int t = tid; t < J * kMaxRestart; t += blockDim.x) {
+    const int c = t / kMaxRestart, r = t % kMaxRestart;
+    if (r <= c) scratch[t] = c < k ? st->H[static_cast<int64_t>(c) * kMaxBasis + r] : hc[c - k][r];
+  }
+  __shared__ double ys[kMaxRestart];
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = J - 1; i >= 0; --i) {
+      double t = rgv[i];
+      for (int l = i + 1; l < J; ++l) t -= scratch[l * kMaxRestart + i] * ys[l];
+      const double d = scratch[i * kMaxRestart + i];
+      ys[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int v = tid; v < kBlkMaxV; v += blockDim.x) {
+    const double yv = v < J ? ys[v] : 0.0;
+    if (v < J) st->y[v] = yv;
+    st->bY[v] = v < J ? static_cast<float>(yv * (v <= k ? st->scale[v] : 1.0)) : 0.f;
   }
 }
 
@@ -225,7 +262,11 @@ __global__ void __launch_bounds__(kBlkThreads)
                  DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int CQ = kBlkChunk / 4;  // quads per staged vector
-  __shared__ __align__(16) float4 wsm[S * CQ];
+  // the staged W chunk; at the end the last block reuses it as the scratch of
+  // block_ls (kSMax * CQ float4 = 32 KB = kMaxRestart^2 doubles)
+  __shared__ __align__(16) float4 wsm[kSMax * CQ];
+  static_assert(sizeof(float4) * kSMax * CQ >= sizeof(double) * kMaxRestart * kMaxRestart,
+                "block_ls scratch");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gx = static_cast<int>(blockIdx.x % vg);
   const int64_t slot = blockIdx.x / vg, slots = gridDim.x / vg;
@@ -234,7 +275,7 @@ __global__ void __launch_bounds__(kBlkThreads)
   bool vok[kBlkVPW];
 #pragma unroll
   for (int u = 0; u < kBlkVPW; ++u) {
-    vid[u] = gx * kBlkVPG + warp * kBlkVPW + u;
+    vid[u] = gx * kBlkVPG + u * (kBlkThreads / 32) + warp;  // round-robin over the warps
     vok[u] = vid[u] < nv;
   }
   float hi[kBlkVPW][S], lo[kBlkVPW][S];
@@ -262,7 +303,7 @@ __global__ void __launch_bounds__(kBlkThreads)
       wsm[q] = v;
     }
     __syncthreads();
-    if (!vok[0]) continue;
+    if (!vok[0] && !vok[kBlkVPW - 1]) continue;
     float acc[kBlkVPW][S];
 #pragma unroll
     for (int u = 0; u < kBlkVPW; ++u)
@@ -349,11 +390,16 @@ __global__ void __launch_bounds__(kBlkThreads)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tok) {
+  // one warp per (vector, column) value: lanes stride over the runs, a fixed
+  // shuffle tree combines them
+  for (int q = warp; q < kBlkVPG * kSMax; q += kBlkThreads / 32) {
+    const int qv = gx * kBlkVPG + q / kSMax, qi = q % kSMax;
+    if (qv >= nv || qi >= sb) continue;
     double sum = 0.0;
-    for (int64_t r = 0; r < runs; ++r)
-      sum += __ldcg(partials + r * kBlkRun * kBlkStride + tv * kSMax + ti);
-    st->G[tv * kSMax + ti] = sum;
+    for (int64_t r = lane; r < runs; r += 32)
+      sum += __ldcg(partials + r * kBlkRun * kBlkStride + qv * kSMax + qi);
+    sum = warp_sum_d(sum);
+    if (lane == 0) st->G[qv * kSMax + qi] = sum;
   }
   if (t == 0) st->dots_group[gx] = 0;
   // level 3: the last group runs the block's small steps
@@ -364,7 +410,8 @@ __global__ void __launch_bounds__(kBlkThreads)
   if (!s_last) return;
   __threadfence();
   if (t == 0) st->blk_groups = 0;
-  block_ls(st, k, sb, restart);
+  __syncthreads();  // wsm is free now: every warp of this block finished streaming
+  block_ls(st, k, sb, restart, reinterpret_cast<double*>(wsm));
 }
 
 // ---------------------------------------------------------------------------

@@ -5,10 +5,11 @@ iteration.
 * Solves with every block size and restart length reach the oracle's solution:
   dense-LU exact policy iteration for small n, else the oracle's FP64
   certificate ||T V - V||_inf and the bound ||V - V*||_inf <= res / (1 - gamma).
-* The Hessenberg matrix an s-step cycle reconstructs equals the one classical
-  Arnoldi builds for the same Krylov space (the basis is the same up to FP32
-  rounding: both orthonormalisations give positive subdiagonals), and its
-  least-squares record agrees with numpy's solver.
+* The Hessenberg matrix an s-step cycle reconstructs matches the FP64 Arnoldi
+  matrix of the same Krylov space about as closely as the classical FP32
+  Gram-Schmidt cycle does (both orthonormalisations give positive
+  subdiagonals, so the bases agree up to rounding), and its least-squares
+  record agrees with numpy's solver.
 * A residual that is an eigenvector of P (uniform transitions) makes the first
   block exactly dependent: the cycle must end on that breakdown with the exact
   solution (closed form V(s) = g(s) + gamma * mean(g) / (1 - gamma)).
@@ -101,26 +102,66 @@ def _one_cycle(mdp, s_step, restart=30):
     return c
 
 
+def _exact_first_cycle(mdp, J):
+    """FP64 Arnoldi (classical Gram-Schmidt, twice) of the first cycle of a solve
+    from V = 0: policy pi_0 = greedy(0), r_0 = T 0 - 0, A = I - gamma P_pi."""
+    import scipy.sparse as sp
+    TV, pi = oracle.bellman(mdp, np.zeros(mdp.n))
+    rows = np.arange(mdp.n) * mdp.m + pi
+    b, e = mdp.row_ptr[rows], mdp.row_ptr[rows + 1]
+    idx = np.concatenate([np.arange(x, y) for x, y in zip(b, e)])
+    P = sp.csr_matrix((mdp.val[idx].astype(np.float64),
+                       (np.repeat(np.arange(mdp.n), e - b), mdp.col[idx])), shape=(mdp.n, mdp.n))
+    A = sp.eye(mdp.n, format="csr") - mdp.gamma * P
+    beta = np.linalg.norm(TV)
+    Q = np.zeros((mdp.n, J + 1))
+    H = np.zeros((J + 1, J))
+    Q[:, 0] = TV / beta
+    for j in range(J):
+        w = A @ Q[:, j]
+        for _ in range(2):
+            h = Q[:, :j + 1].T @ w
+            w -= Q[:, :j + 1] @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        Q[:, j + 1] = w / H[j + 1, j]
+    return H, beta
+
+
+def _ls_residuals(H, beta):
+    out = []
+    for j in range(1, H.shape[1] + 1):
+        e = np.zeros(j + 1)
+        e[0] = beta
+        y = np.linalg.lstsq(H[:j + 1, :j], e, rcond=None)[0]
+        out.append(np.linalg.norm(e - H[:j + 1, :j] @ y))
+    return np.array(out)
+
+
 @pytest.mark.parametrize("s_step", [2, 5, 8])
-def test_sstep_hessenberg_equals_arnoldi(s_step):
+def test_sstep_hessenberg_matches_exact_arnoldi(s_step):
+    """Both GPU cycles (classical FP32 Gram-Schmidt and s-step) rebuild the FP64
+    Arnoldi matrix of the same Krylov space; the s-step one must be about as
+    close to it as the classical one (both keep the basis in FP32)."""
     mdp = synth.banded(40000, 6, 12, 2000, 0.5, 0.99, seed=140, dtype=np.float32)
+    Hx, bx = _exact_first_cycle(mdp, 30)
     ref = _one_cycle(mdp, 0)
     c = _one_cycle(mdp, s_step)
     assert ref["J"] == c["J"] == 30
-    assert abs(c["beta"] - ref["beta"]) <= 1e-12 * ref["beta"]
-    Href, H = ref["H"], c["H"]
-    # the basis vectors are FP32 and the two orthogonalisations round
-    # differently; the matrices agree to the basis' precision times the
-    # conditioning of the block (a few hundred for blocks of up to 8 vectors)
-    assert np.max(np.abs(H - Href)) <= 2e-4 * np.max(np.abs(Href))
-    # GMRES residual after every step: the same to 1e-4 relative
-    for j in range(1, 31):
-        e = np.zeros(j + 1)
-        e[0] = ref["beta"]
-        r_ref = np.linalg.norm(e - Href[:j + 1, :j] @ np.linalg.lstsq(Href[:j + 1, :j], e,
-                                                                      rcond=None)[0])
-        r = np.linalg.norm(e - H[:j + 1, :j] @ np.linalg.lstsq(H[:j + 1, :j], e, rcond=None)[0])
-        assert abs(r - r_ref) <= 1e-4 * ref["beta"]
+    assert abs(c["beta"] - bx) <= 1e-6 * bx and abs(ref["beta"] - bx) <= 1e-6 * bx
+    scale = np.max(np.abs(Hx))
+    d_cls = np.max(np.abs(ref["H"] - Hx)) / scale
+    d_ss = np.max(np.abs(c["H"] - Hx)) / scale
+    print(f"s={s_step} |H_classical - H|/|H| {d_cls:.2e}  |H_sstep - H|/|H| {d_ss:.2e}")
+    assert d_ss <= max(20.0 * d_cls, 1e-5)
+    rx = _ls_residuals(Hx, bx)
+    r_cls = np.max(np.abs(_ls_residuals(ref["H"], ref["beta"]) - rx)) / bx
+    r_ss = np.max(np.abs(_ls_residuals(c["H"], c["beta"]) - rx)) / bx
+    print(f"  GMRES residuals per step: classical {r_cls:.2e}  s-step {r_ss:.2e} (of beta)")
+    # the estimates drive a stop at eta = 0.1 of the outer residual: an error of
+    # 1e-4 beta (larger blocks lose digits to the monomial basis' conditioning)
+    # cannot change that decision by more than one step
+    assert r_ss <= max(20.0 * r_cls, 1e-4)
 
 
 def test_sstep_least_squares_record():
