@@ -13,7 +13,7 @@
 //           monomial basis of A - I), w_i stored in column k+i (k_spmv.cuh,
 //           cdiag = 0).
 //   Gram    one pass over [Q W]: G = [Q W]^T W, C = Q^T W, and the block's own
-//           Gram matrix W^T W; products are summed in FP32 over 32 entries per
+//           Gram matrix W^T W; products are summed in FP32 over 32 terms per
 //           lane, then in float-float, so that the Pythagorean form below keeps
 //           its digits (k_block_dots).  Its last block runs the small FP64
 //           steps (block_ls): R^T R = W^T W - C^T C (Cholesky; "BCGS-PIP",
@@ -35,9 +35,7 @@
 namespace mdpk {
 
 constexpr int kBlkThreads = 256;
-constexpr int kBlkChunk = 1024;             // states of the W block staged per chunk
-constexpr int kBlkVPW = 2;                  // streamed vectors per warp
-constexpr int kBlkVPG = (kBlkThreads / 32) * kBlkVPW;  // vectors per group (16)
+constexpr int kBlkChunk = 1024;             // at least this many states per Gram slot
 constexpr int kBlkStride = kBlkMaxV * kSMax;           // doubles per partial slot
 constexpr int kBlkRun = 8;                  // chunk slots per first-level reduction
 constexpr double kPivotRel = 1e-9;          // dependence threshold on R_ii^2 / ||w_i||^2
@@ -249,104 +247,104 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
 
 // ---------------------------------------------------------------------------
 // Gram pass: G[v][i] = <x_v, w_{i+1}> for x = [u_0..u_k, w_1..w_sb] (raw
-// columns 0..k+sb), i < sb.  Block (group gx, slot y): the warps stream the
-// group's vectors (kBlkVPW each) over the slot's chunks, with the chunk of W
-// staged in shared memory.  Partials: one FP64 value per (slot, v, i), reduced
-// in two fixed-order levels as in k_gs_dots (runs of eight slots, then the
-// runs of a group), then the last group runs block_ls.
+// columns 0..k+sb), i < sb.  Grid (slots x groups): block (y, gx) owns the
+// contiguous states of slot y and the group's 8 * VPW vectors, VPW per warp.
+// Every warp walks the slot in tiles of 128 states (a float4 per lane): it
+// loads the tile of the block vectors W (the eight warps of a block read the
+// same lines, so seven of them hit L1) and the tile of each of its vectors,
+// all loads issued before the products, so each lane has S + VPW 16-byte loads
+// in flight and no barrier stalls the stream.  Products are summed in FP32
+// over eight tiles per lane (32 terms), then folded into float-float sums.
+// Partials: one FP64 value per (slot, v, i), reduced in two fixed-order levels
+// (runs of eight slots, then the runs of a group, one warp per value); the
+// last group runs block_ls.
 // ---------------------------------------------------------------------------
 template <int S>
+struct GramVpw {
+  static constexpr int value = S <= 4 ? 4 : (S <= 6 ? 3 : 2);
+};
+
+template <int S>
 __global__ void __launch_bounds__(kBlkThreads)
-    k_block_dots(int64_t n, int64_t n_chunks, int vg, const float* __restrict__ basis,
-                 int64_t ld, int k, int sb, int restart, double* __restrict__ partials,
+    k_block_dots(int64_t n, int64_t states_per_slot, const float* __restrict__ basis, int64_t ld,
+                 int k, int sb, int restart, double* __restrict__ partials,
                  DevState* __restrict__ st) {
   if (!st->active) return;
-  constexpr int CQ = kBlkChunk / 4;  // quads per staged vector
-  // the staged W chunk; at the end the last block reuses it as the scratch of
-  // block_ls (kSMax * CQ float4 = 32 KB = kMaxRestart^2 doubles)
-  __shared__ __align__(16) float4 wsm[kSMax * CQ];
-  static_assert(sizeof(float4) * kSMax * CQ >= sizeof(double) * kMaxRestart * kMaxRestart,
-                "block_ls scratch");
+  constexpr int VPW = GramVpw<S>::value;
+  constexpr int NW = kBlkThreads / 32;
+  constexpr int VPG = NW * VPW;  // vectors per group
+  __shared__ __align__(16) double scratch[kMaxRestart * kMaxRestart];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gx = static_cast<int>(blockIdx.x % vg);
-  const int64_t slot = blockIdx.x / vg, slots = gridDim.x / vg;
+  const int gx = static_cast<int>(blockIdx.y), vg = static_cast<int>(gridDim.y);
+  const int64_t slot = blockIdx.x, slots = gridDim.x;
   const int nv = k + 1 + sb;
-  int vid[kBlkVPW];
-  bool vok[kBlkVPW];
+  int vid[VPW];
+  bool vok[VPW];
 #pragma unroll
-  for (int u = 0; u < kBlkVPW; ++u) {
-    vid[u] = gx * kBlkVPG + u * (kBlkThreads / 32) + warp;  // round-robin over the warps
+  for (int u = 0; u < VPW; ++u) {
+    vid[u] = gx * VPG + u * NW + warp;  // round-robin over the warps
     vok[u] = vid[u] < nv;
   }
-  float hi[kBlkVPW][S], lo[kBlkVPW][S];
+  float hi[VPW][S], lo[VPW][S], acc[VPW][S];
 #pragma unroll
-  for (int u = 0; u < kBlkVPW; ++u)
+  for (int u = 0; u < VPW; ++u)
 #pragma unroll
-    for (int i = 0; i < S; ++i) hi[u][i] = lo[u][i] = 0.f;
-  for (int64_t c = slot; c < n_chunks; c += slots) {
-    const int64_t c0 = c * kBlkChunk;
-    const int len = static_cast<int>(n - c0 < kBlkChunk ? n - c0 : kBlkChunk);
-    __syncthreads();  // the previous chunk's readers are done with wsm
-    for (int q = threadIdx.x; q < S * CQ; q += kBlkThreads) {
-      const int i = q / CQ, e = 4 * (q % CQ);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < sb) {
-        const float* src = basis + static_cast<int64_t>(k + 1 + i) * ld + c0;
-        if (e + 3 < len) {
-          v = __ldcg(reinterpret_cast<const float4*>(src + e));
-        } else if (e < len) {
-          v.x = src[e];
-          if (e + 1 < len) v.y = src[e + 1];
-          if (e + 2 < len) v.z = src[e + 2];
-        }
+    for (int i = 0; i < S; ++i) hi[u][i] = lo[u][i] = acc[u][i] = 0.f;
+  const int64_t s_begin = slot * states_per_slot;
+  const int64_t s_end = min(n, s_begin + states_per_slot);
+  const float* wcol = basis + static_cast<int64_t>(k + 1) * ld;
+  if (vok[0]) {
+    int run = 0;
+    for (int64_t s = s_begin + 4 * lane; s < s_end; s += 128) {
+      float4 w[S], x[VPW];
+      if (s + 3 < s_end) {
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+          w[i] = i < sb ? __ldcg(reinterpret_cast<const float4*>(wcol + i * ld + s))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < VPW; ++u)
+          x[u] = vok[u] ? __ldcs(reinterpret_cast<const float4*>(basis + vid[u] * ld + s))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {  // ragged end of the vector: entries past n read as zero
+        auto ld4 = [&](const float* p) {
+          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (s < s_end) r.x = p[s];
+          if (s + 1 < s_end) r.y = p[s + 1];
+          if (s + 2 < s_end) r.z = p[s + 2];
+          return r;
+        };
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+          w[i] = i < sb ? ld4(wcol + i * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < VPW; ++u)
+          x[u] = vok[u] ? ld4(basis + vid[u] * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      wsm[q] = v;
-    }
-    __syncthreads();
-    if (!vok[0] && !vok[kBlkVPW - 1]) continue;
-    float acc[kBlkVPW][S];
 #pragma unroll
-    for (int u = 0; u < kBlkVPW; ++u)
+      for (int u = 0; u < VPW; ++u)
 #pragma unroll
-      for (int i = 0; i < S; ++i) acc[u][i] = 0.f;
-    const int nq4 = len >> 2;
-    for (int qd = lane; qd < nq4; qd += 32) {
-      float4 x[kBlkVPW];
+        for (int i = 0; i < S; ++i)
+          acc[u][i] = fmaf(x[u].x, w[i].x, fmaf(x[u].y, w[i].y, fmaf(x[u].z, w[i].z,
+                                                                  fmaf(x[u].w, w[i].w, acc[u][i]))));
+      if (++run == 8) {  // fold the FP32 runs into the float-float sums
+        run = 0;
 #pragma unroll
-      for (int u = 0; u < kBlkVPW; ++u)
-        x[u] = vok[u] ? __ldcs(reinterpret_cast<const float4*>(
-                            basis + static_cast<int64_t>(vid[u]) * ld + c0) + qd)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < VPW; ++u)
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        const float4 w = wsm[i * CQ + qd];
-#pragma unroll
-        for (int u = 0; u < kBlkVPW; ++u)
-          acc[u][i] = fmaf(x[u].x, w.x, fmaf(x[u].y, w.y, fmaf(x[u].z, w.z,
-                                                                fmaf(x[u].w, w.w, acc[u][i]))));
+          for (int i = 0; i < S; ++i) {
+            ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
+            acc[u][i] = 0.f;
+          }
       }
     }
-    if (lane == 0) {  // ragged end of the last chunk, entry by entry
-      const float* ws = reinterpret_cast<const float*>(wsm);
-      for (int e = 4 * nq4; e < len; ++e)
-#pragma unroll
-        for (int u = 0; u < kBlkVPW; ++u) {
-          const float xe = vok[u] ? basis[static_cast<int64_t>(vid[u]) * ld + c0 + e] : 0.f;
-#pragma unroll
-          for (int i = 0; i < S; ++i) acc[u][i] = fmaf(xe, ws[i * kBlkChunk + e], acc[u][i]);
-        }
-    }
-    // fold this chunk's FP32 runs into the float-float sums
-#pragma unroll
-    for (int u = 0; u < kBlkVPW; ++u)
-#pragma unroll
-      for (int i = 0; i < S; ++i) ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
   }
-  // warp sums (float-float) and the slot's partials
+  // fold the last run, warp sums (float-float), the slot's partials
 #pragma unroll
-  for (int u = 0; u < kBlkVPW; ++u)
+  for (int u = 0; u < VPW; ++u)
 #pragma unroll
     for (int i = 0; i < S; ++i) {
+      ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
         ff_merge(hi[u][i], lo[u][i], __shfl_xor_sync(0xffffffffu, hi[u][i], o),
@@ -354,7 +352,7 @@ __global__ void __launch_bounds__(kBlkThreads)
     }
   if (lane == 0) {
 #pragma unroll
-    for (int u = 0; u < kBlkVPW; ++u)
+    for (int u = 0; u < VPW; ++u)
       if (vok[u])
 #pragma unroll
         for (int i = 0; i < S; ++i)
@@ -363,10 +361,7 @@ __global__ void __launch_bounds__(kBlkThreads)
                 static_cast<double>(hi[u][i]) + static_cast<double>(lo[u][i]);
   }
   __shared__ bool s_last;
-  // the group's (vector, column) values, one per thread
   const int t = threadIdx.x;
-  const int tv = gx * kBlkVPG + t / kSMax, ti = t % kSMax;
-  const bool tok = t < kBlkVPG * kSMax && tv < nv && ti < sb;
   // level 1: the last block of this run of slots sums the run in slot order
   const int64_t run = slot / kBlkRun, runs = (slots + kBlkRun - 1) / kBlkRun;
   const int64_t run_len = min(static_cast<int64_t>(kBlkRun), slots - run * kBlkRun);
@@ -376,11 +371,13 @@ __global__ void __launch_bounds__(kBlkThreads)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tok) {
-    const double* pr = partials + run * kBlkRun * kBlkStride + tv * kSMax + ti;
+  for (int q = t; q < VPG * kSMax; q += kBlkThreads) {
+    const int qv = gx * VPG + q / kSMax, qi = q % kSMax;
+    if (qv >= nv || qi >= sb) continue;
+    const double* pr = partials + run * kBlkRun * kBlkStride + qv * kSMax + qi;
     double sum = 0.0;
     for (int r = 0; r < run_len; ++r) sum += __ldcg(pr + r * kBlkStride);
-    partials[run * kBlkRun * kBlkStride + tv * kSMax + ti] = sum;
+    partials[run * kBlkRun * kBlkStride + qv * kSMax + qi] = sum;
   }
   if (t == 0) st->dots_run[gx][run] = 0;
   // level 2: the last run of this group sums the runs in order
@@ -392,8 +389,8 @@ __global__ void __launch_bounds__(kBlkThreads)
   __threadfence();
   // one warp per (vector, column) value: lanes stride over the runs, a fixed
   // shuffle tree combines them
-  for (int q = warp; q < kBlkVPG * kSMax; q += kBlkThreads / 32) {
-    const int qv = gx * kBlkVPG + q / kSMax, qi = q % kSMax;
+  for (int q = warp; q < VPG * kSMax; q += NW) {
+    const int qv = gx * VPG + q / kSMax, qi = q % kSMax;
     if (qv >= nv || qi >= sb) continue;
     double sum = 0.0;
     for (int64_t r = lane; r < runs; r += 32)
@@ -410,8 +407,7 @@ __global__ void __launch_bounds__(kBlkThreads)
   if (!s_last) return;
   __threadfence();
   if (t == 0) st->blk_groups = 0;
-  __syncthreads();  // wsm is free now: every warp of this block finished streaming
-  block_ls(st, k, sb, restart, reinterpret_cast<double*>(wsm));
+  block_ls(st, k, sb, restart, scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -545,12 +541,15 @@ int64_t block_slots(int num_sms, int64_t n);
 template <int S>
 cudaError_t block_dots_launch(const Mat& A, const float* basis, int64_t ld, int k, int sb,
                               int restart, double* partials, DevState* st, cudaStream_t s) {
+  constexpr int VPG = (kBlkThreads / 32) * GramVpw<S>::value;
   const int nv = k + 1 + sb;
-  const int vg = (nv + kBlkVPG - 1) / kBlkVPG;
-  const int64_t n_chunks = (A.n + kBlkChunk - 1) / kBlkChunk;
+  const int vg = (nv + VPG - 1) / VPG;
   const int64_t slots = block_slots(A.num_sms, A.n);
-  k_block_dots<S><<<static_cast<unsigned>(slots * vg), kBlkThreads, 0, s>>>(
-      A.n, n_chunks, vg, basis, ld, k, sb, restart, partials, st);
+  int64_t per = (A.n + slots - 1) / slots;
+  per = (per + 127) / 128 * 128;
+  const int64_t used = (A.n + per - 1) / per;  // <= slots
+  k_block_dots<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kBlkThreads, 0,
+                    s>>>(A.n, per, basis, ld, k, sb, restart, partials, st);
   return cudaGetLastError();
 }
 
