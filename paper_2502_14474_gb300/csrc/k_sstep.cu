@@ -117,6 +117,13 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
   //                - sum_{l<i-1} R[l][i-1] A q_{k+1+l}) / R[i-1][i-1],
   // with A q_v (v < k) the earlier columns of the cycle (Hraw, unrotated).
   const int rows = k + ncol + 1;
+  // the earlier raw columns (rows 0..k), staged: hs[v * kMaxRestart + m]
+  double* hs = scratch;
+  for (int t = tid; t < k * kMaxRestart; t += blockDim.x) {
+    const int v = t / kMaxRestart, m = t % kMaxRestart;
+    hs[t] = m <= v + 1 ? st->Hraw[static_cast<int64_t>(v) * kMaxBasis + m] : 0.0;
+  }
+  __syncthreads();
   for (int m = tid; m < rows; m += blockDim.x) {
     auto coefz = [&](int j) -> double {  // row m of z_j (j >= 1)
       if (m <= k) return C[m * kSMax + (j - 1)];
@@ -128,7 +135,7 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
     for (int i = 1; i < ncol; ++i) {
       double t = coefz(i + 1) + coefz(i);
       for (int v = (m > 0 ? m - 1 : 0); v < k; ++v)
-        t -= C[v * kSMax + (i - 1)] * st->Hraw[static_cast<int64_t>(v) * kMaxBasis + m];
+        t -= C[v * kSMax + (i - 1)] * hs[v * kMaxRestart + m];
       t -= C[k * kSMax + (i - 1)] * hc[0][m];
       for (int l = 0; l < i - 1; ++l) t -= Sm[l * kSMax + (i - 1)] * hc[l + 1][m];
       hc[i][m] = t / Sm[(i - 1) * kSMax + (i - 1)];
@@ -387,16 +394,16 @@ __global__ void __launch_bounds__(kBlkThreads)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // one warp per (vector, column) value: lanes stride over the runs, a fixed
-  // shuffle tree combines them
-  for (int q = warp; q < VPG * kSMax; q += NW) {
+  // one thread per (vector, column) value, the runs summed in order (the
+  // loads are independent, so an unrolled loop keeps several in flight)
+  for (int q = t; q < VPG * kSMax; q += kBlkThreads) {
     const int qv = gx * VPG + q / kSMax, qi = q % kSMax;
     if (qv >= nv || qi >= sb) continue;
+    const double* pr = partials + qv * kSMax + qi;
     double sum = 0.0;
-    for (int64_t r = lane; r < runs; r += 32)
-      sum += __ldcg(partials + r * kBlkRun * kBlkStride + qv * kSMax + qi);
-    sum = warp_sum_d(sum);
-    if (lane == 0) st->G[qv * kSMax + qi] = sum;
+#pragma unroll 8
+    for (int64_t r = 0; r < runs; ++r) sum += __ldcg(pr + r * kBlkRun * kBlkStride);
+    st->G[qv * kSMax + qi] = sum;
   }
   if (t == 0) st->dots_group[gx] = 0;
   // level 3: the last group runs the block's small steps
@@ -544,7 +551,12 @@ cudaError_t block_dots_launch(const Mat& A, const float* basis, int64_t ld, int 
   constexpr int VPG = (kBlkThreads / 32) * GramVpw<S>::value;
   const int nv = k + 1 + sb;
   const int vg = (nv + VPG - 1) / VPG;
-  const int64_t slots = block_slots(A.num_sms, A.n);
+  // about two blocks per SM in one wave (the register budget allows two):
+  // each warp streams many tiles, and the reduction tail has few runs
+  int64_t slots = static_cast<int64_t>(2 * A.num_sms) / vg;
+  const int64_t cap = block_slots(A.num_sms, A.n);
+  if (slots > cap) slots = cap;
+  if (slots < 1) slots = 1;
   int64_t per = (A.n + slots - 1) / slots;
   per = (per + 127) / 128 * 128;
   const int64_t used = (A.n + per - 1) / per;  // <= slots
