@@ -41,18 +41,29 @@ constexpr int kBlkRun = 8;                  // chunk slots per first-level reduc
 constexpr double kPivotRel = 1e-9;          // dependence threshold on R_ii^2 / ||w_i||^2
 
 // ---------------------------------------------------------------------------
-// The small steps of a block (run by the whole last block of the Gram pass;
-// FP64).  k: first step of the block, sb: block vectors, restart: cycle length.
+// The small steps of a block (run by the whole last block of the Gram pass,
+// FP64).  k: first step of the block, sb: block vectors; `scratch` holds
+// kMaxRestart * kMaxRestart doubles of shared memory.
+//
+// FP64 instructions issue at a small fraction of the FP32 rate on this GPU and
+// cost the same whether one lane or all 32 are active, so the sequential parts
+// run on the lanes of warp 0 in parallel wherever the data allow: the Cholesky
+// factor column by column (one lane per remaining column or pair), R^{-1} one
+// column per lane, the earlier rotations applied to all new columns at once,
+// and the back-solve one row per lane.
 // ---------------------------------------------------------------------------
-// `scratch` holds kMaxRestart * kMaxRestart doubles of shared memory.
 __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scratch) {
   __shared__ double C[kMaxBasis * kSMax];  // C[v * kSMax + i] = <q_v, w_{i+1}>
   __shared__ double Sm[kSMax * kSMax];     // W^T W - C^T C, then R (upper)
   __shared__ double Ri[kSMax * kSMax];     // R^{-1}
+  __shared__ double rinv[kSMax];           // 1 / R_jj
   __shared__ double hc[kSMax][kBlkMaxV];   // new Hessenberg columns
-  __shared__ int s_ncol, s_nnew;
-  const int tid = threadIdx.x;
+  __shared__ double rcs[kMaxRestart], rsn[kMaxRestart], rgv[kMaxBasis];
+  __shared__ double ys[kMaxRestart];
+  __shared__ int s_ncol, s_nnew, s_J, s_end;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nq = k + 1;
+  (void)restart;
   // C from the Gram block: dots with the raw columns times their scales
   for (int t = tid; t < nq * kSMax; t += blockDim.x) {
     const int v = t / kSMax, i = t % kSMax;
@@ -69,43 +80,56 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
     Sm[t] = sij;
   }
   __syncthreads();
-  if (tid == 0) {
-    // Cholesky Sm = R^T R in place (upper triangle); stop at the first
-    // dependent column c: R_cc = 0, the columns after it are dropped
+  if (warp == 0) {
+    // right-looking Cholesky S = R^T R in place (upper triangle); a pivot
+    // below kPivotRel of its column's squared norm is an exact dependence:
+    // R_cc = 0 and the columns after c are dropped
     int nnew = sb, ncol = sb;
     for (int j = 0; j < sb; ++j) {
-      for (int i = 0; i < j; ++i) {
-        double t = Sm[i * kSMax + j];
-        for (int l = 0; l < i; ++l) t -= Sm[l * kSMax + i] * Sm[l * kSMax + j];
-        Sm[i * kSMax + j] = t / Sm[i * kSMax + i];
-      }
-      double d = Sm[j * kSMax + j];
-      for (int l = 0; l < j; ++l) d -= Sm[l * kSMax + j] * Sm[l * kSMax + j];
+      const double d = Sm[j * kSMax + j];
       const double wn = st->G[(nq + j) * kSMax + j];  // ||w_{j+1}||^2
       if (!(d > kPivotRel * wn) || !(wn > 0.0)) {
-        Sm[j * kSMax + j] = 0.0;
         nnew = j;
         ncol = j + 1;
         break;
       }
-      Sm[j * kSMax + j] = sqrt(d);
+      const double inv = rsqrt(d);
+      if (lane > j && lane < sb) Sm[j * kSMax + lane] *= inv;  // R[j][l]
+      __syncwarp();
+      // trailing update S[p][q] -= R[j][p] R[j][q], j < p <= q < sb (<= 28 pairs)
+      for (int pq = lane; pq < kSMax * kSMax; pq += 32) {
+        const int pp = pq / kSMax, qq = pq % kSMax;
+        if (pp > j && qq >= pp && qq < sb) Sm[pp * kSMax + qq] -= Sm[j * kSMax + pp] * Sm[j * kSMax + qq];
+      }
+      if (lane == 0) {
+        Sm[j * kSMax + j] = d * inv;
+        rinv[j] = inv;
+      }
+      __syncwarp();
     }
-    for (int t = 0; t < kSMax * kSMax; ++t) {  // R: upper triangle of the kept columns
+    // R: the upper triangle of the kept columns (column c = nnew keeps R[l][c],
+    // l < c, with R_cc = 0 when the block broke down)
+    for (int t = lane; t < kSMax * kSMax; t += 32) {
       const int i = t / kSMax, j = t % kSMax;
-      if (i > j || j >= ncol) Sm[t] = 0.0;
+      if (i > j || j >= ncol || (j == nnew && i == j)) Sm[t] = 0.0;
     }
-    // R^{-1} of the leading nnew x nnew factor (upper triangular)
-    for (int t = 0; t < kSMax * kSMax; ++t) Ri[t] = 0.0;
-    for (int j = 0; j < nnew; ++j) {
-      Ri[j * kSMax + j] = 1.0 / Sm[j * kSMax + j];
+    __syncwarp();
+    // R^{-1} of the leading nnew columns, one column per lane
+    for (int t = lane; t < kSMax * kSMax; t += 32) Ri[t] = 0.0;
+    __syncwarp();
+    if (lane < nnew) {
+      const int j = lane;
+      Ri[j * kSMax + j] = rinv[j];
       for (int i = j - 1; i >= 0; --i) {
         double t = 0.0;
         for (int l = i + 1; l <= j; ++l) t += Sm[i * kSMax + l] * Ri[l * kSMax + j];
-        Ri[i * kSMax + j] = -t / Sm[i * kSMax + i];
+        Ri[i * kSMax + j] = -t * rinv[i];
       }
     }
-    s_ncol = ncol;
-    s_nnew = nnew;
+    if (lane == 0) {
+      s_ncol = ncol;
+      s_nnew = nnew;
+    }
   }
   __syncthreads();
   const int ncol = s_ncol, nnew = s_nnew;
@@ -130,15 +154,13 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
       const int l = m - k - 1;
       return l < j ? Sm[l * kSMax + (j - 1)] : 0.0;
     };
-    double h0 = coefz(1) + (m == k ? 1.0 : 0.0);
-    hc[0][m] = h0;
+    hc[0][m] = coefz(1) + (m == k ? 1.0 : 0.0);
     for (int i = 1; i < ncol; ++i) {
       double t = coefz(i + 1) + coefz(i);
-      for (int v = (m > 0 ? m - 1 : 0); v < k; ++v)
-        t -= C[v * kSMax + (i - 1)] * hs[v * kMaxRestart + m];
+      for (int v = (m > 0 ? m - 1 : 0); v < k; ++v) t -= C[v * kSMax + (i - 1)] * hs[v * kMaxRestart + m];
       t -= C[k * kSMax + (i - 1)] * hc[0][m];
       for (int l = 0; l < i - 1; ++l) t -= Sm[l * kSMax + (i - 1)] * hc[l + 1][m];
-      hc[i][m] = t / Sm[(i - 1) * kSMax + (i - 1)];
+      hc[i][m] = t * rinv[i - 1];
     }
   }
   __syncthreads();
@@ -146,68 +168,79 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
   for (int t = tid; t < ncol * kMaxBasis; t += blockDim.x) {
     const int i = t / kMaxBasis, m = t % kMaxBasis;
     const int j = k + i;
-    const double v = m <= j + 1 ? hc[i][m] : 0.0;
-    st->Hraw[static_cast<int64_t>(j) * kMaxBasis + m] = v;
+    st->Hraw[static_cast<int64_t>(j) * kMaxBasis + m] = m <= j + 1 && m < rows ? hc[i][m] : 0.0;
   }
-  // the rotations so far and the right-hand side, into shared memory
-  __shared__ double rcs[kMaxRestart], rsn[kMaxRestart], rgv[kMaxBasis];
-  __shared__ int s_J, s_end;
+  // the rotations so far and the right-hand side
   for (int t = tid; t < k; t += blockDim.x) {
     rcs[t] = st->cs[t];
     rsn[t] = st->sn[t];
   }
   for (int t = tid; t <= k; t += blockDim.x) rgv[t] = st->gv[t];
   __syncthreads();
-  if (tid == 0) {
-    // Givens rotations of the new columns in order, convergence per column
-    bool end = false, conv = false, brk = false;
-    int J = k + ncol;
-    for (int i = 0; i < ncol && !end; ++i) {
-      const int j = k + i;
-      double* h = hc[i];
-      for (int l = 0; l < j; ++l) {
+  if (warp == 0) {
+    // the earlier rotations on every new column at once (lane = column)
+    if (lane < ncol) {
+      double* h = hc[lane];
+      for (int l = 0; l < k; ++l) {
         const double t = rcs[l] * h[l] + rsn[l] * h[l + 1];
         h[l + 1] = -rsn[l] * h[l] + rcs[l] * h[l + 1];
         h[l] = t;
       }
-      const double a = h[j], b = h[j + 1];
-      const bool breakdown = !(b != 0.0);
-      const double den = hypot(a, b);
-      double c = 1.0, sn = 0.0;
-      if (den > 0.0) {
-        c = a / den;
-        sn = b / den;
-      }
-      rcs[j] = c;
-      rsn[j] = sn;
-      h[j] = den > 0.0 ? den : a;
-      h[j + 1] = 0.0;
-      rgv[j + 1] = -sn * rgv[j];
-      rgv[j] = c * rgv[j];
-      const double est = fabs(rgv[j + 1]);
-      st->est = est;
-      if (breakdown || est <= st->target) {
-        end = true;
-        conv = true;
-        brk = breakdown;
-        J = j + 1;
-      }
     }
-    if (!end && k + ncol >= restart) end = true;
-    st->jdone = J;
-    st->bsb = nnew;
-    st->nspmv = k + sb;
-    if (end) {
-      st->active = 0;
-      st->converged = conv ? 1 : 0;
-      st->breakdown = brk ? 1 : 0;
-      st->bfin_k = k;
-      st->last_J = J;
-      st->last_beta = st->beta;
-      st->last_est = st->est;
+    __syncwarp();
+    if (lane == 0) {
+      // the block's own rotations in order, and the convergence test per column
+      bool end = false, conv = false, brk = false;
+      int J = k + ncol;
+      for (int i = 0; i < ncol && !end; ++i) {
+        const int j = k + i;
+        double* h = hc[i];
+        for (int l = k; l < j; ++l) {
+          const double t = rcs[l] * h[l] + rsn[l] * h[l + 1];
+          h[l + 1] = -rsn[l] * h[l] + rcs[l] * h[l + 1];
+          h[l] = t;
+        }
+        const double a = h[j], b = h[j + 1];
+        const bool breakdown = !(b != 0.0);
+        const double r2 = a * a + b * b;
+        double c = 1.0, sn = 0.0, den = a;
+        if (r2 > 0.0) {
+          const double inv = rsqrt(r2);
+          c = a * inv;
+          sn = b * inv;
+          den = r2 * inv;
+        }
+        rcs[j] = c;
+        rsn[j] = sn;
+        h[j] = den;
+        h[j + 1] = 0.0;
+        rgv[j + 1] = -sn * rgv[j];
+        rgv[j] = c * rgv[j];
+        const double est = fabs(rgv[j + 1]);
+        st->est = est;
+        if (breakdown || est <= st->target) {
+          end = true;
+          conv = true;
+          brk = breakdown;
+          J = j + 1;
+        }
+      }
+      if (!end && k + ncol >= st->restart) end = true;
+      st->jdone = J;
+      st->bsb = nnew;
+      st->nspmv = k + sb;
+      if (end) {
+        st->active = 0;
+        st->converged = conv ? 1 : 0;
+        st->breakdown = brk ? 1 : 0;
+        st->bfin_k = k;
+        st->last_J = J;
+        st->last_beta = st->beta;
+        st->last_est = st->est;
+      }
+      s_J = J;
+      s_end = end ? 1 : 0;
     }
-    s_J = J;
-    s_end = end ? 1 : 0;
   }
   __syncthreads();
   const int J = s_J;
@@ -229,19 +262,32 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
   for (int i = tid; i < nnew; i += blockDim.x) st->scale[k + 1 + i] = 1.0;
   if (!s_end) return;
   // end of the cycle: back-solve R y = g over the J columns, R staged in the
-  // scratch (column c at scratch[c * kMaxRestart], rows 0..c)
+  // scratch (column c at scratch[c * kMaxRestart], rows 0..c); lane l owns
+  // rows l and l + 32
   for (int t = tid; t < J * kMaxRestart; t += blockDim.x) {
     const int c = t / kMaxRestart, r = t % kMaxRestart;
     if (r <= c) scratch[t] = c < k ? st->H[static_cast<int64_t>(c) * kMaxBasis + r] : hc[c - k][r];
   }
-  __shared__ double ys[kMaxRestart];
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
+    double tr[2], dinv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      tr[h] = r < J ? rgv[r] : 0.0;
+      const double d = r < J ? scratch[r * kMaxRestart + r] : 0.0;
+      dinv[h] = d != 0.0 ? 1.0 / d : 0.0;
+    }
     for (int i = J - 1; i >= 0; --i) {
-      double t = rgv[i];
-      for (int l = i + 1; l < J; ++l) t -= scratch[l * kMaxRestart + i] * ys[l];
-      const double d = scratch[i * kMaxRestart + i];
-      ys[i] = d != 0.0 ? t / d : 0.0;
+      const int hi = i >> 5, li = i & 31;
+      const double mine = (hi ? tr[1] * dinv[1] : tr[0] * dinv[0]);
+      const double yi = __shfl_sync(0xffffffffu, mine, li);
+      if (lane == li) ys[i] = yi;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        if (r < i) tr[h] -= scratch[i * kMaxRestart + r] * yi;
+      }
     }
   }
   __syncthreads();
