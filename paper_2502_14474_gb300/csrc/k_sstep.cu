@@ -331,12 +331,15 @@ __global__ void __launch_bounds__(kBlkThreads)
   const int gx = static_cast<int>(blockIdx.y), vg = static_cast<int>(gridDim.y);
   const int64_t slot = blockIdx.x, slots = gridDim.x;
   const int nv = k + 1 + sb;
+  // the vectors split evenly over the groups, then round-robin over the warps
+  const int per_g = (nv + vg - 1) / vg;
+  const int g0 = gx * per_g, g1 = min(nv, g0 + per_g);
   int vid[VPW];
   bool vok[VPW];
 #pragma unroll
   for (int u = 0; u < VPW; ++u) {
-    vid[u] = gx * VPG + u * NW + warp;  // round-robin over the warps
-    vok[u] = vid[u] < nv;
+    vid[u] = g0 + u * NW + warp;
+    vok[u] = vid[u] < g1;
   }
   float hi[VPW][S], lo[VPW][S], acc[VPW][S];
 #pragma unroll
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(kBlkThreads)
       if (s + 3 < s_end) {
 #pragma unroll
         for (int i = 0; i < S; ++i)
-          w[i] = i < sb ? __ldcg(reinterpret_cast<const float4*>(wcol + i * ld + s))
+          w[i] = i < sb ? __ldg(reinterpret_cast<const float4*>(wcol + i * ld + s))
                         : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < VPW; ++u)
@@ -425,8 +428,8 @@ __global__ void __launch_bounds__(kBlkThreads)
   if (!s_last) return;
   __threadfence();
   for (int q = t; q < VPG * kSMax; q += kBlkThreads) {
-    const int qv = gx * VPG + q / kSMax, qi = q % kSMax;
-    if (qv >= nv || qi >= sb) continue;
+    const int qv = g0 + q / kSMax, qi = q % kSMax;
+    if (qv >= g1 || qi >= sb) continue;
     const double* pr = partials + run * kBlkRun * kBlkStride + qv * kSMax + qi;
     double sum = 0.0;
     for (int r = 0; r < run_len; ++r) sum += __ldcg(pr + r * kBlkStride);
@@ -443,8 +446,8 @@ __global__ void __launch_bounds__(kBlkThreads)
   // one thread per (vector, column) value, the runs summed in order (the
   // loads are independent, so an unrolled loop keeps several in flight)
   for (int q = t; q < VPG * kSMax; q += kBlkThreads) {
-    const int qv = gx * VPG + q / kSMax, qi = q % kSMax;
-    if (qv >= nv || qi >= sb) continue;
+    const int qv = g0 + q / kSMax, qi = q % kSMax;
+    if (qv >= g1 || qi >= sb) continue;
     const double* pr = partials + qv * kSMax + qi;
     double sum = 0.0;
 #pragma unroll 8
