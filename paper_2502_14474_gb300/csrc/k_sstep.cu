@@ -350,39 +350,48 @@ __global__ void __launch_bounds__(kBlkThreads)
   const int64_t s_end = min(n, s_begin + states_per_slot);
   const float* wcol = basis + static_cast<int64_t>(k + 1) * ld;
   if (vok[0]) {
+    // the warp's vector tiles are loaded one tile ahead, so two tiles of
+    // streamed bytes are in flight per lane; the W tile comes from L1
+    auto ld4 = [&](const float* p, int64_t e) {
+      if (e + 3 < s_end) return *reinterpret_cast<const float4*>(p + e);
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // ragged end: past n reads as zero
+      if (e < s_end) r.x = p[e];
+      if (e + 1 < s_end) r.y = p[e + 1];
+      if (e + 2 < s_end) r.z = p[e + 2];
+      return r;
+    };
+    auto ldx = [&](int64_t e, float4 (&x)[VPW]) {
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) {
+        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vok[u] && e < s_end) {
+          const float* p = basis + vid[u] * ld;
+          x[u] = e + 3 < s_end ? __ldcs(reinterpret_cast<const float4*>(p + e)) : ld4(p, e);
+        }
+      }
+    };
     int run = 0;
+    float4 xc[VPW];
+    ldx(s_begin + 4 * lane, xc);
     for (int64_t s = s_begin + 4 * lane; s < s_end; s += 128) {
-      float4 w[S], x[VPW];
-      if (s + 3 < s_end) {
+      float4 xn[VPW];
+      ldx(s + 128, xn);
+      float4 w[S];
 #pragma unroll
-        for (int i = 0; i < S; ++i)
-          w[i] = i < sb ? __ldg(reinterpret_cast<const float4*>(wcol + i * ld + s))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < VPW; ++u)
-          x[u] = vok[u] ? __ldcs(reinterpret_cast<const float4*>(basis + vid[u] * ld + s))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {  // ragged end of the vector: entries past n read as zero
-        auto ld4 = [&](const float* p) {
-          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (s < s_end) r.x = p[s];
-          if (s + 1 < s_end) r.y = p[s + 1];
-          if (s + 2 < s_end) r.z = p[s + 2];
-          return r;
-        };
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-          w[i] = i < sb ? ld4(wcol + i * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < VPW; ++u)
-          x[u] = vok[u] ? ld4(basis + vid[u] * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < S; ++i) {
+        w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < sb)
+          w[i] = s + 3 < s_end ? __ldg(reinterpret_cast<const float4*>(wcol + i * ld + s))
+                               : ld4(wcol + i * ld, s);
       }
 #pragma unroll
       for (int u = 0; u < VPW; ++u)
 #pragma unroll
         for (int i = 0; i < S; ++i)
-          acc[u][i] = fmaf(x[u].x, w[i].x, fmaf(x[u].y, w[i].y, fmaf(x[u].z, w[i].z,
-                                                                  fmaf(x[u].w, w[i].w, acc[u][i]))));
+          acc[u][i] = fmaf(xc[u].x, w[i].x, fmaf(xc[u].y, w[i].y, fmaf(xc[u].z, w[i].z,
+                                                                  fmaf(xc[u].w, w[i].w, acc[u][i]))));
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) xc[u] = xn[u];
       if (++run == 8) {  // fold the FP32 runs into the float-float sums
         run = 0;
 #pragma unroll
