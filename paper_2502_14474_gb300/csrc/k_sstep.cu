@@ -313,9 +313,39 @@ __device__ void block_ls(DevState* st, int k, int sb, int restart, double* scrat
 // last group runs block_ls.
 // ---------------------------------------------------------------------------
 template <int S>
-struct GramVpw {
-  static constexpr int value = S <= 4 ? 4 : (S <= 6 ? 3 : 2);
+struct GramVpw {  // vectors per warp: 8 * VPW vectors per group, FP32 accumulators VPW * S
+  static constexpr int value = S <= 4 ? 6 : 4;
 };
+constexpr int kGramChunk = 512;  // states of W staged per chunk (4 tiles of 128)
+
+// Dynamic shared memory of the Gram pass: the per-lane float-float sums
+// (hi, lo) of every accumulator, thread-contiguous, then two W chunk buffers;
+// the last block reuses the space as block_ls's scratch.
+template <int S>
+constexpr size_t gram_ff_bytes() {
+  return 2ull * GramVpw<S>::value * S * kBlkThreads * sizeof(float);
+}
+template <int S>
+constexpr size_t gram_smem_bytes() {
+  constexpr size_t b = gram_ff_bytes<S>() + 2ull * S * kGramChunk * sizeof(float);
+  constexpr size_t ls = sizeof(double) * kMaxRestart * kMaxRestart;
+  return b > ls ? b : ls;
+}
+
+// 16-byte asynchronous copy global -> shared; bytes past `src_bytes` are zero.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <int S>
 __global__ void __launch_bounds__(kBlkThreads)
@@ -326,7 +356,13 @@ __global__ void __launch_bounds__(kBlkThreads)
   constexpr int VPW = GramVpw<S>::value;
   constexpr int NW = kBlkThreads / 32;
   constexpr int VPG = NW * VPW;  // vectors per group
-  __shared__ __align__(16) double scratch[kMaxRestart * kMaxRestart];
+  constexpr int NA = VPW * S;    // accumulators per lane
+  constexpr int CQ = kGramChunk / 4;  // quads per staged column
+  extern __shared__ __align__(16) unsigned char gram_dyn[];
+  float* fhi = reinterpret_cast<float*>(gram_dyn);
+  float* flo = fhi + NA * kBlkThreads;
+  float4* wbuf = reinterpret_cast<float4*>(gram_dyn + gram_ff_bytes<S>());  // [2][S][CQ]
+  double* scratch = reinterpret_cast<double*>(gram_dyn);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gx = static_cast<int>(blockIdx.y), vg = static_cast<int>(gridDim.y);
   const int64_t slot = blockIdx.x, slots = gridDim.x;
@@ -341,90 +377,111 @@ __global__ void __launch_bounds__(kBlkThreads)
     vid[u] = g0 + u * NW + warp;
     vok[u] = vid[u] < g1;
   }
-  float hi[VPW][S], lo[VPW][S], acc[VPW][S];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) fhi[a * kBlkThreads + threadIdx.x] = flo[a * kBlkThreads + threadIdx.x] = 0.f;
+  float acc[VPW][S];
 #pragma unroll
   for (int u = 0; u < VPW; ++u)
 #pragma unroll
-    for (int i = 0; i < S; ++i) hi[u][i] = lo[u][i] = acc[u][i] = 0.f;
+    for (int i = 0; i < S; ++i) acc[u][i] = 0.f;
+  auto fold = [&]() {  // this lane's FP32 runs into its float-float sums
+#pragma unroll
+    for (int u = 0; u < VPW; ++u)
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const int a = (u * S + i) * kBlkThreads + threadIdx.x;
+        float h = fhi[a], l = flo[a];
+        ff_merge(h, l, acc[u][i], 0.f);
+        fhi[a] = h;
+        flo[a] = l;
+        acc[u][i] = 0.f;
+      }
+  };
   const int64_t s_begin = slot * states_per_slot;
   const int64_t s_end = min(n, s_begin + states_per_slot);
   const float* wcol = basis + static_cast<int64_t>(k + 1) * ld;
-  if (vok[0]) {
-    // the warp's vector tiles are loaded one tile ahead, so two tiles of
-    // streamed bytes are in flight per lane; the W tile comes from L1
-    auto ld4 = [&](const float* p, int64_t e) {
-      if (e + 3 < s_end) return *reinterpret_cast<const float4*>(p + e);
-      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // ragged end: past n reads as zero
-      if (e < s_end) r.x = p[e];
-      if (e + 1 < s_end) r.y = p[e + 1];
-      if (e + 2 < s_end) r.z = p[e + 2];
-      return r;
-    };
-    auto ldx = [&](int64_t e, float4 (&x)[VPW]) {
+  // W chunk c of this slot into buffer b (zero past the end of the vector)
+  auto stage = [&](int64_t c0, int b) {
+    for (int q = threadIdx.x; q < sb * CQ; q += kBlkThreads) {
+      const int i = q / CQ, e4 = q % CQ;
+      const int64_t e = c0 + 4 * e4;
+      int64_t left = s_end - e;
+      const int bytes = left >= 4 ? 16 : (left > 0 ? static_cast<int>(left) * 4 : 0);
+      cp_async16(wbuf + (b * S + i) * CQ + e4, wcol + i * ld + (bytes > 0 ? e : s_begin), bytes);
+    }
+    cp_async_commit();
+  };
+  auto ldx = [&](int64_t e, float4 (&x)[VPW]) {  // the warp's vectors at quad e
 #pragma unroll
-      for (int u = 0; u < VPW; ++u) {
-        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (vok[u] && e < s_end) {
-          const float* p = basis + vid[u] * ld;
-          x[u] = e + 3 < s_end ? __ldcs(reinterpret_cast<const float4*>(p + e)) : ld4(p, e);
+    for (int u = 0; u < VPW; ++u) {
+      x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (vok[u] && e < s_end) {
+        const float* p = basis + vid[u] * ld;
+        if (e + 3 < s_end) {
+          x[u] = __ldcs(reinterpret_cast<const float4*>(p + e));
+        } else {  // ragged end: past n reads as zero
+          x[u].x = p[e];
+          if (e + 1 < s_end) x[u].y = p[e + 1];
+          if (e + 2 < s_end) x[u].z = p[e + 2];
         }
       }
-    };
-    int run = 0;
-    float4 xc[VPW];
-    ldx(s_begin + 4 * lane, xc);
-    for (int64_t s = s_begin + 4 * lane; s < s_end; s += 128) {
+    }
+  };
+  const int64_t nch = (s_end - s_begin + kGramChunk - 1) / kGramChunk;
+  if (nch > 0) stage(s_begin, 0);
+  float4 xc[VPW];
+  ldx(s_begin + 4 * lane, xc);
+  int frun = 0;
+  for (int64_t c = 0; c < nch; ++c) {
+    const int64_t c0 = s_begin + c * kGramChunk;
+    if (c + 1 < nch) {
+      stage(c0 + kGramChunk, static_cast<int>((c + 1) & 1));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // chunk c is in its buffer for every warp
+    const float4* wb = wbuf + static_cast<int>(c & 1) * S * CQ;
+#pragma unroll
+    for (int t = 0; t < kGramChunk / 128; ++t) {
       float4 xn[VPW];
-      ldx(s + 128, xn);
-      float4 w[S];
+      ldx(c0 + 128 * (t + 1) + 4 * lane, xn);  // one tile ahead (the next chunk's first)
+      if (vok[0]) {
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < sb)
-          w[i] = s + 3 < s_end ? __ldg(reinterpret_cast<const float4*>(wcol + i * ld + s))
-                               : ld4(wcol + i * ld, s);
+        for (int i = 0; i < S; ++i) {
+          if (i < sb) {
+            const float4 w = wb[i * CQ + t * 32 + lane];
+#pragma unroll
+            for (int u = 0; u < VPW; ++u)
+              acc[u][i] = fmaf(xc[u].x, w.x, fmaf(xc[u].y, w.y, fmaf(xc[u].z, w.z,
+                                                                  fmaf(xc[u].w, w.w, acc[u][i]))));
+          }
+        }
       }
-#pragma unroll
-      for (int u = 0; u < VPW; ++u)
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-          acc[u][i] = fmaf(xc[u].x, w[i].x, fmaf(xc[u].y, w[i].y, fmaf(xc[u].z, w[i].z,
-                                                                  fmaf(xc[u].w, w[i].w, acc[u][i]))));
 #pragma unroll
       for (int u = 0; u < VPW; ++u) xc[u] = xn[u];
-      if (++run == 8) {  // fold the FP32 runs into the float-float sums
-        run = 0;
-#pragma unroll
-        for (int u = 0; u < VPW; ++u)
-#pragma unroll
-          for (int i = 0; i < S; ++i) {
-            ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
-            acc[u][i] = 0.f;
-          }
-      }
     }
+    if (++frun == 2) {  // 8 tiles of FP32 products per lane, then float-float
+      frun = 0;
+      fold();
+    }
+    __syncthreads();  // every warp is done with this buffer before it is refilled
   }
-  // fold the last run, warp sums (float-float), the slot's partials
+  fold();
+  // warp sums (float-float) and the slot's partials
 #pragma unroll
   for (int u = 0; u < VPW; ++u)
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      ff_merge(hi[u][i], lo[u][i], acc[u][i], 0.f);
+      const int a = (u * S + i) * kBlkThreads + threadIdx.x;
+      float h = fhi[a], l = flo[a];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
-        ff_merge(hi[u][i], lo[u][i], __shfl_xor_sync(0xffffffffu, hi[u][i], o),
-                 __shfl_xor_sync(0xffffffffu, lo[u][i], o));
+        ff_merge(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+      if (lane == 0 && vok[u] && i < sb)
+        partials[slot * kBlkStride + vid[u] * kSMax + i] =
+            static_cast<double>(h) + static_cast<double>(l);
     }
-  if (lane == 0) {
-#pragma unroll
-    for (int u = 0; u < VPW; ++u)
-      if (vok[u])
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-          if (i < sb)
-            partials[slot * kBlkStride + vid[u] * kSMax + i] =
-                static_cast<double>(hi[u][i]) + static_cast<double>(lo[u][i]);
-  }
   __shared__ bool s_last;
   const int t = threadIdx.x;
   // level 1: the last block of this run of slots sums the run in slot order
@@ -472,6 +529,7 @@ __global__ void __launch_bounds__(kBlkThreads)
   if (!s_last) return;
   __threadfence();
   if (t == 0) st->blk_groups = 0;
+  __syncthreads();  // the float-float sums are no longer read: the space is block_ls's
   block_ls(st, k, sb, restart, scratch);
 }
 
@@ -618,8 +676,15 @@ cudaError_t block_dots_launch(const Mat& A, const float* basis, int64_t ld, int 
   int64_t per = (A.n + slots - 1) / slots;
   per = (per + 127) / 128 * 128;
   const int64_t used = (A.n + per - 1) / per;  // <= slots
-  k_block_dots<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kBlkThreads, 0,
-                    s>>>(A.n, per, basis, ld, k, sb, restart, partials, st);
+  constexpr size_t smem = gram_smem_bytes<S>();
+  static bool attr = [] {
+    cudaFuncSetAttribute(k_block_dots<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    return true;
+  }();
+  (void)attr;
+  k_block_dots<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kBlkThreads,
+                    smem, s>>>(A.n, per, basis, ld, k, sb, restart, partials, st);
   return cudaGetLastError();
 }
 
