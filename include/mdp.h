@@ -113,8 +113,8 @@ typedef struct {
                            <= eta * ||T V - V||_inf (default, conservative);
                            1: additionally stop after any restart cycle whose explicit
                            policy residual has ||.||_inf <= eta * ||T V - V||_inf */
-  int32_t s_step;       /* GMRES in s-step form: 0 = classical Gram-Schmidt Arnoldi
-                           (one orthogonalisation per step); 1..8 = blocks of s_step
+  int32_t s_step;       /* GMRES in s-step form (default 6): 0 = classical Gram-Schmidt
+                           Arnoldi (one orthogonalisation per step); 1..8 = blocks of s_step
                            Krylov vectors (monomial basis of A - I) orthogonalised
                            together, with the solution update fused into the last
                            block's pass; not combinable with cgs2 */

@@ -830,6 +830,7 @@ void mdp_default_opts(mdp_solve_opts* o) {
   o->cgs2 = 0;
   o->low_precision_inner = 0;
   o->inner_norm = 0;
+  o->s_step = 6;
 }
 
 size_t mdp_bytes_required(int64_t n, int32_t m, int64_t nnz, mdp_dtype val_t, mdp_dtype store_t,
