@@ -276,22 +276,34 @@ def test_action_major_policy_copy_is_bitwise_neutral(store, kind, monkeypatch):
     b.close()
 
 
-def test_profiler_counts_and_bytes_match_the_solve():
+@pytest.mark.parametrize("s_step", [0, 6])
+def test_profiler_counts_and_bytes_match_the_solve(s_step):
     """The event profiler behind the roofline numbers: one timed launch per
-    executed GMRES step and per sweep, the algorithmic bytes of the policy-row
-    SpMV (4 action + 16 x 8 packed row + 4 v_j + 4 w bytes per state), and
-    percentiles that bracket the mean."""
+    executed policy SpMV and per sweep (classical Arnoldi: one dots and one
+    orthogonalisation launch per step; s-step: one Gram and one update launch
+    per block), the algorithmic bytes of the policy-row SpMV (4 action + 16 x 8
+    packed row + 4 v_j + 4 w bytes per state), and percentiles that bracket the
+    mean."""
     mdp = synth.banded(65536, 8, 16, 4096, 0.5, 0.99, seed=2, dtype=np.float32)
     h = _mk(mdp)
     h.profile(True)
-    V, pi, st = h.solve(tol=1e-9)
+    V, pi, st = h.solve(tol=1e-9, s_step=s_step)
     prof = h.profile_read()
     h.profile(False)
     k = prof["kinds"]
     assert st["converged"]
     assert k["arnoldi_spmv"]["launches"] == st["inner_iters"]
-    assert k["arnoldi_dots"]["launches"] == st["inner_iters"]
-    assert k["arnoldi_ortho"]["launches"] == st["inner_iters"]
+    if s_step == 0:
+        assert k["arnoldi_dots"]["launches"] == st["inner_iters"]
+        assert k["arnoldi_ortho"]["launches"] == st["inner_iters"]
+        assert k["block_gram"]["launches"] == 0
+    else:
+        nb = k["block_gram"]["launches"]
+        assert k["arnoldi_dots"]["launches"] == k["arnoldi_ortho"]["launches"] == 0
+        assert k["block_update"]["launches"] == nb
+        # every block but the last of a cycle ran all s SpMVs
+        assert s_step * nb >= st["inner_iters"] > 0
+        assert k["block_gram"]["bytes"] > 0 and k["block_update"]["bytes"] > 0
     assert k["bellman_ff"]["launches"] == st["bellman_sweeps"]
     assert k["policy_residual"]["launches"] == st["policy_sweeps"] - st["inner_iters"]
     sp = k["arnoldi_spmv"]
