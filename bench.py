@@ -60,6 +60,9 @@ def _args():
                         "solved concurrently; serve: Poisson request stream through the "
                         "continuous-batching loop")
     p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--batch-mode", choices=["fused", "streams"], default="fused",
+                   help="batch512: every solve phase of all MDPs in one launch (fused), or "
+                        "concurrent handles on a pool of streams")
     p.add_argument("--streams", type=int, default=16)
     p.add_argument("--requests", type=int, default=10000)
     p.add_argument("--pool", type=int, default=512,
@@ -362,11 +365,18 @@ def run_batch(args):
     opts = capi.mdp_default_opts()
     opts.max_inner = args.max_inner
 
-    def go(streams):
+    fstream = torch.cuda.Stream()
+
+    def go(streams, mode=None):
+        mode = mode or args.batch_mode
         torch.cuda.synchronize()
         t = time.perf_counter()
-        stats, status = capi.mdp_batch_solve([h.h for h in hs], Vs, pis, opts=opts,
-                                             n_streams=streams, raise_on_error=False)
+        if mode == "fused":
+            stats, status = capi.mdp_batch_solve_fused([h.h for h in hs], Vs, pis, opts=opts,
+                                                       stream=fstream, raise_on_error=False)
+        else:
+            stats, status = capi.mdp_batch_solve([h.h for h in hs], Vs, pis, opts=opts,
+                                                 n_streams=streams, raise_on_error=False)
         torch.cuda.synchronize()
         return time.perf_counter() - t, stats, status
 
@@ -376,7 +386,9 @@ def run_batch(args):
     for _ in range(args.steps):
         el, stats, status = go(args.streams)
         times.append(el)
-    seq_el, _, _ = go(1)
+    other = "streams" if args.batch_mode == "fused" else "fused"
+    other_el = min(go(args.streams, other)[0] for _ in range(2))
+    seq_el, _, _ = go(1, "streams")
     trans = sum(st["transitions"] for st in stats)
     el = float(np.median(times))
     sample = list(range(0, len(mdps), 100))
@@ -407,8 +419,9 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"uneven_batch_{len(mdps)}", "mdps": len(mdps), "nnz": nnz,
                        "n_range": [min(m.n for m in mdps), max(m.n for m in mdps)],
-                       "streams": args.streams, "tol": 1e-9, "autotune": True,
-                       "generation_s": gen_s},
+                       "mode": args.batch_mode, "streams": args.streams, "tol": 1e-9,
+                       "autotune": True, "generation_s": gen_s},
+            f"{other}_ms": other_el * 1e3,
             "converged": sum(1 for x in status if x == "MDP_OK"),
             "sequential_ms": seq_el * 1e3, "speedup_vs_one_stream": seq_el / el,
             "solve_residual_sample": res, "oracle_error": oracle_error, "cpu_baseline": cpu}

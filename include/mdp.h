@@ -253,6 +253,39 @@ mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts*
                            double* const* V_out, int32_t* const* pi_out, mdp_solve_stats* stats,
                            mdp_status* status_out, int32_t n_streams);
 
+/*
+ * mdp_batch_solve_fused -- solve `count` independent MDPs (one handle each) by
+ * the inexact policy iteration of mdp_solve with every solve phase of all the
+ * MDPs in one launch (madupite's solver applied to many problems at once; the
+ * batching of many uneven MDPs is this implementation's).  Each phase kernel
+ * is persistent (one wave of blocks) and walks a device-side work list of
+ * units -- a tile of one MDP's states -- over the MDPs in that phase: the
+ * float-float Bellman backup, the policy residual between restart cycles, and
+ * the s-step GMRES cycle (SpMVs, Gram pass with the least squares, update).
+ * Rounds advance every MDP by one phase; the host reads all MDPs' status with
+ * one copy per phase and rebuilds the work lists; a restart cycle is captured
+ * once as a CUDA graph and replayed (on a non-default stream).
+ *   hs[count]      distinct handles on the current device, at most 64 actions.
+ *   opts           NULL = defaults; needs the GMRES inner solver in s-step form
+ *                  (s_step 1..8) on the FP32 probabilities (no cgs2, no
+ *                  low_precision_inner).  Every cycle has `restart` steps, so the
+ *                  max_inner cap is checked after each cycle.
+ *   V_out[i]       double[n_i] device;  pi_out[i] int32[n_i] device or NULL
+ *                  (pi_out may be NULL);  stats[count] host or NULL.
+ *   stream         one stream for every launch (NULL = legacy default stream,
+ *                  no graph capture).
+ * Each MDP's units and reduction order depend only on that MDP, so its result
+ * is bitwise the same when solved alone through this call and in any batch.
+ * (It is not bitwise the same as mdp_solve, whose kernels are laid out for one
+ * large MDP; both meet the same tolerance.)  mdp_cancel is not checked.
+ * Returns MDP_OK when all converged, else the first non-OK status in index
+ * order (per-MDP statuses in status_out[count] when not NULL); MDP_ERR_ARG for
+ * options or handles it does not support.  Synchronises the stream.
+ */
+mdp_status mdp_batch_solve_fused(mdp_t const* hs, int32_t count, const mdp_solve_opts* opts,
+                                 double* const* V_out, int32_t* const* pi_out,
+                                 mdp_solve_stats* stats, mdp_status* status_out, void* stream);
+
 /* Handle properties (layout chosen at create, memory held). */
 mdp_status mdp_info(mdp_t h, mdp_info_t* info);
 

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["k_bellman.cu", "k_gmres.cu", "k_spmv_f32.cu", "k_spmv_bf16.cu", "k_spmv_f16.cu",
-           "k_sstep.cu", "k_prep.cu", "capi.cu", "noalloc.cu", "ingest.cpp"]
+           "k_sstep.cu", "k_batch.cu", "k_prep.cu", "capi.cu", "noalloc.cu", "ingest.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -32,6 +32,7 @@ EXPORTED = sorted(["mdp_create", "mdp_destroy", "mdp_bellman", "mdp_policy_eval"
                    "mdp_default_opts", "mdp_solve", "mdp_info", "mdp_bytes_required", "mdp_cancel",
                    "mdp_last_error", "mdp_version", "mdp_profile_enable", "mdp_profile_read",
                    "mdp_bellman_noalloc", "mdp_batch_solve", "mdp_pool_trim", "mdp_last_cycle",
+                   "mdp_batch_solve_fused",
                    "mdp_csr_from_functions", "mdp_csr_from_rows", "mdp_csr_from_samples",
                    "mdp_csr_read_petsc",
                    "mdp_csr_write_petsc", "mdp_csr_free"])
@@ -202,6 +203,10 @@ def load(build_if_missing: bool = True):
         lib.mdp_batch_solve.argtypes = [P, I32, ctypes.POINTER(mdp_solve_opts), P, P,
                                         ctypes.POINTER(mdp_solve_stats), P, I32]
         lib.mdp_batch_solve.restype = ctypes.c_int
+        lib.mdp_batch_solve_fused.argtypes = [P, I32, ctypes.POINTER(mdp_solve_opts), P, P,
+                                              ctypes.POINTER(mdp_solve_stats),
+                                              ctypes.POINTER(ctypes.c_int), P]
+        lib.mdp_batch_solve_fused.restype = ctypes.c_int
         lib.mdp_pool_trim.argtypes = [I32, U64, ctypes.POINTER(U64)]
         lib.mdp_pool_trim.restype = ctypes.c_int
         HP = ctypes.POINTER(mdp_host_csr)
@@ -386,6 +391,25 @@ def mdp_batch_solve(handles, V_outs, pi_outs=None, opts=None, n_streams=8,
     status = (ctypes.c_int * max(count, 1))()
     rc = load().mdp_batch_solve(H, count, ctypes.byref(opts) if opts is not None else None, Vp,
                                 Pp, st, status, int(n_streams))
+    if rc != MDP_OK and raise_on_error:
+        _check(rc)
+    return [st[i].as_dict() for i in range(count)], [STATUS_NAMES.get(status[i], status[i])
+                                                     for i in range(count)]
+
+
+def mdp_batch_solve_fused(handles, V_outs, pi_outs=None, opts=None, stream=None,
+                          raise_on_error=True):
+    """Solve independent MDPs with every solve phase of all of them in one launch;
+    returns (per-MDP stats dicts, statuses)."""
+    count = len(handles)
+    H = (ctypes.c_void_p * max(count, 1))(*handles)
+    Vp = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in V_outs])
+    Pp = (ctypes.c_void_p * max(count, 1))(*[_ptr(p) for p in pi_outs]) if pi_outs else None
+    st = (mdp_solve_stats * max(count, 1))()
+    status = (ctypes.c_int * max(count, 1))()
+    rc = load().mdp_batch_solve_fused(H, count,
+                                      ctypes.byref(opts) if opts is not None else None, Vp, Pp,
+                                      st, status, _stream(stream))
     if rc != MDP_OK and raise_on_error:
         _check(rc)
     return [st[i].as_dict() for i in range(count)], [STATUS_NAMES.get(status[i], status[i])

@@ -19,6 +19,7 @@
 #include <tuple>
 #include <string>
 #include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -125,6 +126,9 @@ struct mdp_s {
   float* bt = nullptr;      // BiCGStab t = A s
   double* partials = nullptr;
   double* bpart = nullptr;  // s-step Gram pass partials (allocated on first use)
+  size_t bpart_len = 0;     // doubles
+  double* bnorm = nullptr;  // fused-batch residual partials (allocated on first use)
+  size_t bnorm_len = 0;     // doubles
   DevState* st = nullptr;
   int* flag = nullptr;      // policy range check
   StatusHead* head = nullptr;  // pinned host mirror
@@ -347,7 +351,7 @@ double bytes_richardson(const Mat& A, bool lp) {
 void free_all(mdp_s* h) {
   void* ptrs[] = {h->rp, h->pk, h->pk_am, h->val_lo, h->g, h->g_lo, h->val16, h->lpk, h->row_scale,
                   h->V, h->W1, h->W2, h->pi, h->basis, h->d0, h->d1, h->bt, h->partials, h->bpart,
-                  h->st, h->flag};
+                  h->bnorm, h->st, h->flag};
   cudaStream_t fs = free_stream(h->device);
   if (fs && h->done_ev) cudaStreamWaitEvent(fs, h->done_ev, 0);
   for (void* p : ptrs)
@@ -525,16 +529,45 @@ mdp_status ensure_bicgstab(mdp_s* h, cudaStream_t s) {
 
 // The s-step Gram pass's partial sums: one slot of kBlkMaxV x kSMax doubles
 // per chunk slot (at most one slot per 1024 states).
-mdp_status ensure_sstep(mdp_s* h, cudaStream_t s) {
-  if (h->bpart) return MDP_OK;
+mdp_status ensure_sstep(mdp_s* h, cudaStream_t s, size_t min_doubles = 0) {
+  const size_t want = std::max(block_partials_len(h->A.num_sms, h->A.n), min_doubles);
+  if (h->bpart && h->bpart_len >= want) return MDP_OK;
   const cudaStream_t home = h->home;
   h->home = s;
-  cudaError_t e = dalloc(h, &h->bpart, block_partials_len(h->A.num_sms, h->A.n) * sizeof(double));
+  if (h->bpart) {
+    cudaFreeAsync(h->bpart, s);
+    h->bytes -= h->bpart_len * sizeof(double);
+    h->bpart = nullptr;
+    h->bpart_len = 0;
+  }
+  cudaError_t e = dalloc(h, &h->bpart, want * sizeof(double));
   h->home = home;
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(MDP_ERR_OOM, "device allocation of the s-step partials failed");
   }
+  h->bpart_len = want;
+  return MDP_OK;
+}
+
+// Residual partials of the fused batch kernels (two doubles per unit).
+mdp_status ensure_bnorm(mdp_s* h, cudaStream_t s, size_t doubles) {
+  if (h->bnorm && h->bnorm_len >= doubles) return MDP_OK;
+  const cudaStream_t home = h->home;
+  h->home = s;
+  if (h->bnorm) {
+    cudaFreeAsync(h->bnorm, s);
+    h->bytes -= h->bnorm_len * sizeof(double);
+    h->bnorm = nullptr;
+    h->bnorm_len = 0;
+  }
+  cudaError_t e = dalloc(h, &h->bnorm, doubles * sizeof(double));
+  h->home = home;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, "device allocation of the batch partials failed");
+  }
+  h->bnorm_len = doubles;
   return MDP_OK;
 }
 
@@ -1611,6 +1644,285 @@ mdp_status mdp_batch_solve(mdp_t const* hs, int32_t count, const mdp_solve_opts*
     }
   }
   return first;
+}
+
+mdp_status mdp_batch_solve_fused(mdp_t const* hs, int32_t count, const mdp_solve_opts* opts_in,
+                                 double* const* V_out, int32_t* const* pi_out,
+                                 mdp_solve_stats* stats, mdp_status* status_out, void* stream) {
+  Range nvtx("mdp_batch_solve_fused");
+  if (count < 0 || (count > 0 && (!hs || !V_out)))
+    return fail(MDP_ERR_ARG, "mdp_batch_solve_fused: bad arguments");
+  if (count == 0) return MDP_OK;
+  mdp_solve_opts o;
+  if (opts_in) o = *opts_in;
+  else mdp_default_opts(&o);
+  if (o.restart < 1 || o.restart > kMaxRestart) return fail(MDP_ERR_ARG, "restart in [1, 64]");
+  if (!(o.tol >= 0.0) || !(o.inner_rtol > 0.0)) return fail(MDP_ERR_ARG, "bad tolerances");
+  if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_ERR_ARG, "bad iteration limits");
+  if (o.inner != MDP_INNER_GMRES || o.cgs2 || o.low_precision_inner || o.s_step < 1 ||
+      o.s_step > kSMax || (o.inner_norm != 0 && o.inner_norm != 1))
+    return fail(MDP_ERR_ARG,
+                "mdp_batch_solve_fused runs s-step GMRES (s_step 1..%d) on the FP32 probabilities",
+                kSMax);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(MDP_ERR_CUDA, "no current device");
+  std::unordered_set<mdp_t> seen;
+  for (int32_t i = 0; i < count; ++i) {
+    mdp_s* h = hs[i];
+    if (!h || !V_out[i]) return fail(MDP_ERR_ARG, "mdp_batch_solve_fused: NULL handle or output");
+    if (!seen.insert(h).second)
+      return fail(MDP_ERR_ARG, "mdp_batch_solve_fused: a handle appears twice");
+    if (h->device != dev)
+      return fail(MDP_ERR_ARG, "mdp_batch_solve_fused: every handle must be on the current device");
+    if (h->broken) return fail(MDP_ERR_CUDA, "mdp_batch_solve_fused: handle %d is broken", i);
+    if (h->A.m > 64) return fail(MDP_ERR_ARG, "mdp_batch_solve_fused: at most 64 actions");
+  }
+  DeviceGuard dg(dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int R = o.restart, sblk = o.s_step;
+  const int num_sms = hs[0]->A.num_sms;
+  // per-MDP buffers, initial state and the device descriptors
+  std::vector<BMdp> hd(static_cast<size_t>(count));
+  std::vector<double> pnnz(static_cast<size_t>(count));
+  for (int32_t i = 0; i < count; ++i) {
+    mdp_s* h = hs[i];
+    const Mat& A = h->A;
+    BMdp& d = hd[static_cast<size_t>(i)];
+    d.u_bell = batch_units_bellman(A.n, A.m);
+    d.u_state = batch_units_state(A.n);
+    d.u_gram = batch_units_gram(A.n);
+    mdp_status rc = ensure_basis(h, R, s);
+    if (rc == MDP_OK)
+      rc = ensure_sstep(h, s, static_cast<size_t>(d.u_gram) * (kBlkMaxV * kSMax));
+    if (rc == MDP_OK)
+      rc = ensure_bnorm(h, s, 2 * static_cast<size_t>(std::max(d.u_bell, d.u_state)));
+    if (rc == MDP_OK) rc = set_cycle(h, R, 1, o.inner_rtol, 0.0, 0, s);
+    if (rc != MDP_OK) return rc;
+    CK(h, cudaMemsetAsync(h->V, 0, static_cast<size_t>(A.n) * sizeof(float2), s));
+    d.rp = A.rp;
+    d.col = A.col;
+    d.val = A.val;
+    d.val_lo = A.val_lo;
+    d.g = A.g;
+    d.g_lo = A.g_lo;
+    d.V = h->V;
+    d.pi = h->pi;
+    d.basis = h->basis;
+    d.st = h->st;
+    d.part = h->bnorm;
+    d.bpart = h->bpart;
+    d.n = A.n;
+    d.ld = h->ld;
+    d.m = A.m;
+    d.idx64 = A.idx64;
+    d.uniform_len = A.uniform_len;
+    d.vw = pow2_floor(std::min(32, std::max(1, A.vw)));
+    d.tb = batch_bellman_tile(A.m);
+    d.gamma = static_cast<float>(A.gamma);
+    d.gamma_hi = d.gamma;
+    d.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(d.gamma));
+    pnnz[static_cast<size_t>(i)] =
+        A.uniform_len > 0 ? static_cast<double>(A.n) * A.uniform_len
+                          : static_cast<double>(A.nnz) / static_cast<double>(A.m);
+  }
+  // device buffers: descriptors, four work lists (Bellman, residual, and the
+  // cycle's state-range and Gram units), the gathered status heads
+  const size_t n4 = static_cast<size_t>(count);
+  const size_t off_lists = round_up(n4 * sizeof(BMdp), 256);
+  const size_t off_mdp = off_lists + round_up(4 * sizeof(BList), 256);
+  const size_t off_first = off_mdp + round_up(4 * n4 * sizeof(int32_t), 256);
+  const size_t off_heads = off_first + round_up(4 * (n4 + 1) * sizeof(int64_t), 256);
+  const size_t total_bytes = off_heads + n4 * kHeadBytes;
+  void* dbuf = nullptr;
+  if (pool_alloc(dev, &dbuf, total_bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, "mdp_batch_solve_fused: device allocation failed");
+  }
+  unsigned char* db = static_cast<unsigned char*>(dbuf);
+  const BMdp* d_mdps = reinterpret_cast<const BMdp*>(db);
+  BList* d_lists = reinterpret_cast<BList*>(db + off_lists);
+  std::vector<unsigned char> hbuf(off_heads);  // descriptors + lists, uploaded together
+  std::vector<unsigned char> heads(n4 * kHeadBytes);
+  memcpy(hbuf.data(), hd.data(), n4 * sizeof(BMdp));
+  BList* hl = reinterpret_cast<BList*>(hbuf.data() + off_lists);
+  int32_t* hmdp = reinterpret_cast<int32_t*>(hbuf.data() + off_mdp);
+  int64_t* hfirst = reinterpret_cast<int64_t*>(hbuf.data() + off_first);
+  for (int l = 0; l < 4; ++l) {
+    hl[l].mdp = reinterpret_cast<const int32_t*>(db + off_mdp) + l * n4;
+    hl[l].first = reinterpret_cast<const int64_t*>(db + off_first) + l * (n4 + 1);
+    hl[l].count = 0;
+    hl[l].total = 0;
+  }
+  mdp_status result = MDP_OK;
+  cudaError_t ce = cudaSuccess;
+  auto build = [&](int l, const std::vector<int32_t>& members, int kind) {
+    int64_t t = 0;
+    int32_t* mm = hmdp + l * n4;
+    int64_t* ff = hfirst + l * (n4 + 1);
+    for (size_t p = 0; p < members.size(); ++p) {
+      const BMdp& d = hd[static_cast<size_t>(members[p])];
+      mm[p] = members[p];
+      ff[p] = t;
+      t += kind == 0 ? d.u_bell : (kind == 1 ? d.u_state : d.u_gram);
+    }
+    ff[members.size()] = t;
+    hl[l].count = static_cast<int32_t>(members.size());
+    hl[l].total = t;
+  };
+  auto upload = [&]() {
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(db, hbuf.data(), off_heads, cudaMemcpyHostToDevice, s);
+  };
+  auto read_heads = [&]() {
+    if (ce == cudaSuccess) ce = launch_batch_heads(d_mdps, count, kHeadBytes, db + off_heads, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(heads.data(), db + off_heads, n4 * kHeadBytes, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  };
+  auto head = [&](int32_t i) -> const StatusHead& {
+    return *reinterpret_cast<const StatusHead*>(heads.data() + static_cast<size_t>(i) * kHeadBytes);
+  };
+  // one restart cycle of every MDP in the inner phase: lists 2 (state units) and 3 (Gram units)
+  auto enqueue_cycle_all = [&]() -> cudaError_t {
+    for (int k = 0; k < R; k += sblk) {
+      const int sb = std::min(sblk, R - k);
+      for (int i = 0; i < sb; ++i) {
+        cudaError_t e = launch_batch_spmv(d_mdps, d_lists + 2, k + i, num_sms, s);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_batch_gram(d_mdps, d_lists + 3, k, sb, num_sms, s);
+      if (e != cudaSuccess) return e;
+      e = launch_batch_update(d_mdps, d_lists + 2, k, sb, num_sms, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaGraphExec_t cycle = nullptr;
+  bool tried_graph = false;
+  enum { kOuter = 0, kCont = 1, kInner = 2, kDone = 3 };
+  std::vector<int> phase(n4, kOuter), outer(n4, 0), used(n4, 0);
+  std::vector<double> target(n4, 0.0);
+  std::vector<mdp_solve_stats> ss(n4);
+  std::vector<mdp_status> st(n4, MDP_OK);
+  std::vector<std::string> msg(n4);
+  for (auto& x : ss) memset(&x, 0, sizeof(x));
+  int remaining = count;
+  auto finish_inner = [&](int32_t i) {
+    mdp_solve_stats& q = ss[static_cast<size_t>(i)];
+    q.inner_iters += used[static_cast<size_t>(i)];
+    if (q.outer_iters - 1 < MDP_HISTORY) q.inner_history[q.outer_iters - 1] = used[static_cast<size_t>(i)];
+    phase[static_cast<size_t>(i)] = kOuter;
+  };
+  while (remaining > 0 && ce == cudaSuccess) {
+    std::vector<int32_t> bell, res, inner;
+    for (int32_t i = 0; i < count; ++i) {
+      if (phase[static_cast<size_t>(i)] == kOuter) bell.push_back(i);
+      if (phase[static_cast<size_t>(i)] == kCont) res.push_back(i);
+    }
+    build(0, bell, 0);
+    build(1, res, 1);
+    upload();
+    if (ce == cudaSuccess && !bell.empty()) ce = launch_batch_bellman(d_mdps, d_lists + 0, num_sms, s);
+    if (ce == cudaSuccess && !res.empty())
+      ce = launch_batch_policy_resid(d_mdps, d_lists + 1, num_sms, s);
+    read_heads();
+    if (ce != cudaSuccess) break;
+    for (int32_t i : bell) {
+      const size_t u = static_cast<size_t>(i);
+      mdp_solve_stats& q = ss[u];
+      const double r = head(i).res_inf;
+      q.bellman_sweeps += 1;
+      q.transitions += static_cast<double>(hs[i]->A.nnz);
+      if (q.n_history < MDP_HISTORY) q.residual_history[q.n_history++] = r;
+      q.residual_inf = r;
+      if (r <= o.tol) {
+        q.converged = 1;
+        phase[u] = kDone;
+      } else if (!std::isfinite(r)) {
+        st[u] = MDP_ERR_NOT_CONVERGED;
+        msg[u] = "non-finite Bellman residual";
+        phase[u] = kDone;
+      } else if (outer[u] >= o.max_outer) {
+        st[u] = MDP_ERR_NOT_CONVERGED;
+        msg[u] = "max_outer reached";
+        phase[u] = kDone;
+      } else {
+        outer[u] += 1;
+        q.outer_iters += 1;
+        used[u] = 0;
+        target[u] = o.inner_rtol * r;
+        phase[u] = kInner;
+      }
+      if (phase[u] == kDone) --remaining;
+    }
+    for (int32_t i : res) {
+      const size_t u = static_cast<size_t>(i);
+      ss[u].policy_sweeps += 1;
+      ss[u].transitions += pnnz[u];
+      if (!head(i).active || (o.inner_norm == 1 && head(i).res_inf <= target[u])) finish_inner(i);
+      else phase[u] = kInner;
+    }
+    for (int32_t i = 0; i < count; ++i)
+      if (phase[static_cast<size_t>(i)] == kInner) inner.push_back(i);
+    if (inner.empty()) continue;
+    build(2, inner, 1);
+    build(3, inner, 2);
+    upload();
+    if (ce != cudaSuccess) break;
+    if (!tried_graph && s != nullptr && !getenv("MDP_NO_GRAPHS")) {
+      tried_graph = true;
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+          cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaError_t e = enqueue_cycle_all();
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g ||
+            cudaGraphInstantiate(&cycle, g, 0) != cudaSuccess)
+          cycle = nullptr;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+    }
+    ce = cycle ? cudaGraphLaunch(cycle, s) : enqueue_cycle_all();
+    read_heads();
+    if (ce != cudaSuccess) break;
+    for (int32_t i : inner) {
+      const size_t u = static_cast<size_t>(i);
+      const StatusHead& hh = head(i);
+      used[u] += hh.nspmv;
+      ss[u].policy_sweeps += hh.nspmv;
+      ss[u].transitions += pnnz[u] * hh.nspmv;
+      if (hh.converged || used[u] >= o.max_inner || hh.jdone == 0) finish_inner(i);
+      else phase[u] = kCont;
+    }
+  }
+  if (cycle) cudaGraphExecDestroy(cycle);
+  if (ce != cudaSuccess) {
+    cudaFreeAsync(dbuf, s);
+    for (int32_t i = 0; i < count; ++i) hs[i]->broken = true;
+    return fail(MDP_ERR_CUDA, "mdp_batch_solve_fused: %s", cudaGetErrorString(ce));
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    mdp_s* h = hs[i];
+    CK(h, launch_from_ff(h->A.n, h->V, V_out[i], 1, h->neg, h->A.num_sms, s));
+    if (pi_out && pi_out[i])
+      CK(h, cudaMemcpyAsync(pi_out[i], h->pi, static_cast<size_t>(h->A.n) * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, s));
+    mark_done(h, s);
+  }
+  cudaFreeAsync(dbuf, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(MDP_ERR_CUDA, "mdp_batch_solve_fused: the final synchronisation failed");
+  for (int32_t i = 0; i < count; ++i) {
+    const size_t u = static_cast<size_t>(i);
+    if (stats) stats[u] = ss[u];
+    if (status_out) status_out[u] = st[u];
+    if (result == MDP_OK && st[u] != MDP_OK) {
+      result = st[u];
+      g_err = "mdp_batch_solve_fused: MDP " + std::to_string(i) + ": " + msg[u];
+    }
+  }
+  return result;
 }
 
 mdp_status mdp_profile_enable(mdp_t h, int on) {

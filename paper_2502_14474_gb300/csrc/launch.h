@@ -100,6 +100,50 @@ cudaError_t launch_block_update(const Mat& A, float* basis, int64_t ld, int k, i
 // Doubles of the Gram pass's partials buffer for n states.
 size_t block_partials_len(int num_sms, int64_t n);
 
+// ---- many MDPs per launch (k_batch.cu) --------------------------------------
+// One MDP of a fused batch, as the batched kernels see it (device copy).
+struct BMdp {
+  const void* rp;          // row pointers (int32 or int64 by idx64; unused when uniform_len)
+  const int32_t* col;      // packed col/val groups (k_rows.cuh)
+  const float* val;
+  const float* val_lo;     // FP64 remainders or nullptr
+  const float* g;
+  const float* g_lo;
+  float2* V;               // float-float iterate
+  int32_t* pi;
+  float* basis;
+  DevState* st;
+  double* part;            // per-unit residual partials (2 per unit)
+  double* bpart;           // per-unit Gram partials (float-float pairs, kBlkMaxV * kSMax per unit)
+  int64_t n, ld;
+  int64_t u_bell, u_state, u_gram;  // units of the Bellman, state-range and Gram kernels
+  int32_t m, idx64, uniform_len, vw, tb;
+  float gamma, gamma_hi, gamma_lo;
+};
+// The MDPs taking part in one batched launch: participant p is MDP mdp[p]
+// and owns the global units [first[p], first[p + 1]); total = first[count].
+struct BList {
+  const int32_t* mdp;
+  const int64_t* first;
+  int32_t count;
+  int64_t total;
+};
+cudaError_t launch_batch_bellman(const BMdp* mdps, const BList* list, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_policy_resid(const BMdp* mdps, const BList* list, int num_sms,
+                                      cudaStream_t s);
+cudaError_t launch_batch_spmv(const BMdp* mdps, const BList* list, int j, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_batch_gram(const BMdp* mdps, const BList* list, int k, int sb, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_batch_update(const BMdp* mdps, const BList* list, int k, int sb, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_batch_heads(const BMdp* mdps, int count, size_t head_bytes, unsigned char* out,
+                               cudaStream_t s);
+int batch_bellman_tile(int m);
+int64_t batch_units_bellman(int64_t n, int m);
+int64_t batch_units_state(int64_t n);
+int64_t batch_units_gram(int64_t n);
+
 // K5: V += sum_i y_i v_i over the completed steps (float-float V).
 cudaError_t launch_gmres_update(const Mat& A, float* basis, int64_t ld, float2* V,
                                 DevState* st, cudaStream_t s);
