@@ -380,6 +380,11 @@ def run_batch(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t, stats, status
 
+    if args.profile_solve:  # one batch solve, nothing else (for ncu launch lists)
+        el, stats, _ = go(args.streams)
+        print(json.dumps({"profile_batch_ms": el * 1e3,
+                          "policy_sweeps": sum(st["policy_sweeps"] for st in stats)}))
+        return 0
     for _ in range(max(1, args.warmup)):
         go(args.streams)
     times, stats, status = [], None, None
