@@ -1716,7 +1716,10 @@ mdp_status mdp_batch_solve_fused(mdp_t const* hs, int32_t count, const mdp_solve
     d.m = A.m;
     d.idx64 = A.idx64;
     d.uniform_len = A.uniform_len;
-    d.vw = pow2_floor(std::min(32, std::max(1, A.vw)));
+    // rows of up to 40 entries on average: a thread per row (the packed groups
+    // of two rows in flight); longer rows: the handle's lanes per row
+    const double avg_len = static_cast<double>(A.nnz) / static_cast<double>(A.rows);
+    d.vw = avg_len <= 40.0 ? 1 : pow2_floor(std::min(32, std::max(1, A.vw)));
     d.tb = batch_bellman_tile(A.m);
     d.gamma = static_cast<float>(A.gamma);
     d.gamma_hi = d.gamma;

@@ -135,22 +135,52 @@ __global__ void __launch_bounds__(kBT)
     const int64_t s0 = lu * T;
     const int ns = static_cast<int>(min(static_cast<int64_t>(T), M.n - s0));
     const int rows = ns * m;
-    const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
-    for (int base = 0; base < rows; base += nvec) {
-      const int lr = base + vec;
-      int64_t b = 0, e = 0;
-      if (lr < rows) row_span(M, s0 * m + lr, b, e);
-      float hi, lo;
-      row_ff(M, b, e, lane, vw, hi, lo);
-      gsum_ff_rt(hi, lo, vw);
-      if (lane == 0 && lr < rows) {
-        const int64_t r = s0 * m + lr;
-        const ff sum = ff_norm(hi, lo);
-        const ff gq = ff_norm(__ldcs(M.g + r), M.g_lo ? __ldcs(M.g_lo + r) : 0.f);
-        const ff q = ff_add(ff_mul(sum, ff{M.gamma_hi, M.gamma_lo}), gq);
-        const int a = lr % m, sl = lr / m;
-        qh[a * T + sl] = q.hi;
-        ql[a * T + sl] = q.lo;
+    auto put_q = [&](int lr, float hi, float lo) {
+      const int64_t r = s0 * m + lr;
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(M.g + r), M.g_lo ? __ldcs(M.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{M.gamma_hi, M.gamma_lo}), gq);
+      const int a = lr % m, sl = lr / m;
+      qh[a * T + sl] = q.hi;
+      ql[a * T + sl] = q.lo;
+    };
+    if (vw == 1) {
+      // short rows: a thread per row, the first two packed groups of two rows in flight
+      for (int base = 0; base < rows; base += 2 * kBT) {
+        const int lr[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
+        float hi[2], lo[2];
+        if (M.val_lo) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            int64_t b = 0, e = 0;
+            if (lr[u] < rows) row_span(M, s0 * m + lr[u], b, e);
+            row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi[u], lo[u]);
+          }
+        } else {
+          RowPre<float> R[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            int64_t b = 0, e = 0;
+            if (lr[u] < rows) row_span(M, s0 * m + lr[u], b, e);
+            row_pre<float>(M.col, M.val, b, e, R[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) row_pre_dot_ff(M.col, M.val, GatherFF{M.V}, R[u], hi[u], lo[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (lr[u] < rows) put_q(lr[u], hi[u], lo[u]);
+      }
+    } else {
+      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+      for (int base = 0; base < rows; base += nvec) {
+        const int lr = base + vec;
+        int64_t b = 0, e = 0;
+        if (lr < rows) row_span(M, s0 * m + lr, b, e);
+        float hi, lo;
+        row_ff(M, b, e, lane, vw, hi, lo);
+        gsum_ff_rt(hi, lo, vw);
+        if (lane == 0 && lr < rows) put_q(lr, hi, lo);
       }
     }
     __syncthreads();
@@ -190,31 +220,60 @@ __global__ void __launch_bounds__(kBT)
     const int p = find_part(L, u);
     const BMdp& M = mdps[L.mdp[p]];
     const int64_t lu = u - L.first[p];
-    const int vw = M.vw, lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+    const int vw = M.vw;
     const int64_t s0 = lu * kBStateUnit;
     const int ns = static_cast<int>(min(static_cast<int64_t>(kBStateUnit), M.n - s0));
     double my_max = 0.0, my_sq = 0.0;
-    for (int base = 0; base < ns; base += nvec) {
-      const int t = base + vec;
-      const int64_t s = s0 + t;
-      int64_t b = 0, e = 0, r = 0;
-      if (t < ns) {
-        r = s * M.m + M.pi[s];
-        row_span(M, r, b, e);
+    auto emit = [&](int64_t s, int64_t r, float hi, float lo) {
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(M.g + r), M.g_lo ? __ldcs(M.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{M.gamma_hi, M.gamma_lo}), gq);
+      const float2 v = M.V[s];
+      const float rr = ff_diff_to_float(q.hi, q.lo, v.x, v.y);
+      M.basis[s] = rr;
+      const double rd = static_cast<double>(rr);
+      my_max = fmax(my_max, fabs(rd));
+      my_sq += rd * rd;
+    };
+    if (vw == 1) {
+      // short rows: a thread per state, two policy rows in flight
+      for (int base = 0; base < ns; base += 2 * kBT) {
+        const int t[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
+        int64_t r[2] = {0, 0};
+        float hi[2], lo[2];
+        RowPre<float> R[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          int64_t b = 0, e = 0;
+          if (t[u] < ns) {
+            r[u] = (s0 + t[u]) * M.m + M.pi[s0 + t[u]];
+            row_span(M, r[u], b, e);
+          }
+          if (M.val_lo) row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi[u], lo[u]);
+          else row_pre<float>(M.col, M.val, b, e, R[u]);
+        }
+        if (!M.val_lo) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) row_pre_dot_ff(M.col, M.val, GatherFF{M.V}, R[u], hi[u], lo[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (t[u] < ns) emit(s0 + t[u], r[u], hi[u], lo[u]);
       }
-      float hi, lo;
-      row_ff(M, b, e, lane, vw, hi, lo);
-      gsum_ff_rt(hi, lo, vw);
-      if (lane == 0 && t < ns) {
-        const ff sum = ff_norm(hi, lo);
-        const ff gq = ff_norm(__ldcs(M.g + r), M.g_lo ? __ldcs(M.g_lo + r) : 0.f);
-        const ff q = ff_add(ff_mul(sum, ff{M.gamma_hi, M.gamma_lo}), gq);
-        const float2 v = M.V[s];
-        const float rr = ff_diff_to_float(q.hi, q.lo, v.x, v.y);
-        M.basis[s] = rr;
-        const double rd = static_cast<double>(rr);
-        my_max = fmax(my_max, fabs(rd));
-        my_sq += rd * rd;
+    } else {
+      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+      for (int base = 0; base < ns; base += nvec) {
+        const int t = base + vec;
+        const int64_t s = s0 + t;
+        int64_t b = 0, e = 0, r = 0;
+        if (t < ns) {
+          r = s * M.m + M.pi[s];
+          row_span(M, r, b, e);
+        }
+        float hi, lo;
+        row_ff(M, b, e, lane, vw, hi, lo);
+        gsum_ff_rt(hi, lo, vw);
+        if (lane == 0 && t < ns) emit(s, r, hi, lo);
       }
     }
     unit_norms(M, lu, static_cast<unsigned>(M.u_state), &M.st->counter[kCntPolicy], my_max,
@@ -233,22 +292,44 @@ __global__ void __launch_bounds__(kBT)
     const BMdp& M = mdps[L.mdp[p]];
     if (!M.st->active) continue;
     const int64_t lu = u - L.first[p];
-    const int vw = M.vw, lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+    const int vw = M.vw;
     const float sj = static_cast<float>(M.st->scale[j]);
     const float* x = M.basis + static_cast<int64_t>(j) * M.ld;
     float* w = M.basis + static_cast<int64_t>(j + 1) * M.ld;
     const int64_t s0 = lu * kBStateUnit;
     const int ns = static_cast<int>(min(static_cast<int64_t>(kBStateUnit), M.n - s0));
-    for (int base = 0; base < ns; base += nvec) {
-      const int t = base + vec;
-      const int64_t s = s0 + t;
-      int64_t b = 0, e = 0;
-      if (t < ns) row_span(M, s * M.m + M.pi[s], b, e);
-      float d = 0.f;
-      for (int64_t i = b + lane; i < e; i += vw)
-        d = fmaf(Ld<float>::one(M.val, i), __ldg(x + ldcol(M.col, i)), d);
-      d = gsum_rt(d, vw);
-      if (lane == 0 && t < ns) w[s] = sj * (-M.gamma * d);
+    if (vw == 1) {
+      // short rows: a thread per state, two policy rows in flight
+      for (int base = 0; base < ns; base += 2 * kBT) {
+        const int t[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
+        RowPre<float> R[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          int64_t b = 0, e = 0;
+          if (t[u] < ns) row_span(M, (s0 + t[u]) * M.m + M.pi[s0 + t[u]], b, e);
+          row_pre<float>(M.col, M.val, b, e, R[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (t[u] < ns) {
+            const float d = row_pre_dot<float>(M.col, M.val, GatherF32{x}, R[u]);
+            w[s0 + t[u]] = sj * (-M.gamma * d);
+          }
+        }
+      }
+    } else {
+      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+      for (int base = 0; base < ns; base += nvec) {
+        const int t = base + vec;
+        const int64_t s = s0 + t;
+        int64_t b = 0, e = 0;
+        if (t < ns) row_span(M, s * M.m + M.pi[s], b, e);
+        float d = 0.f;
+        for (int64_t i = b + lane; i < e; i += vw)
+          d = fmaf(Ld<float>::one(M.val, i), __ldg(x + ldcol(M.col, i)), d);
+        d = gsum_rt(d, vw);
+        if (lane == 0 && t < ns) w[s] = sj * (-M.gamma * d);
+      }
     }
   }
 }
