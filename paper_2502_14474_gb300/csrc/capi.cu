@@ -1721,6 +1721,7 @@ mdp_status mdp_batch_solve_fused(mdp_t const* hs, int32_t count, const mdp_solve
     const double avg_len = static_cast<double>(A.nnz) / static_cast<double>(A.rows);
     d.vw = avg_len <= 40.0 ? 1 : pow2_floor(std::min(32, std::max(1, A.vw)));
     d.tb = batch_bellman_tile(A.m);
+    d.maxlen = h->max_len;
     d.gamma = static_cast<float>(A.gamma);
     d.gamma_hi = d.gamma;
     d.gamma_lo = static_cast<float>(A.gamma - static_cast<double>(d.gamma));

@@ -21,6 +21,7 @@ constexpr int kBT = 256;              // threads per block of every batched kern
 constexpr int kBStateUnit = 1024;     // states per unit of the residual, SpMV and update
 constexpr int kBGramUnit = 1024;      // states per unit of the Gram pass
 constexpr int kBRowTile = 2048;       // rows of a Bellman unit (states = max(32, 2048 / m))
+constexpr int kBStreamEnt = 11264;    // entries of a Bellman row batch streamed through shared memory
 
 int batch_bellman_tile(int m) {
   const int t = kBRowTile / m;
@@ -36,6 +37,34 @@ __device__ __forceinline__ int find_part(const BList& L, int64_t u) {
     else hi = mid - 1;
   }
   return lo;
+}
+
+// The units of one block: a contiguous range of the list (equal counts per
+// block), so that consecutive units mostly belong to the same MDP.  `next`
+// advances to unit u, finding its participant and (on a change of MDP) copying
+// the descriptor to shared memory.
+struct UnitWalk {
+  int64_t u0, u1, pend;
+  int p;
+};
+__device__ __forceinline__ UnitWalk walk_begin(const BList& L) {
+  UnitWalk w;
+  const int64_t per = (L.total + gridDim.x - 1) / gridDim.x;
+  w.u0 = static_cast<int64_t>(blockIdx.x) * per;
+  w.u1 = min(L.total, w.u0 + per);
+  w.pend = -1;
+  w.p = -1;
+  return w;
+}
+__device__ __forceinline__ void walk_next(UnitWalk& w, const BList& L, const BMdp* mdps, int64_t u,
+                                          BMdp& sm) {
+  if (u < w.pend) return;
+  __syncthreads();  // every thread is done with the previous descriptor
+  if (w.p < 0) w.p = find_part(L, u);
+  while (u >= L.first[w.p + 1]) ++w.p;
+  w.pend = L.first[w.p + 1];
+  if (threadIdx.x == 0) sm = mdps[L.mdp[w.p]];
+  __syncthreads();
 }
 
 // The block that draws the last of `total` tickets on `counter` (fixed order
@@ -126,11 +155,16 @@ __device__ __forceinline__ void unit_norms(const BMdp& M, int64_t lu, unsigned u
 __global__ void __launch_bounds__(kBT)
     kb_bellman(const BMdp* __restrict__ mdps, const BList* __restrict__ Lp) {
   __shared__ float qh[kBRowTile], ql[kBRowTile];
+  __shared__ BMdp sm;
+  extern __shared__ float ent[];  // [2][kBStreamEnt]: per-entry float-float products
+  float* eh = ent;
+  float* el = ent + kBStreamEnt;
   const BList L = *Lp;
-  for (int64_t u = blockIdx.x; u < L.total; u += gridDim.x) {
-    const int p = find_part(L, u);
-    const BMdp& M = mdps[L.mdp[p]];
-    const int64_t lu = u - L.first[p];
+  UnitWalk wk = walk_begin(L);
+  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+    walk_next(wk, L, mdps, u, sm);
+    const BMdp& M = sm;
+    const int64_t lu = u - L.first[wk.p];
     const int m = M.m, T = M.tb, vw = M.vw;
     const int64_t s0 = lu * T;
     const int ns = static_cast<int>(min(static_cast<int64_t>(T), M.n - s0));
@@ -144,32 +178,66 @@ __global__ void __launch_bounds__(kBT)
       qh[a * T + sl] = q.hi;
       ql[a * T + sl] = q.lo;
     };
-    if (vw == 1) {
-      // short rows: a thread per row, the first two packed groups of two rows in flight
-      for (int base = 0; base < rows; base += 2 * kBT) {
-        const int lr[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
-        float hi[2], lo[2];
-        if (M.val_lo) {
+    const int rb_rows = M.maxlen > 0 ? kBStreamEnt / M.maxlen : 0;
+    if (vw == 1 && !M.val_lo && rb_rows > 0) {
+      // Row batches whose nonzeros fit the shared buffer: the batch's entries
+      // are contiguous in the packed array, so every thread streams whole
+      // 32-byte groups (coalesced, many loads in flight) and stores each
+      // entry's float-float product p*V(col); then a thread per row sums its
+      // products in entry order (the arithmetic of ff_acc, in the same order).
+      for (int rb = 0; rb < rows; rb += rb_rows) {
+        const int nr = min(rb_rows, rows - rb);
+        const int64_t rr0 = s0 * m + rb;
+        int64_t E0, E1, tmp;
+        row_span(M, rr0, E0, tmp);
+        row_span(M, rr0 + nr - 1, tmp, E1);
+        for (int64_t g = (E0 >> 2) + threadIdx.x; (g << 2) < E1; g += kBT) {
+          const int64_t i0 = g << 2;
+          const int4 c = ldcol4(M.col, i0);
+          const float4 pv = Ld<float>::four(M.val, i0);
+          const int cc[4] = {c.x, c.y, c.z, c.w};
+          const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            int64_t b = 0, e = 0;
-            if (lr[u] < rows) row_span(M, s0 * m + lr[u], b, e);
-            row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi[u], lo[u]);
+          for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + q;
+            if (i >= E0 && i < E1) {
+              const float2 v = __ldg(M.V + cc[q]);
+              const float ph = __fmul_rn(pp[q], v.x);
+              float pl = __fmaf_rn(pp[q], v.x, -ph);
+              pl = __fmaf_rn(pp[q], v.y, pl);
+              eh[i - E0] = ph;
+              el[i - E0] = pl;
+            }
           }
-        } else {
-          RowPre<float> R[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            int64_t b = 0, e = 0;
-            if (lr[u] < rows) row_span(M, s0 * m + lr[u], b, e);
-            row_pre<float>(M.col, M.val, b, e, R[u]);
-          }
-#pragma unroll
-          for (int u = 0; u < 2; ++u) row_pre_dot_ff(M.col, M.val, GatherFF{M.V}, R[u], hi[u], lo[u]);
         }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nr; t += kBT) {
+          int64_t b, e;
+          row_span(M, rr0 + t, b, e);
+          float hi = 0.f, lo = 0.f;
+          for (int64_t i = b - E0; i < e - E0; ++i) {
+            float sum, err;
+            two_sum(hi, eh[i], sum, err);
+            hi = sum;
+            lo = __fadd_rn(lo, __fadd_rn(err, el[i]));
+          }
+          put_q(rb + t, hi, lo);
+        }
+        __syncthreads();  // the products are read before the next batch overwrites them
+      }
+    } else if (vw == 1) {
+      // short rows with FP64 remainders or very long rows: a thread per row
+      for (int base = 0; base < rows; base += 2 * kBT) {
+        const int lr[2] = {base + static_cast<int>(threadIdx.x),
+                           base + kBT + static_cast<int>(threadIdx.x)};
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (lr[u] < rows) put_q(lr[u], hi[u], lo[u]);
+        for (int u2 = 0; u2 < 2; ++u2) {
+          int64_t b = 0, e = 0;
+          if (lr[u2] < rows) row_span(M, s0 * m + lr[u2], b, e);
+          float hi, lo;
+          row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi, lo);
+          if (lr[u2] < rows) put_q(lr[u2], hi, lo);
+        }
       }
     } else {
       const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
@@ -216,10 +284,12 @@ __global__ void __launch_bounds__(kBT)
 __global__ void __launch_bounds__(kBT)
     kb_policy_resid(const BMdp* __restrict__ mdps, const BList* __restrict__ Lp) {
   const BList L = *Lp;
-  for (int64_t u = blockIdx.x; u < L.total; u += gridDim.x) {
-    const int p = find_part(L, u);
-    const BMdp& M = mdps[L.mdp[p]];
-    const int64_t lu = u - L.first[p];
+  __shared__ BMdp sm;
+  UnitWalk wk = walk_begin(L);
+  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+    walk_next(wk, L, mdps, u, sm);
+    const BMdp& M = sm;
+    const int64_t lu = u - L.first[wk.p];
     const int vw = M.vw;
     const int64_t s0 = lu * kBStateUnit;
     const int ns = static_cast<int>(min(static_cast<int64_t>(kBStateUnit), M.n - s0));
@@ -284,14 +354,16 @@ __global__ void __launch_bounds__(kBT)
 // ---------------------------------------------------------------------------
 // s-step basis vector: column j+1 = -gamma P_pi (scale_j u_j): unit = 1024 states
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBT)
+__global__ void __launch_bounds__(kBT, 3)
     kb_spmv(const BMdp* __restrict__ mdps, const BList* __restrict__ Lp, int j) {
   const BList L = *Lp;
-  for (int64_t u = blockIdx.x; u < L.total; u += gridDim.x) {
-    const int p = find_part(L, u);
-    const BMdp& M = mdps[L.mdp[p]];
+  __shared__ BMdp sm;
+  UnitWalk wk = walk_begin(L);
+  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+    walk_next(wk, L, mdps, u, sm);
+    const BMdp& M = sm;
     if (!M.st->active) continue;
-    const int64_t lu = u - L.first[p];
+    const int64_t lu = u - L.first[wk.p];
     const int vw = M.vw;
     const float sj = static_cast<float>(M.st->scale[j]);
     const float* x = M.basis + static_cast<int64_t>(j) * M.ld;
@@ -350,11 +422,13 @@ __global__ void __launch_bounds__(kBT)
   const BList L = *Lp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nv = k + 1 + sb;
-  for (int64_t u = blockIdx.x; u < L.total; u += gridDim.x) {
-    const int p = find_part(L, u);
-    const BMdp& M = mdps[L.mdp[p]];
+  __shared__ BMdp sm;
+  UnitWalk wk = walk_begin(L);
+  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+    walk_next(wk, L, mdps, u, sm);
+    const BMdp& M = sm;
     if (!M.st->active) continue;
-    const int64_t lu = u - L.first[p];
+    const int64_t lu = u - L.first[wk.p];
     const int64_t c0 = lu * kBGramUnit;
     const int len = static_cast<int>(min(static_cast<int64_t>(kBGramUnit), M.n - c0));
     __syncthreads();  // the previous unit's readers are done with wsm
@@ -398,25 +472,31 @@ __global__ void __launch_bounds__(kBT)
       }
 #pragma unroll
       for (int i = 0; i < kSMax; ++i) {
+        if (i >= sb) break;  // the same for the whole block
         float h = acc[i], l = 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
           ff_merge(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
-        if (lane == 0 && i < sb) out[v * kSMax + i] = make_float2(h, l);
+        if (lane == 0) out[v * kSMax + i] = make_float2(h, l);
       }
     }
     if (last_of(&M.st->dots_group[0], static_cast<unsigned>(M.u_gram))) {
       // the MDP's Gram block: float-float sums over its units in order
       const float2* all = reinterpret_cast<const float2*>(M.bpart);
-      for (int q = threadIdx.x; q < nv * kSMax; q += kBT) {
+      // one warp per (vector, column): lanes stride over the units, then a
+      // fixed float-float shuffle tree
+      for (int q = warp; q < nv * kSMax; q += kBT / 32) {
         const int v = q / kSMax, i = q % kSMax;
         if (i >= sb) continue;
         float h = 0.f, l = 0.f;
-        for (int64_t c = 0; c < M.u_gram; ++c) {
+        for (int64_t c = lane; c < M.u_gram; c += 32) {
           const float2 t = __ldcg(all + c * kBlkStride + v * kSMax + i);
           ff_merge(h, l, t.x, t.y);
         }
-        M.st->G[v * kSMax + i] = static_cast<double>(h) + static_cast<double>(l);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          ff_merge(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+        if (lane == 0) M.st->G[v * kSMax + i] = static_cast<double>(h) + static_cast<double>(l);
       }
       __syncthreads();
       block_ls(M.st, k, sb, M.st->restart, reinterpret_cast<double*>(wsm));
@@ -434,13 +514,15 @@ __global__ void __launch_bounds__(kBT)
   __shared__ float yc[kBlkMaxV];
   const BList L = *Lp;
   (void)sb;
-  for (int64_t u = blockIdx.x; u < L.total; u += gridDim.x) {
-    const int p = find_part(L, u);
-    const BMdp& M = mdps[L.mdp[p]];
+  __shared__ BMdp sm;
+  UnitWalk wk = walk_begin(L);
+  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+    walk_next(wk, L, mdps, u, sm);
+    const BMdp& M = sm;
     const DevState* st = M.st;
     const bool fin = st->bfin_k == k;
     if (!st->active && !fin) continue;
-    const int64_t lu = u - L.first[p];
+    const int64_t lu = u - L.first[wk.p];
     const int nnew = st->bsb;
     const int J = fin ? st->jdone : 0;
     __syncthreads();  // the previous unit's readers are done with the coefficients
@@ -525,16 +607,22 @@ __global__ void kb_heads(const BMdp* __restrict__ mdps, int count, size_t head_b
 // Launchers: one persistent wave (num_sms x resident blocks per SM)
 // ---------------------------------------------------------------------------
 template <typename K>
-static unsigned waves_of(K kern, int num_sms) {
+static unsigned waves_of(K kern, int num_sms, size_t smem = 0) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBT, 0) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBT, smem) != cudaSuccess ||
+      occ < 1)
     occ = 1;
   return static_cast<unsigned>(num_sms * occ);
 }
 
 cudaError_t launch_batch_bellman(const BMdp* mdps, const BList* list, int num_sms, cudaStream_t s) {
-  static const unsigned nb = waves_of(kb_bellman, num_sms);
-  kb_bellman<<<nb, kBT, 0, s>>>(mdps, list);
+  constexpr size_t smem = 2 * kBStreamEnt * sizeof(float);
+  static const unsigned nb = [&] {
+    cudaFuncSetAttribute(kb_bellman, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    return waves_of(kb_bellman, num_sms, smem);
+  }();
+  kb_bellman<<<nb, kBT, smem, s>>>(mdps, list);
   return cudaGetLastError();
 }
 
