@@ -806,6 +806,12 @@ mdp_status gmres_cycle(mdp_s* h, const int32_t* pi, int steps, bool lp, int cgs2
 
 bool dtype_ok_vec(mdp_dtype t) { return t == MDP_F32 || t == MDP_F64; }
 
+int pow2_ceil(int x) {
+  int p = 1;
+  while (p < x) p *= 2;
+  return p;
+}
+
 int pow2_floor(int x) {
   int p = 1;
   while (p * 2 <= x) p *= 2;
@@ -1716,10 +1722,13 @@ mdp_status mdp_batch_solve_fused(mdp_t const* hs, int32_t count, const mdp_solve
     d.m = A.m;
     d.idx64 = A.idx64;
     d.uniform_len = A.uniform_len;
-    // rows of up to 40 entries on average: a thread per row (the packed groups
-    // of two rows in flight); longer rows: the handle's lanes per row
-    const double avg_len = static_cast<double>(A.nnz) / static_cast<double>(A.rows);
-    d.vw = avg_len <= 40.0 ? 1 : pow2_floor(std::min(32, std::max(1, A.vw)));
+    // rows of up to 64 entries: one packed group of 4 entries per lane, as many
+    // lanes as the longest row has groups (2..16), so a row's loads are in
+    // flight together; longer rows: the handle's lanes per row, entry by entry
+    const int groups = (h->max_len + 3) / 4;
+    d.grp = h->max_len <= 64 ? 1 : 0;
+    d.vw = d.grp ? std::max(2, std::min(16, pow2_ceil(groups)))
+                 : pow2_floor(std::min(32, std::max(1, A.vw)));
     d.tb = batch_bellman_tile(A.m);
     d.maxlen = h->max_len;
     d.gamma = static_cast<float>(A.gamma);

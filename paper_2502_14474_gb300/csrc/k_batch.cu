@@ -21,7 +21,6 @@ constexpr int kBT = 256;              // threads per block of every batched kern
 constexpr int kBStateUnit = 1024;     // states per unit of the residual, SpMV and update
 constexpr int kBGramUnit = 1024;      // states per unit of the Gram pass
 constexpr int kBRowTile = 2048;       // rows of a Bellman unit (states = max(32, 2048 / m))
-constexpr int kBStreamEnt = 11264;    // entries of a Bellman row batch streamed through shared memory
 
 int batch_bellman_tile(int m) {
   const int t = kBRowTile / m;
@@ -119,6 +118,47 @@ __device__ __forceinline__ void row_ff(const BMdp& M, int64_t b, int64_t e, int 
   for (int64_t i = b + lane; i < e; i += vw) ff_elem(M.col, M.val, M.val_lo, V, i, hi, lo);
 }
 
+// Group mode (short rows): lane l of a row's vw lanes takes the packed groups
+// (b >> 2) + l, + vw, ... of the row, so a row of up to 4 vw entries has all its
+// loads in flight at once; within a group the entries are added in order, then
+// the lanes' sums are combined by a fixed shuffle tree.
+__device__ __forceinline__ void row_ff_groups(const BMdp& M, int64_t b, int64_t e, int lane,
+                                              int vw, float& hi, float& lo) {
+  hi = 0.f;
+  lo = 0.f;
+  for (int64_t g = (b >> 2) + lane; (g << 2) < e; g += vw) {
+    const int64_t i0 = g << 2;
+    const int4 c = ldcol4(M.col, i0);
+    const float4 p = Ld<float>::four(M.val, i0);
+    const int cc[4] = {c.x, c.y, c.z, c.w};
+    const float pp[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + q;
+      if (i >= b && i < e) {
+        const float2 v = __ldg(M.V + cc[q]);
+        ff_acc(hi, lo, pp[q], v.x, v.y);
+      }
+    }
+  }
+  gsum_ff_rt(hi, lo, vw);
+}
+
+__device__ __forceinline__ float row_f32_groups(const BMdp& M, const float* __restrict__ x,
+                                                int64_t b, int64_t e, int lane, int vw) {
+  float d = 0.f;
+  for (int64_t g = (b >> 2) + lane; (g << 2) < e; g += vw) {
+    const int64_t i0 = g << 2;
+    const int4 c = ldcol4(M.col, i0);
+    const float4 p = Ld<float>::four(M.val, i0);
+    if (i0 >= b) d = fmaf(p.x, __ldg(x + c.x), d);
+    if (i0 + 1 >= b && i0 + 1 < e) d = fmaf(p.y, __ldg(x + c.y), d);
+    if (i0 + 2 >= b && i0 + 2 < e) d = fmaf(p.z, __ldg(x + c.z), d);
+    if (i0 + 3 >= b && i0 + 3 < e) d = fmaf(p.w, __ldg(x + c.w), d);
+  }
+  return gsum_rt(d, vw);
+}
+
 // Per-unit partials (max |r|, sum r^2) and the MDP's fixed-order reduction.
 __device__ __forceinline__ void unit_norms(const BMdp& M, int64_t lu, unsigned units,
                                            unsigned* counter, double my_max, double my_sq,
@@ -156,9 +196,6 @@ __global__ void __launch_bounds__(kBT)
     kb_bellman(const BMdp* __restrict__ mdps, const BList* __restrict__ Lp) {
   __shared__ float qh[kBRowTile], ql[kBRowTile];
   __shared__ BMdp sm;
-  extern __shared__ float ent[];  // [2][kBStreamEnt]: per-entry float-float products
-  float* eh = ent;
-  float* el = ent + kBStreamEnt;
   const BList L = *Lp;
   UnitWalk wk = walk_begin(L);
   for (int64_t u = wk.u0; u < wk.u1; ++u) {
@@ -178,78 +215,19 @@ __global__ void __launch_bounds__(kBT)
       qh[a * T + sl] = q.hi;
       ql[a * T + sl] = q.lo;
     };
-    const int rb_rows = M.maxlen > 0 ? kBStreamEnt / M.maxlen : 0;
-    if (vw == 1 && !M.val_lo && rb_rows > 0) {
-      // Row batches whose nonzeros fit the shared buffer: the batch's entries
-      // are contiguous in the packed array, so every thread streams whole
-      // 32-byte groups (coalesced, many loads in flight) and stores each
-      // entry's float-float product p*V(col); then a thread per row sums its
-      // products in entry order (the arithmetic of ff_acc, in the same order).
-      for (int rb = 0; rb < rows; rb += rb_rows) {
-        const int nr = min(rb_rows, rows - rb);
-        const int64_t rr0 = s0 * m + rb;
-        int64_t E0, E1, tmp;
-        row_span(M, rr0, E0, tmp);
-        row_span(M, rr0 + nr - 1, tmp, E1);
-        for (int64_t g = (E0 >> 2) + threadIdx.x; (g << 2) < E1; g += kBT) {
-          const int64_t i0 = g << 2;
-          const int4 c = ldcol4(M.col, i0);
-          const float4 pv = Ld<float>::four(M.val, i0);
-          const int cc[4] = {c.x, c.y, c.z, c.w};
-          const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int64_t i = i0 + q;
-            if (i >= E0 && i < E1) {
-              const float2 v = __ldg(M.V + cc[q]);
-              const float ph = __fmul_rn(pp[q], v.x);
-              float pl = __fmaf_rn(pp[q], v.x, -ph);
-              pl = __fmaf_rn(pp[q], v.y, pl);
-              eh[i - E0] = ph;
-              el[i - E0] = pl;
-            }
-          }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < nr; t += kBT) {
-          int64_t b, e;
-          row_span(M, rr0 + t, b, e);
-          float hi = 0.f, lo = 0.f;
-          for (int64_t i = b - E0; i < e - E0; ++i) {
-            float sum, err;
-            two_sum(hi, eh[i], sum, err);
-            hi = sum;
-            lo = __fadd_rn(lo, __fadd_rn(err, el[i]));
-          }
-          put_q(rb + t, hi, lo);
-        }
-        __syncthreads();  // the products are read before the next batch overwrites them
-      }
-    } else if (vw == 1) {
-      // short rows with FP64 remainders or very long rows: a thread per row
-      for (int base = 0; base < rows; base += 2 * kBT) {
-        const int lr[2] = {base + static_cast<int>(threadIdx.x),
-                           base + kBT + static_cast<int>(threadIdx.x)};
-#pragma unroll
-        for (int u2 = 0; u2 < 2; ++u2) {
-          int64_t b = 0, e = 0;
-          if (lr[u2] < rows) row_span(M, s0 * m + lr[u2], b, e);
-          float hi, lo;
-          row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi, lo);
-          if (lr[u2] < rows) put_q(lr[u2], hi, lo);
-        }
-      }
-    } else {
-      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
-      for (int base = 0; base < rows; base += nvec) {
-        const int lr = base + vec;
-        int64_t b = 0, e = 0;
-        if (lr < rows) row_span(M, s0 * m + lr, b, e);
-        float hi, lo;
+    const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+    for (int base = 0; base < rows; base += nvec) {
+      const int lr = base + vec;
+      int64_t b = 0, e = 0;
+      if (lr < rows) row_span(M, s0 * m + lr, b, e);
+      float hi, lo;
+      if (M.grp) {
+        row_ff_groups(M, b, e, lane, vw, hi, lo);
+      } else {
         row_ff(M, b, e, lane, vw, hi, lo);
         gsum_ff_rt(hi, lo, vw);
-        if (lane == 0 && lr < rows) put_q(lr, hi, lo);
       }
+      if (lane == 0 && lr < rows) put_q(lr, hi, lo);
     }
     __syncthreads();
     double my_max = 0.0, my_sq = 0.0;
@@ -305,46 +283,23 @@ __global__ void __launch_bounds__(kBT)
       my_max = fmax(my_max, fabs(rd));
       my_sq += rd * rd;
     };
-    if (vw == 1) {
-      // short rows: a thread per state, two policy rows in flight
-      for (int base = 0; base < ns; base += 2 * kBT) {
-        const int t[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
-        int64_t r[2] = {0, 0};
-        float hi[2], lo[2];
-        RowPre<float> R[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          int64_t b = 0, e = 0;
-          if (t[u] < ns) {
-            r[u] = (s0 + t[u]) * M.m + M.pi[s0 + t[u]];
-            row_span(M, r[u], b, e);
-          }
-          if (M.val_lo) row_dot_ff_g1(M.col, M.val, M.val_lo, GatherFF{M.V}, b, e, hi[u], lo[u]);
-          else row_pre<float>(M.col, M.val, b, e, R[u]);
-        }
-        if (!M.val_lo) {
-#pragma unroll
-          for (int u = 0; u < 2; ++u) row_pre_dot_ff(M.col, M.val, GatherFF{M.V}, R[u], hi[u], lo[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (t[u] < ns) emit(s0 + t[u], r[u], hi[u], lo[u]);
+    const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+    for (int base = 0; base < ns; base += nvec) {
+      const int t = base + vec;
+      const int64_t s = s0 + t;
+      int64_t b = 0, e = 0, r = 0;
+      if (t < ns) {
+        r = s * M.m + M.pi[s];
+        row_span(M, r, b, e);
       }
-    } else {
-      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
-      for (int base = 0; base < ns; base += nvec) {
-        const int t = base + vec;
-        const int64_t s = s0 + t;
-        int64_t b = 0, e = 0, r = 0;
-        if (t < ns) {
-          r = s * M.m + M.pi[s];
-          row_span(M, r, b, e);
-        }
-        float hi, lo;
+      float hi, lo;
+      if (M.grp) {
+        row_ff_groups(M, b, e, lane, vw, hi, lo);
+      } else {
         row_ff(M, b, e, lane, vw, hi, lo);
         gsum_ff_rt(hi, lo, vw);
-        if (lane == 0 && t < ns) emit(s, r, hi, lo);
       }
+      if (lane == 0 && t < ns) emit(s, r, hi, lo);
     }
     unit_norms(M, lu, static_cast<unsigned>(M.u_state), &M.st->counter[kCntPolicy], my_max,
                my_sq, false);
@@ -354,7 +309,7 @@ __global__ void __launch_bounds__(kBT)
 // ---------------------------------------------------------------------------
 // s-step basis vector: column j+1 = -gamma P_pi (scale_j u_j): unit = 1024 states
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBT, 3)
+__global__ void __launch_bounds__(kBT, 4)
     kb_spmv(const BMdp* __restrict__ mdps, const BList* __restrict__ Lp, int j) {
   const BList L = *Lp;
   __shared__ BMdp sm;
@@ -370,38 +325,22 @@ __global__ void __launch_bounds__(kBT, 3)
     float* w = M.basis + static_cast<int64_t>(j + 1) * M.ld;
     const int64_t s0 = lu * kBStateUnit;
     const int ns = static_cast<int>(min(static_cast<int64_t>(kBStateUnit), M.n - s0));
-    if (vw == 1) {
-      // short rows: a thread per state, two policy rows in flight
-      for (int base = 0; base < ns; base += 2 * kBT) {
-        const int t[2] = {base + static_cast<int>(threadIdx.x), base + kBT + static_cast<int>(threadIdx.x)};
-        RowPre<float> R[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          int64_t b = 0, e = 0;
-          if (t[u] < ns) row_span(M, (s0 + t[u]) * M.m + M.pi[s0 + t[u]], b, e);
-          row_pre<float>(M.col, M.val, b, e, R[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (t[u] < ns) {
-            const float d = row_pre_dot<float>(M.col, M.val, GatherF32{x}, R[u]);
-            w[s0 + t[u]] = sj * (-M.gamma * d);
-          }
-        }
-      }
-    } else {
-      const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
-      for (int base = 0; base < ns; base += nvec) {
-        const int t = base + vec;
-        const int64_t s = s0 + t;
-        int64_t b = 0, e = 0;
-        if (t < ns) row_span(M, s * M.m + M.pi[s], b, e);
-        float d = 0.f;
+    const int lane = threadIdx.x % vw, vec = threadIdx.x / vw, nvec = kBT / vw;
+    for (int base = 0; base < ns; base += nvec) {
+      const int t = base + vec;
+      const int64_t s = s0 + t;
+      int64_t b = 0, e = 0;
+      if (t < ns) row_span(M, s * M.m + M.pi[s], b, e);
+      float d;
+      if (M.grp) {
+        d = row_f32_groups(M, x, b, e, lane, vw);
+      } else {
+        d = 0.f;
         for (int64_t i = b + lane; i < e; i += vw)
           d = fmaf(Ld<float>::one(M.val, i), __ldg(x + ldcol(M.col, i)), d);
         d = gsum_rt(d, vw);
-        if (lane == 0 && t < ns) w[s] = sj * (-M.gamma * d);
       }
+      if (lane == 0 && t < ns) w[s] = sj * (-M.gamma * d);
     }
   }
 }
@@ -616,13 +555,8 @@ static unsigned waves_of(K kern, int num_sms, size_t smem = 0) {
 }
 
 cudaError_t launch_batch_bellman(const BMdp* mdps, const BList* list, int num_sms, cudaStream_t s) {
-  constexpr size_t smem = 2 * kBStreamEnt * sizeof(float);
-  static const unsigned nb = [&] {
-    cudaFuncSetAttribute(kb_bellman, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    return waves_of(kb_bellman, num_sms, smem);
-  }();
-  kb_bellman<<<nb, kBT, smem, s>>>(mdps, list);
+  static const unsigned nb = waves_of(kb_bellman, num_sms);
+  kb_bellman<<<nb, kBT, 0, s>>>(mdps, list);
   return cudaGetLastError();
 }
 

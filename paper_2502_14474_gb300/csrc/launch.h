@@ -119,6 +119,7 @@ struct BMdp {
   int64_t u_bell, u_state, u_gram;  // units of the Bellman, state-range and Gram kernels
   int32_t m, idx64, uniform_len, vw, tb;
   int32_t maxlen;          // longest row (entries)
+  int32_t grp;             // 1: short rows, a packed group (4 entries) per lane
   float gamma, gamma_hi, gamma_lo;
 };
 // The MDPs taking part in one batched launch: participant p is MDP mdp[p]
