@@ -38,33 +38,39 @@ __device__ __forceinline__ int find_part(const BList& L, int64_t u) {
   return lo;
 }
 
-// The units of one block: a contiguous range of the list (equal counts per
-// block), so that consecutive units mostly belong to the same MDP.  `next`
-// advances to unit u, finding its participant and (on a change of MDP) copying
-// the descriptor to shared memory.
+// The units of one block: chunks of kBChunk consecutive units, the chunks
+// dealt round-robin to the blocks (chunk c to block c mod gridDim), so that at
+// any time the grid works on a window of neighbouring units -- a few MDPs,
+// whose gathered value vectors stay in L2 -- and a block meets a new MDP only
+// at some chunk boundaries.  `walk_next` finds unit u's participant (moving
+// forward from the last one) and, on a change of MDP, copies the descriptor to
+// shared memory.
+constexpr int kBChunk = 4;
 struct UnitWalk {
-  int64_t u0, u1, pend;
+  int64_t pend;
   int p;
 };
 __device__ __forceinline__ UnitWalk walk_begin(const BList& L) {
+  (void)L;
   UnitWalk w;
-  const int64_t per = (L.total + gridDim.x - 1) / gridDim.x;
-  w.u0 = static_cast<int64_t>(blockIdx.x) * per;
-  w.u1 = min(L.total, w.u0 + per);
   w.pend = -1;
   w.p = -1;
   return w;
 }
 __device__ __forceinline__ void walk_next(UnitWalk& w, const BList& L, const BMdp* mdps, int64_t u,
                                           BMdp& sm) {
-  if (u < w.pend) return;
+  if (w.p >= 0 && u < w.pend) return;
   __syncthreads();  // every thread is done with the previous descriptor
-  if (w.p < 0) w.p = find_part(L, u);
+  if (w.p < 0 || u >= L.first[w.p + 1] + 64) w.p = find_part(L, u);
   while (u >= L.first[w.p + 1]) ++w.p;
   w.pend = L.first[w.p + 1];
   if (threadIdx.x == 0) sm = mdps[L.mdp[w.p]];
   __syncthreads();
 }
+// for (unit u of this block): BATCH_UNITS(L, u) { ... }
+#define BATCH_UNITS(L, u)                                                               \
+  for (int64_t chunk_ = blockIdx.x; chunk_ * kBChunk < (L).total; chunk_ += gridDim.x) \
+    for (int64_t u = chunk_ * kBChunk; u < min((L).total, (chunk_ + 1) * kBChunk); ++u)
 
 // The block that draws the last of `total` tickets on `counter` (fixed order
 // reductions of one MDP's units; the last one resets the counter).
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(kBT)
   __shared__ BMdp sm;
   const BList L = *Lp;
   UnitWalk wk = walk_begin(L);
-  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+  BATCH_UNITS(L, u) {
     walk_next(wk, L, mdps, u, sm);
     const BMdp& M = sm;
     const int64_t lu = u - L.first[wk.p];
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(kBT)
   const BList L = *Lp;
   __shared__ BMdp sm;
   UnitWalk wk = walk_begin(L);
-  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+  BATCH_UNITS(L, u) {
     walk_next(wk, L, mdps, u, sm);
     const BMdp& M = sm;
     const int64_t lu = u - L.first[wk.p];
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(kBT, 4)
   const BList L = *Lp;
   __shared__ BMdp sm;
   UnitWalk wk = walk_begin(L);
-  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+  BATCH_UNITS(L, u) {
     walk_next(wk, L, mdps, u, sm);
     const BMdp& M = sm;
     if (!M.st->active) continue;
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(kBT)
   const int nv = k + 1 + sb;
   __shared__ BMdp sm;
   UnitWalk wk = walk_begin(L);
-  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+  BATCH_UNITS(L, u) {
     walk_next(wk, L, mdps, u, sm);
     const BMdp& M = sm;
     if (!M.st->active) continue;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kBT)
   (void)sb;
   __shared__ BMdp sm;
   UnitWalk wk = walk_begin(L);
-  for (int64_t u = wk.u0; u < wk.u1; ++u) {
+  BATCH_UNITS(L, u) {
     walk_next(wk, L, mdps, u, sm);
     const BMdp& M = sm;
     const DevState* st = M.st;
