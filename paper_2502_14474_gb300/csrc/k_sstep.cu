@@ -29,6 +29,10 @@
 // is an exact dependence of the block (an invariant subspace): its Hessenberg
 // column gets a zero subdiagonal and the cycle ends there, as an Arnoldi
 // breakdown does.
+#include <cstdlib>
+#include <type_traits>
+
+#include "k_async.cuh"
 #include "k_sstep.cuh"
 
 namespace mdpk {
@@ -269,6 +273,263 @@ __global__ void __launch_bounds__(kBlkThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Gram pass, bulk-copy form (the default): one CTA per SM owns a contiguous
+// slot of states and walks it in stages of kGramStage states.  A producer warp
+// copies each stage of every vector of the CTA's group (and of W, when the
+// group does not hold it) from HBM into shared memory with cp.async.bulk,
+// completing on the stage's mbarrier; the copies of up to `nstages` stages are
+// in flight at once, independent of the registers.  Eight consumer warps each
+// own a few of the group's vectors: per 128-state tile a lane reads its quad
+// of W's columns and of its vectors from the stage and accumulates the
+// products in pairs with the packed FP32x2 FMA (two running sums per dot, of
+// the quads' (x, y) and (z, w) entries), folds them into float-float sums held
+// in registers every eight tiles, and releases the stage.  Partials and their
+// fixed-order reduction are those of the register form above (runs of eight
+// slots, then the runs, then block_ls).
+// ---------------------------------------------------------------------------
+constexpr int kGramCW = 8;                          // consumer warps
+constexpr int kGramTh = 32 * (kGramCW + 1);         // + the producer warp
+constexpr int kGramStage = 512;                     // states per stage
+constexpr int kGramMaxStages = 8;
+constexpr size_t kGramSmemBudget = 200 * 1024;      // stage buffers
+constexpr int kGramErrTimeout = 1;                  // dev_error code of a wait that gave up
+// vectors per consumer warp and per group.  A thread holds 2 * VPW * S FP32
+// sums and as many float-float parts; with nine warps per SM (three on one of
+// the four schedulers' register files) a thread has at most 168 registers.
+constexpr int gram_vpw(int S) { return S <= 4 ? 6 : (S <= 6 ? 4 : 3); }
+constexpr int gram_vpg(int S) { return kGramCW * gram_vpw(S); }
+
+template <int S>
+__global__ void __launch_bounds__(kGramTh, 1)
+    k_block_gram(int64_t n, int64_t states_per_slot, const float* __restrict__ basis, int64_t ld,
+                 int k, int sb, int restart, int nstages, double* __restrict__ partials,
+                 DevState* __restrict__ st) {
+  if (!st->active) return;
+  constexpr int NW = kGramCW, VPW = gram_vpw(S);
+  extern __shared__ __align__(128) unsigned char gram_stage_dyn[];
+  __shared__ __align__(8) uint64_t full[kGramMaxStages], empty[kGramMaxStages];
+  __shared__ int s_abort;
+  __shared__ bool s_last;
+  float* stages = reinterpret_cast<float*>(gram_stage_dyn);
+  double* scratch = reinterpret_cast<double*>(gram_stage_dyn);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+  const int gx = static_cast<int>(blockIdx.y), vg = static_cast<int>(gridDim.y);
+  const int64_t slot = blockIdx.x, slots = gridDim.x;
+  const int nv = k + 1 + sb;
+  const int per_g = (nv + vg - 1) / vg;
+  const int g0 = gx * per_g, g1 = min(nv, g0 + per_g);
+  const int ng = g1 - g0;
+  // W's columns inside the group's copies (the group holds the last vectors) or after them
+  const bool w_in = g1 == nv && g0 <= k + 1;
+  const int w_off = w_in ? k + 1 - g0 : ng;
+  const int ncp = ng + (w_in ? 0 : sb);
+  const int64_t s_begin = slot * states_per_slot;
+  const int64_t s_end = min(n, s_begin + states_per_slot);
+  const int64_t nch = s_end > s_begin ? (s_end - s_begin + kGramStage - 1) / kGramStage : 0;
+  if (t == 0) {
+    s_abort = 0;
+    for (int b = 0; b < nstages; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  float fh[VPW][S], fl[VPW][S];
+  int vloc[VPW];
+  bool vok[VPW];
+#pragma unroll
+  for (int u = 0; u < VPW; ++u) {
+    vloc[u] = u * NW + warp;
+    vok[u] = warp < NW && vloc[u] < ng;
+  }
+  if (warp == NW) {
+    // ---- producer: stage c into buffer c % nstages once its last reader left
+    int64_t issued = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const int b = static_cast<int>(c % nstages);
+      if (c >= nstages &&
+          !mbar_wait(&empty[b], static_cast<unsigned>((c / nstages - 1) & 1), &s_abort)) {
+        s_abort = 1;
+        break;
+      }
+      const int64_t c0 = s_begin + c * kGramStage;
+      const int64_t left = s_end - c0;
+      // a short last stage rounds up to 16 bytes: the column's padding (ld >=
+      // n rounded up to 64) or the next slot's states, masked by the consumers
+      const unsigned bytes = left >= kGramStage ? kGramStage * 4u
+                                                : static_cast<unsigned>((left * 4 + 15) & ~15);
+      if (lane == 0) mbar_arrive_expect_tx(&full[b], bytes * static_cast<unsigned>(ncp));
+      __syncwarp();
+      float* dst = stages + static_cast<size_t>(b) * ncp * kGramStage;
+      for (int q = lane; q < ncp; q += 32) {
+        const int v = q < ng ? g0 + q : k + 1 + (q - ng);
+        bulk_g2s(dst + static_cast<size_t>(q) * kGramStage, basis + v * ld + c0, bytes, &full[b]);
+      }
+      issued = c + 1;
+    }
+    // copies still in flight (only after an abort) land before the CTA leaves
+    if (lane == 0 && s_abort) {
+      const int none = 0;
+      for (int64_t c = max(int64_t(0), issued - nstages); c < issued; ++c)
+        mbar_wait(&full[c % nstages], static_cast<unsigned>((c / nstages) & 1), &none);
+    }
+  } else {
+    // ---- consumers.  acc[u][i] holds two running sums, of the (x, y) and of
+    // the (z, w) entries of the lane's quads
+    float2 acc[VPW][S];
+#pragma unroll
+    for (int u = 0; u < VPW; ++u)
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        acc[u][i] = make_float2(0.f, 0.f);
+        fh[u][i] = fl[u][i] = 0.f;
+      }
+    auto fold = [&]() {
+#pragma unroll
+      for (int u = 0; u < VPW; ++u)
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          ff_merge(fh[u][i], fl[u][i], acc[u][i].x, 0.f);
+          ff_merge(fh[u][i], fl[u][i], acc[u][i].y, 0.f);
+          acc[u][i] = make_float2(0.f, 0.f);
+        }
+    };
+    // one 128-state tile of a stage; MASKED: the stage ends inside the slot
+    // and its entries from `left` on are zero
+    auto tile = [&](const float* stg, int tl, int64_t left, auto masked) {
+      constexpr bool MASKED = decltype(masked)::value;
+      const int e = tl * 128 + 4 * lane;
+      int lim = 4;
+      if constexpr (MASKED)
+        lim = left - e >= 4 ? 4 : (left - e > 0 ? static_cast<int>(left - e) : 0);
+      auto ld4 = [&](const float* p) {
+        float4 x = *reinterpret_cast<const float4*>(p);
+        if constexpr (MASKED) {
+          if (lim < 1) x.x = 0.f;
+          if (lim < 2) x.y = 0.f;
+          if (lim < 3) x.z = 0.f;
+          if (lim < 4) x.w = 0.f;
+        }
+        return x;
+      };
+      float2 wa[S], wb[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const float4 w = i < sb ? ld4(stg + (w_off + i) * kGramStage + e)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        wa[i] = make_float2(w.x, w.y);
+        wb[i] = make_float2(w.z, w.w);
+      }
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) {
+        if (vok[u]) {
+          const float4 x = ld4(stg + vloc[u] * kGramStage + e);
+          const float2 xa = make_float2(x.x, x.y), xb = make_float2(x.z, x.w);
+#pragma unroll
+          for (int i = 0; i < S; ++i)
+            acc[u][i] = __ffma2_rn(xb, wb[i], __ffma2_rn(xa, wa[i], acc[u][i]));
+        }
+      }
+    };
+    int ftiles = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const int b = static_cast<int>(c % nstages);
+      if (!mbar_wait(&full[b], static_cast<unsigned>((c / nstages) & 1), &s_abort)) {
+        s_abort = 1;
+        break;
+      }
+      const float* stg = stages + static_cast<size_t>(b) * ncp * kGramStage;
+      const int64_t left = s_end - (s_begin + c * kGramStage);
+      if (left >= kGramStage) {
+#pragma unroll
+        for (int tl = 0; tl < kGramStage / 128; ++tl)
+          tile(stg, tl, left, std::integral_constant<bool, false>{});
+      } else {
+#pragma unroll
+        for (int tl = 0; tl < kGramStage / 128; ++tl)
+          tile(stg, tl, left, std::integral_constant<bool, true>{});
+      }
+      // this warp no longer reads the stage (__syncwarp orders the lanes'
+      // reads before lane 0's release)
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+      ftiles += kGramStage / 128;
+      if (ftiles >= 8) {
+        ftiles = 0;
+        fold();
+      }
+    }
+    fold();
+    // warp sums (float-float) and the slot's partials
+#pragma unroll
+    for (int u = 0; u < VPW; ++u)
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        float h = fh[u][i], l = fl[u][i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          ff_merge(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+        if (lane == 0 && vok[u] && i < sb)
+          partials[slot * kBlkStride + (g0 + vloc[u]) * kSMax + i] =
+              static_cast<double>(h) + static_cast<double>(l);
+      }
+  }
+  __syncthreads();
+  // a wait gave up: report it (the solve reads the flag at its next status
+  // check and fails the call) and still take part in the reduction, so that
+  // the tickets return to zero
+  if (s_abort && t == 0) atomicExch(&st->dev_error, kGramErrTimeout);
+
+  // level 1: the last block of this run of slots sums the run in slot order
+  const int64_t run = slot / kBlkRun, runs = (slots + kBlkRun - 1) / kBlkRun;
+  const int64_t run_len = min(static_cast<int64_t>(kBlkRun), slots - run * kBlkRun);
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->dots_run[gx][run], 1u) == run_len - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int q = t; q < ng * kSMax; q += kGramTh) {
+    const int qv = g0 + q / kSMax, qi = q % kSMax;
+    if (qi >= sb) continue;
+    const double* pr = partials + run * kBlkRun * kBlkStride + qv * kSMax + qi;
+    double sum = 0.0;
+    for (int r = 0; r < run_len; ++r) sum += __ldcg(pr + r * kBlkStride);
+    partials[run * kBlkRun * kBlkStride + qv * kSMax + qi] = sum;
+  }
+  if (t == 0) st->dots_run[gx][run] = 0;
+  // level 2: the last run of this group sums the runs in order
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->dots_group[gx], 1u) == runs - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int q = t; q < ng * kSMax; q += kGramTh) {
+    const int qv = g0 + q / kSMax, qi = q % kSMax;
+    if (qi >= sb) continue;
+    const double* pr = partials + qv * kSMax + qi;
+    double sum = 0.0;
+#pragma unroll 8
+    for (int64_t r = 0; r < runs; ++r) sum += __ldcg(pr + r * kBlkRun * kBlkStride);
+    st->G[qv * kSMax + qi] = sum;
+  }
+  if (t == 0) st->dots_group[gx] = 0;
+  // level 3: the last group runs the block's small steps
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&st->blk_groups, 1u) == static_cast<unsigned>(vg) - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (t == 0) st->blk_groups = 0;
+  __syncthreads();  // the stages are no longer read: the space is block_ls's
+  block_ls(st, k, sb, restart, scratch);
+}
+
+// ---------------------------------------------------------------------------
 // Update pass: q_{k+1+i} = sum_{l <= i} (w_{l+1} - sum_v C[v][l] u_v) Rinv[l][i]
 // over basis columns k+1.., in place; on the block that ends the cycle also
 // V += sum_{v < J} y_v q_v (float-float V).  Warp tiles of 128 states: lane l
@@ -365,8 +626,42 @@ __global__ void __launch_bounds__(kBlkThreads)
 int64_t block_slots(int num_sms, int64_t n);
 
 template <int S>
+cudaError_t block_gram_launch(const Mat& A, const float* basis, int64_t ld, int k, int sb,
+                              int restart, double* partials, DevState* st, cudaStream_t s) {
+  const int nv = k + 1 + sb;
+  const int vg = (nv + gram_vpg(S) - 1) / gram_vpg(S);
+  // one CTA per SM in one wave; slot boundaries on whole stages
+  int64_t slots = static_cast<int64_t>(A.num_sms) / vg;
+  const int64_t cap = block_slots(A.num_sms, A.n);
+  if (slots > cap) slots = cap;
+  if (slots < 1) slots = 1;
+  int64_t per = (A.n + slots - 1) / slots;
+  per = (per + kGramStage - 1) / kGramStage * kGramStage;
+  const int64_t used = (A.n + per - 1) / per;  // <= slots
+  const int per_g = (nv + vg - 1) / vg;
+  const size_t stage_bytes = static_cast<size_t>(per_g + sb) * kGramStage * sizeof(float);
+  int nstages = static_cast<int>(kGramSmemBudget / stage_bytes);
+  if (nstages > kGramMaxStages) nstages = kGramMaxStages;
+  size_t smem = static_cast<size_t>(nstages) * stage_bytes;
+  const size_t ls = sizeof(double) * kMaxRestart * kMaxRestart;
+  if (smem < ls) smem = ls;
+  static bool attr = [] {
+    cudaFuncSetAttribute(k_block_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kGramSmemBudget));
+    return true;
+  }();
+  (void)attr;
+  k_block_gram<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kGramTh, smem,
+                    s>>>(A.n, per, basis, ld, k, sb, restart, nstages, partials, st);
+  return cudaGetLastError();
+}
+
+template <int S>
 cudaError_t block_dots_launch(const Mat& A, const float* basis, int64_t ld, int k, int sb,
                               int restart, double* partials, DevState* st, cudaStream_t s) {
+  // the register-staged form stays selectable for comparison (MDP_GRAM_REGS)
+  static const bool regs = getenv("MDP_GRAM_REGS") != nullptr;
+  if (!regs) return block_gram_launch<S>(A, basis, ld, k, sb, restart, partials, st, s);
   constexpr int VPG = (kBlkThreads / 32) * GramVpw<S>::value;
   const int nv = k + 1 + sb;
   const int vg = (nv + VPG - 1) / VPG;

@@ -232,6 +232,8 @@ struct DevState {
   double est;         // current residual estimate |g_{j+1}|
   int nspmv;          // policy-row SpMVs the cycle ran (s-step: may exceed jdone)
   int bfin_k;         // s-step: first step of the block that ends the cycle, -1 before
+  int dev_error;      // non-zero: a bounded device wait gave up (the kernel's code)
+  int dev_error_pad;
   double H[kMaxBasis * kMaxRestart];
   double cs[kMaxRestart], sn[kMaxRestart];
   double gv[kMaxBasis];
