@@ -155,6 +155,12 @@ typedef struct {
   size_t device_bytes;   /* library-owned device memory of this handle */
   double gamma;
   int32_t maximize;      /* 1 when created with MDP_FLAG_MAXIMIZE */
+  int32_t window;        /* 1 when the banded kernels stage V in a shared-memory ring */
+  int32_t ff_screen;     /* 1 when the float-float backups screen the actions in FP32
+                            and repeat only the candidate rows in float-float (same
+                            results bit for bit; opt-in: environment MDP_FF_SCREEN
+                            at create, for banded rows of 16 aligned entries and a
+                            power-of-two action count up to 32) */
 } mdp_info_t;
 
 /*

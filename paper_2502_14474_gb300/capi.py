@@ -91,7 +91,8 @@ class mdp_info_t(ctypes.Structure):
                 ("uniform_len", ctypes.c_int32), ("idx64", ctypes.c_int32),
                 ("band", ctypes.c_int64), ("has_low_precision", ctypes.c_int32),
                 ("store_t", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
-                ("gamma", ctypes.c_double), ("maximize", ctypes.c_int32)]
+                ("gamma", ctypes.c_double), ("maximize", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("ff_screen", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -63,9 +63,12 @@ struct StatusHead {
   int active, jdone, converged, breakdown, restart, target_rel;
   double eta, target, beta, est;
   int nspmv, bfin_k;
+  int dev_error, dev_error_pad;
 };
 static_assert(offsetof(StatusHead, est) == offsetof(DevState, est), "DevState prefix layout");
 static_assert(offsetof(StatusHead, bfin_k) == offsetof(DevState, bfin_k), "DevState prefix layout");
+static_assert(offsetof(StatusHead, dev_error) == offsetof(DevState, dev_error),
+              "DevState prefix layout");
 constexpr size_t kHeadBytes = sizeof(StatusHead);
 
 struct ProfRec {
@@ -576,6 +579,15 @@ mdp_status read_head(mdp_s* h, cudaStream_t s, bool flush = true) {
   CK(h, cudaMemcpyAsync(h->head, h->st, kHeadBytes, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   if (flush) prof_flush(h);
+  if (h->head->dev_error) {
+    // a kernel's bounded wait gave up: the work of that launch is incomplete;
+    // the flag is cleared so that the handle stays usable
+    const int code = h->head->dev_error;
+    CK(h, cudaMemsetAsync(reinterpret_cast<char*>(h->st) + offsetof(DevState, dev_error), 0,
+                          sizeof(int), s));
+    CK(h, cudaStreamSynchronize(s));
+    return fail(MDP_ERR_TIMEOUT, "a device wait exceeded its bound (code %d)", code);
+  }
   return MDP_OK;
 }
 
@@ -1105,6 +1117,7 @@ mdp_status mdp_create(mdp_t* out, int64_t n, int32_t m, const int64_t* row_ptr,
   // float-float slots) and the matrix is large enough to amortise the fills
   A.window = (h->band <= 7680 && n >= 16 * (2 * h->band + 1)) ? 1 : 0;
   if (getenv("MDP_NO_WINDOW")) A.window = 0;
+  A.screen = getenv("MDP_FF_SCREEN") ? 1 : 0;
 
   h->store_t = store_t;
   h->neg = neg;
@@ -1194,6 +1207,8 @@ mdp_status mdp_info(mdp_t h, mdp_info_t* info) {
   info->has_low_precision = (h->val16 != nullptr || h->lpk != nullptr) ? 1 : 0;
   info->store_t = h->store_t;
   info->maximize = h->neg;
+  info->window = h->A.window;
+  info->ff_screen = bellman_screened(h->A) ? 1 : 0;
   info->device_bytes = h->bytes;
   info->gamma = h->A.gamma;
   return MDP_OK;

@@ -17,6 +17,8 @@
 // FF = float-float: V is float2 (hi, lo), the row sums are error-free
 // TwoSum/TwoProd accumulations, gamma and g are float-float; this is the
 // high-precision residual of the outer iteration.  Otherwise FP32 throughout.
+#include <type_traits>
+
 #include "k_rows.cuh"
 #include "launch.h"
 
@@ -389,65 +391,195 @@ __global__ void __launch_bounds__(kThreads)
 // because R exceeds the distance between them.  Gathers become shared-memory
 // loads instead of scattered 32-byte L2 sectors.
 // ---------------------------------------------------------------------------
-template <bool FF>
-struct RingOf;
-template <>
-struct RingOf<true> {
-  using T = float2;
-  using G = RingFF;
-};
-template <>
-struct RingOf<false> {
-  using T = float;
-  using G = RingF32;
-};
+// Screened float-float pass (rows of 4*VW aligned entries, m a power of two
+// dividing 32, so that after the reduce-scatter thread base + i owns row
+// base + i and a state's m rows sit on m aligned lanes of one warp).
+//
+// Every row is first summed in FP32 over the high parts of V, q32 =
+// fl(gamma * sum p h + g), together with a bound E >= |q32 - q| on the
+// distance to the float-float value q of the full pass:
+//   |q32 - q| <= u (|q32| + (k + 2) gamma A + |g|) + O(u^2),  A = sum |p h|,
+// for k entries per row, u = 2^-24 (the FP32 dot product's error (k+1) u A,
+// the dropped low parts of V, gamma and g one u each, the final rounding u
+// |q32|).  E doubles the constant, E = 2 (k + 3) u (gamma A + |g| + |q32|).
+// A row whose lower bound q32 - E (rounded down) exceeds the smallest upper
+// bound q32 + E (rounded up) among its state's actions has a float-float
+// value strictly above the state's minimum, so it can neither attain the
+// minimum nor tie with it.  Only the remaining candidates gather the low parts
+// and repeat the row sum in float-float with exactly the operations of the
+// full pass; the state's minimum and its lowest minimising action, hence V'
+// and pi, are bitwise those of the full pass.  The winner of each state is
+// left in b_hi / b_lo / b_arg at the state's tile slot.
+template <int VW, typename IdxT>
+__device__ __forceinline__ void bellman_pass_screened(const Csr<IdxT>& P,
+                                                      const float* __restrict__ rh,
+                                                      const float* __restrict__ rl, int mask,
+                                                      int64_t r0, int lr0, int64_t rows_here,
+                                                      int lane, float* b_hi, float* b_lo,
+                                                      int* b_arg) {
+  constexpr unsigned kAll = 0xffffffffu;
+  int4 c[VW];
+  float4 q[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    if (lr0 + u < rows_here) {
+      const int64_t b = (r0 + lr0 + u) * P.uniform_len + 4 * lane;
+      c[u] = ldcol4(P.col, b);
+      q[u] = Ld<float>::four(P.val, b);
+    } else {
+      c[u] = make_int4(0, 0, 0, 0);
+      q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  float p32[VW], a32[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    c[u] = make_int4(c[u].x & mask, c[u].y & mask, c[u].z & mask, c[u].w & mask);
+    const float h0 = rh[c[u].x], h1 = rh[c[u].y], h2 = rh[c[u].z], h3 = rh[c[u].w];
+    p32[u] = fmaf(q[u].w, h3, fmaf(q[u].z, h2, fmaf(q[u].y, h1, q[u].x * h0)));
+    a32[u] = fmaf(fabsf(q[u].w), fabsf(h3),
+                  fmaf(fabsf(q[u].z), fabsf(h2), fmaf(fabsf(q[u].y), fabsf(h1), fabsf(q[u].x * h0))));
+  }
+  const float s32 = reduce_scatter<VW>(p32, lane);
+  const float sa = reduce_scatter<VW>(a32, lane);
+  const int lr = lr0 + lane;
+  const bool valid = lr < rows_here;
+  const int64_t r = r0 + lr;
+  float ghi = 0.f, glo = 0.f;
+  if (valid) {
+    ghi = __ldcs(P.g + r);
+    if (P.g_lo) glo = __ldcs(P.g_lo + r);
+  }
+  const float inf = __int_as_float(0x7f800000);
+  const float q32 = fmaf(P.gamma_hi, s32, ghi);
+  const float cE = 2.f * static_cast<float>(P.uniform_len + 3) * 0x1p-24f;
+  const float E = fmaf(cE, fmaf(P.gamma_hi, sa, fabsf(ghi)) + fabsf(q32), 1e-30f);
+  float up = valid ? __fadd_ru(q32, E) : inf;
+  const float dn = valid ? __fsub_rd(q32, E) : inf;
+  for (int o = 1; o < P.m; o <<= 1) up = fminf(up, __shfl_xor_sync(kAll, up, o));
+  const bool cand = valid && !(dn > up);  // NaN bounds keep the row
+  float ph[VW], pl[VW];
+#pragma unroll
+  for (int u = 0; u < VW; ++u) {
+    float h = 0.f, l = 0.f;
+    if (__shfl_sync(kAll, cand ? 1 : 0, u, VW)) {
+      ff_acc(h, l, q[u].x, rh[c[u].x], rl[c[u].x]);
+      ff_acc(h, l, q[u].y, rh[c[u].y], rl[c[u].y]);
+      ff_acc(h, l, q[u].z, rh[c[u].z], rl[c[u].z]);
+      ff_acc(h, l, q[u].w, rh[c[u].w], rl[c[u].w]);
+    }
+    ph[u] = h;
+    pl[u] = l;
+  }
+  float hi, lo;
+  reduce_scatter_ff<VW>(ph, pl, lane, hi, lo);
+  float bh = inf, bl = 0.f;
+  if (cand) {
+    const ff qq = ff_add(ff_mul(ff_norm(hi, lo), ff{P.gamma_hi, P.gamma_lo}), ff_norm(ghi, glo));
+    bh = qq.hi;
+    bl = qq.lo;
+  }
+  // (value, action) minimum over the state's lanes: the full pass keeps the
+  // first of equal values, i.e. the lowest action among them
+  const int a = lr & (P.m - 1);
+  int ba = a;
+  for (int o = 1; o < P.m; o <<= 1) {
+    const float oh = __shfl_xor_sync(kAll, bh, o);
+    const float ol = __shfl_xor_sync(kAll, bl, o);
+    const int oa = __shfl_xor_sync(kAll, ba, o);
+    if (oh < bh || (oh == bh && (ol < bl || (ol == bl && oa < ba)))) {
+      bh = oh;
+      bl = ol;
+      ba = oa;
+    }
+  }
+  if (valid && a == 0) {
+    const int sl = lr / P.m;
+    b_hi[sl] = bh;
+    b_lo[sl] = bl;
+    b_arg[sl] = ba;
+  }
+}
 
-template <typename VT, int NT>
+template <int NT, typename VT>
 __device__ __forceinline__ void ring_fill(VT* ring, int mask, const VT* __restrict__ src,
                                           int64_t lo, int64_t hi) {
   for (int64_t i = lo + threadIdx.x; i < hi; i += NT) ring[i & mask] = src[i];
 }
 
-template <bool FF, typename IdxT, int VW, int NT>
+template <int NT>
+__device__ __forceinline__ void ring_fill_split(float* ring_hi, float* ring_lo, int mask,
+                                                const float2* __restrict__ src, int64_t lo,
+                                                int64_t hi) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
+    const float2 v = src[i];
+    ring_hi[i & mask] = v.x;
+    ring_lo[i & mask] = v.y;
+  }
+}
+
+// Shared memory: the ring (R float2 for the float-float pass; with SCREEN R
+// high parts, then R low parts, so that the screen reads 4-byte words; R
+// floats for FP32), then the tile: the Q tile q_hi[T*m] (and q_lo[T*m]) of
+// the full pass, or with SCREEN each state's winner b_hi[T], b_lo[T], b_arg[T].
+template <bool FF, typename IdxT, int VW, int NT, bool SCREEN>
 __global__ void __launch_bounds__(NT)
     k_bellman_win(Csr<IdxT> P, Grid G, int64_t band, int ring_log2, const void* __restrict__ Vin,
                   void* __restrict__ Vout, int32_t* __restrict__ pi_out,
                   float* __restrict__ r_out, double* __restrict__ partials,
                   DevState* __restrict__ st, int init_gmres) {
-  using VT = typename RingOf<FF>::T;
+  static_assert(!SCREEN || (FF && VW <= 4), "screening is a float-float fast-path form");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
   constexpr int NV = NT / VW;
   const int R = 1 << ring_log2;
   const int mask = R - 1;
-  VT* ring = reinterpret_cast<VT*>(smem_raw);
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  float* ring_lo = ring + R;                            // SCREEN only
+  float2* ring2 = reinterpret_cast<float2*>(smem_raw);  // FF without SCREEN
   const int lane = threadIdx.x % VW;
   const int vec = threadIdx.x / VW;
   const int m = P.m;
   const int T = G.tile_states;
   const int RT = T * m;
-  float* q_hi = reinterpret_cast<float*>(ring + R);
-  float* q_lo = q_hi + RT;
-  const VT* V = static_cast<const VT*>(Vin);
-  const typename RingOf<FF>::G gx{ring, mask};
+  float* q_hi = ring + (FF ? 2 * R : R);
+  float* q_lo = q_hi + (SCREEN ? T : RT);
+  int* b_arg = reinterpret_cast<int*>(q_lo + T);  // SCREEN only
+  using GX = typename std::conditional<FF, RingFF, RingF32>::type;
+  GX gx;
+  if constexpr (FF)
+    gx = RingFF{ring2, mask};
+  else
+    gx = RingF32{ring, mask};
   const bool vec4 = P.vec4 != 0;
   const bool fast = VW <= 4 && P.uniform_len == 4 * VW && vec4 && !P.val_lo;
 
   double my_max = 0.0, my_sq = 0.0;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  auto fill = [&](int64_t lo, int64_t hi) {
+    if constexpr (SCREEN)
+      ring_fill_split<NT>(ring, ring_lo, mask, static_cast<const float2*>(Vin), lo, hi);
+    else if constexpr (FF)
+      ring_fill<NT>(ring2, mask, static_cast<const float2*>(Vin), lo, hi);
+    else
+      ring_fill<NT>(ring, mask, static_cast<const float*>(Vin), lo, hi);
+  };
   if (t_begin < t_end) {
     const int64_t s_first = t_begin * T;
-    ring_fill<VT, NT>(ring, mask, V, max(int64_t(0), s_first - band), min(P.n, s_first + T + band));
+    fill(max(int64_t(0), s_first - band), min(P.n, s_first + T + band));
   }
   for (int64_t tile = t_begin; tile < t_end; ++tile) {
     const int64_t s0 = tile * T;
     const int64_t r0 = s0 * m;
-    __syncthreads();  // window of this tile complete; q tile free
-    if (tile + 1 < t_end)
-      ring_fill<VT, NT>(ring, mask, V, s0 + T + band, min(P.n, s0 + 2 * T + band));
+    __syncthreads();  // window of this tile complete; tile area free
+    if (tile + 1 < t_end) fill(s0 + T + band, min(P.n, s0 + 2 * T + band));
     const int64_t rows_here = min(static_cast<int64_t>(RT), (P.n - s0) * m);
-    if (fast) {
+    if constexpr (SCREEN) {
+      for (int base = 0; base < RT; base += NT)
+        bellman_pass_screened<VW>(P, ring, ring_lo, mask, r0, base + vec * VW, rows_here, lane,
+                                  q_hi, q_lo, b_arg);
+    } else if (fast) {
       if constexpr (VW <= 4) {
         for (int base = 0; base < RT; base += NT)
           bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, T, q_hi, q_lo);
@@ -488,20 +620,31 @@ __global__ void __launch_bounds__(NT)
     for (int t = threadIdx.x; t < T; t += NT) {
       const int64_t s = s0 + t;
       if (s < P.n) {
-        float bh = q_hi[t], bl = FF ? q_lo[t] : 0.f;
+        float bh, bl = 0.f;
         int arg = 0;
-        for (int a = 1; a < m; ++a) {
-          const float h = q_hi[a * T + t];
-          const float l = FF ? q_lo[a * T + t] : 0.f;
-          if (h < bh || (FF && h == bh && l < bl)) {
-            bh = h;
-            bl = l;
-            arg = a;
+        if constexpr (SCREEN) {
+          bh = q_hi[t];
+          bl = q_lo[t];
+          arg = b_arg[t];
+        } else {
+          bh = q_hi[t];
+          if (FF) bl = q_lo[t];
+          for (int a = 1; a < m; ++a) {
+            const float h = q_hi[a * T + t];
+            const float l = FF ? q_lo[a * T + t] : 0.f;
+            if (h < bh || (FF && h == bh && l < bl)) {
+              bh = h;
+              bl = l;
+              arg = a;
+            }
           }
         }
         float r;
-        if constexpr (FF) {
-          const float2 v = ring[s & mask];
+        if constexpr (SCREEN) {
+          r = ff_diff_to_float(bh, bl, ring[s & mask], ring_lo[s & mask]);
+          if (Vout) static_cast<float2*>(Vout)[s] = make_float2(bh, bl);
+        } else if constexpr (FF) {
+          const float2 v = ring2[s & mask];
           r = ff_diff_to_float(bh, bl, v.x, v.y);
           if (Vout) static_cast<float2*>(Vout)[s] = make_float2(bh, bl);
         } else {
@@ -680,14 +823,15 @@ int window_log2(int64_t band, int T, size_t entry_bytes, size_t budget) {
   return lg;
 }
 
-template <bool FF, typename IdxT, int VW, int NT>
+template <bool FF, typename IdxT, int VW, int NT, bool SCREEN>
 static cudaError_t bellman_win(const Mat& A, int lg, int T, const void* V, void* V_out,
                                int32_t* pi, float* r, double* partials, DevState* st,
                                int init_gmres, cudaStream_t s) {
   const size_t entry = FF ? sizeof(float2) : sizeof(float);
-  const size_t smem = (size_t(1) << lg) * entry + static_cast<size_t>(T) * A.m * sizeof(float) *
-                                                        (FF ? 2 : 1);
-  auto kern = k_bellman_win<FF, IdxT, VW, NT>;
+  const size_t tile = SCREEN ? static_cast<size_t>(T) * 12
+                             : static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);
+  const size_t smem = (size_t(1) << lg) * entry + tile;
+  auto kern = k_bellman_win<FF, IdxT, VW, NT, SCREEN>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess ||
@@ -701,18 +845,45 @@ static cudaError_t bellman_win(const Mat& A, int lg, int T, const void* V, void*
   return cudaGetLastError();
 }
 
+// The FP32 screen applies to float-float backups on the fast path (rows of
+// 4*VW aligned entries, FP32 probabilities) when a state's actions fit in
+// aligned lanes of one warp (m a power of two up to 32).
+static bool screened(const Mat& A, int VW) {
+  return A.screen && VW <= 4 && A.uniform_len == 4 * VW && A.vec4 && !A.val_lo && A.m <= 32 &&
+         (A.m & (A.m - 1)) == 0;
+}
+
+// Ring geometry of the windowed float-float backup: NT threads, T states a tile.
+static constexpr int kWinFFThreads = 1024;
+static int win_tile(int NT, int m) {
+  int T = 4 * NT / m;  // about 4*NT rows per tile
+  if (T < 1) T = 1;
+  if (T > NT) T = NT;
+  return T;
+}
+
+bool bellman_screened(const Mat& A) {
+  return A.window && A.vw <= 4 && screened(A, A.vw) &&
+         window_log2(A.band, win_tile(kWinFFThreads, A.m), 8, 128 * 1024) > 0;
+}
+
 template <bool FF, typename IdxT, int VW>
 static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t* pi, float* r,
                               double* partials, DevState* st, int init_gmres, cudaStream_t s) {
   if (A.window) {
     // 1024 threads per CTA for the float-float ring (one CTA per SM), 512 for FP32
-    constexpr int NT = FF ? 1024 : 512;
-    int T = 4 * NT / A.m;  // about 4*NT rows per tile
-    if (T < 1) T = 1;
-    if (T > NT) T = NT;
+    constexpr int NT = FF ? kWinFFThreads : 512;
+    const int T = win_tile(NT, A.m);
     const int lg = window_log2(A.band, T, FF ? 8 : 4, 128 * 1024);
-    if (lg > 0)
-      return bellman_win<FF, IdxT, VW, NT>(A, lg, T, V, V_out, pi, r, partials, st, init_gmres, s);
+    if (lg > 0) {
+      if constexpr (FF && VW <= 4) {
+        if (screened(A, VW))
+          return bellman_win<FF, IdxT, VW, NT, true>(A, lg, T, V, V_out, pi, r, partials, st,
+                                                     init_gmres, s);
+      }
+      return bellman_win<FF, IdxT, VW, NT, false>(A, lg, T, V, V_out, pi, r, partials, st,
+                                                  init_gmres, s);
+    }
   }
   const int T = bellman_tile_states(A.m);
   const size_t smem = static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);

@@ -36,10 +36,13 @@ struct Mat {
   int32_t vw = 4;           // lanes per row
   int64_t band = 0;         // max |col - s| (measured at create)
   int32_t window = 0;       // 1: banded kernels stage V in a shared-memory ring
+  int32_t screen = 0;       // 1: float-float backups screen actions in FP32 first
   double gamma = 0.0;
   int num_sms = 1;
 };
 
+// True when float-float backups of A take the FP32-screened windowed kernel.
+bool bellman_screened(const Mat& A);
 // K1 / K6: Bellman backup + greedy + residual.  ff selects float-float (V is
 // float2 hi/lo) versus FP32 (V is float).  init_gmres: the last block also
 // starts a GMRES cycle from r (target = eta*||r||_inf when st->target_rel).
