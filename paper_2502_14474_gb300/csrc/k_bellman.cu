@@ -24,13 +24,22 @@
 
 namespace mdpk {
 
+// Row stride of the action-major Q tile (q[a * stride + state]).  A warp of
+// the row passes writes the m actions of 32/m consecutive states at once; with
+// stride = 32/m (mod 32) their 32 words fall in 32 different banks (a stride
+// that is a multiple of 32 put the m actions of a state in one bank).
+__host__ __device__ __forceinline__ int qtile_stride(int T, int m) {
+  const int target = (32 % m == 0) ? (32 / m) & 31 : 1;
+  return T + (((target - T) % 32) + 32) % 32;
+}
+
 // Fast path of one pass over the rows of a tile when every row holds 4*VW
 // entries (16-byte aligned): the vector owns VW consecutive rows, each lane
 // loads its slice of all of them before any gather, and a reduce-scatter
 // leaves lane l with the sum of row lr0 + l, which it turns into Q(s, a).
 template <bool FF, int VW, typename IdxT, typename GX>
 __device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int64_t r0, int lr0,
-                                                  int64_t rows_here, int lane, int T,
+                                                  int64_t rows_here, int lane, int QS,
                                                   float* q_hi, float* q_lo) {
   int64_t b[VW];
   bool vd[VW];
@@ -58,10 +67,10 @@ __device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int
       const ff sum = ff_norm(hi, lo);
       const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
       const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
-      q_hi[a * T + sl] = q.hi;
-      q_lo[a * T + sl] = q.lo;
+      q_hi[a * QS + sl] = q.hi;
+      q_lo[a * QS + sl] = q.lo;
     } else {
-      q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+      q_hi[a * QS + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
     }
   }
 }
@@ -69,7 +78,7 @@ __device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int
 // One thread per row, two rows per thread in flight (short rows, VW == 1).
 template <bool FF, typename IdxT, typename GX>
 __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int64_t r0, int lr_a,
-                                                  int lr_b, int64_t rows_here, int T, float* q_hi,
+                                                  int lr_b, int64_t rows_here, int QS, float* q_hi,
                                                   float* q_lo) {
   int64_t b[2] = {0, 0}, e[2] = {0, 0};
   const int lr[2] = {lr_a, lr_b};
@@ -98,8 +107,8 @@ __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int
         const ff sum = ff_norm(hi[u], lo[u]);
         const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
         const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
-        q_hi[a * T + sl] = q.hi;
-        q_lo[a * T + sl] = q.lo;
+        q_hi[a * QS + sl] = q.hi;
+        q_lo[a * QS + sl] = q.lo;
       }
     }
   } else {
@@ -111,7 +120,7 @@ __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int
       if (lr[u] < rows_here) {
         const int a = lr[u] % P.m, sl = lr[u] / P.m;
         const float d = row_pre_dot<float>(P.col, P.val, gx, R[u]);
-        q_hi[a * T + sl] = fmaf(P.gamma, d, __ldcs(P.g + r0 + lr[u]));
+        q_hi[a * QS + sl] = fmaf(P.gamma, d, __ldcs(P.g + r0 + lr[u]));
       }
     }
   }
@@ -130,8 +139,9 @@ __global__ void __launch_bounds__(kThreads)
   const int m = P.m;
   const int T = G.tile_states;
   const int RT = T * m;
+  const int QS = qtile_stride(T, m);
   float* q_hi = smem;
-  float* q_lo = smem + RT;
+  float* q_lo = smem + m * QS;
   const float* Vf = static_cast<const float*>(Vin);
   const float2* Vff = static_cast<const float2*>(Vin);
   const bool vec4 = P.vec4 != 0;
@@ -148,10 +158,10 @@ __global__ void __launch_bounds__(kThreads)
       if constexpr (VW <= 4) {
         for (int base = 0; base < RT; base += kThreads) {
           if constexpr (FF)
-            bellman_pass_fast<FF, VW>(P, GatherFF{Vff}, r0, base + vec * VW, rows_here, lane, T,
+            bellman_pass_fast<FF, VW>(P, GatherFF{Vff}, r0, base + vec * VW, rows_here, lane, QS,
                                       q_hi, q_lo);
           else
-            bellman_pass_fast<FF, VW>(P, GatherF32{Vf}, r0, base + vec * VW, rows_here, lane, T,
+            bellman_pass_fast<FF, VW>(P, GatherF32{Vf}, r0, base + vec * VW, rows_here, lane, QS,
                                       q_hi, q_lo);
         }
       }
@@ -159,10 +169,10 @@ __global__ void __launch_bounds__(kThreads)
       for (int base = 0; base < RT; base += 2 * kThreads) {
         if constexpr (FF)
           bellman_pass_g1x2<FF>(P, GatherFF{Vff}, r0, base + threadIdx.x,
-                                base + kThreads + threadIdx.x, rows_here, T, q_hi, q_lo);
+                                base + kThreads + threadIdx.x, rows_here, QS, q_hi, q_lo);
         else
           bellman_pass_g1x2<FF>(P, GatherF32{Vf}, r0, base + threadIdx.x,
-                                base + kThreads + threadIdx.x, rows_here, T, q_hi, q_lo);
+                                base + kThreads + threadIdx.x, rows_here, QS, q_hi, q_lo);
       }
     } else
     for (int base = 0; base < RT; base += NV) {
@@ -185,10 +195,10 @@ __global__ void __launch_bounds__(kThreads)
           const ff sum = ff_norm(hi, lo);
           const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
           const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
-          q_hi[a * T + sl] = q.hi;
-          q_lo[a * T + sl] = q.lo;
+          q_hi[a * QS + sl] = q.hi;
+          q_lo[a * QS + sl] = q.lo;
         } else {
-          q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+          q_hi[a * QS + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
         }
       }
     }
@@ -199,8 +209,8 @@ __global__ void __launch_bounds__(kThreads)
         float bh = q_hi[t], bl = FF ? q_lo[t] : 0.f;
         int arg = 0;
         for (int a = 1; a < m; ++a) {
-          const float h = q_hi[a * T + t];
-          const float l = FF ? q_lo[a * T + t] : 0.f;
+          const float h = q_hi[a * QS + t];
+          const float l = FF ? q_lo[a * QS + t] : 0.f;
           if (h < bh || (FF && h == bh && l < bl)) {
             bh = h;
             bl = l;
@@ -542,8 +552,9 @@ __global__ void __launch_bounds__(NT)
   const int m = P.m;
   const int T = G.tile_states;
   const int RT = T * m;
+  const int QS = qtile_stride(T, m);
   float* q_hi = ring + (FF ? 2 * R : R);
-  float* q_lo = q_hi + (SCREEN ? T : RT);
+  float* q_lo = q_hi + (SCREEN ? T : m * QS);
   int* b_arg = reinterpret_cast<int*>(q_lo + T);  // SCREEN only
   using GX = typename std::conditional<FF, RingFF, RingF32>::type;
   GX gx;
@@ -582,12 +593,12 @@ __global__ void __launch_bounds__(NT)
     } else if (fast) {
       if constexpr (VW <= 4) {
         for (int base = 0; base < RT; base += NT)
-          bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, T, q_hi, q_lo);
+          bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, QS, q_hi, q_lo);
       }
     } else if (VW == 1) {
       for (int base = 0; base < RT; base += 2 * NT)
         bellman_pass_g1x2<FF>(P, gx, r0, base + threadIdx.x, base + NT + threadIdx.x, rows_here,
-                              T, q_hi, q_lo);
+                              QS, q_hi, q_lo);
     } else
     for (int base = 0; base < RT; base += NV) {
       const int lr = base + vec;
@@ -609,10 +620,10 @@ __global__ void __launch_bounds__(NT)
           const ff sum = ff_norm(hi, lo);
           const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
           const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
-          q_hi[a * T + sl] = q.hi;
-          q_lo[a * T + sl] = q.lo;
+          q_hi[a * QS + sl] = q.hi;
+          q_lo[a * QS + sl] = q.lo;
         } else {
-          q_hi[a * T + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
+          q_hi[a * QS + sl] = fmaf(P.gamma, hi, __ldcs(P.g + r));
         }
       }
     }
@@ -630,8 +641,8 @@ __global__ void __launch_bounds__(NT)
           bh = q_hi[t];
           if (FF) bl = q_lo[t];
           for (int a = 1; a < m; ++a) {
-            const float h = q_hi[a * T + t];
-            const float l = FF ? q_lo[a * T + t] : 0.f;
+            const float h = q_hi[a * QS + t];
+            const float l = FF ? q_lo[a * QS + t] : 0.f;
             if (h < bh || (FF && h == bh && l < bl)) {
               bh = h;
               bl = l;
@@ -829,7 +840,8 @@ static cudaError_t bellman_win(const Mat& A, int lg, int T, const void* V, void*
                                int init_gmres, cudaStream_t s) {
   const size_t entry = FF ? sizeof(float2) : sizeof(float);
   const size_t tile = SCREEN ? static_cast<size_t>(T) * 12
-                             : static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);
+                             : static_cast<size_t>(qtile_stride(T, A.m)) * A.m * sizeof(float) *
+                                   (FF ? 2 : 1);
   const size_t smem = (size_t(1) << lg) * entry + tile;
   auto kern = k_bellman_win<FF, IdxT, VW, NT, SCREEN>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -886,7 +898,8 @@ static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t*
     }
   }
   const int T = bellman_tile_states(A.m);
-  const size_t smem = static_cast<size_t>(T) * A.m * sizeof(float) * (FF ? 2 : 1);
+  const size_t smem =
+      static_cast<size_t>(qtile_stride(T, A.m)) * A.m * sizeof(float) * (FF ? 2 : 1);
   auto kern = k_bellman<FF, IdxT, VW>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

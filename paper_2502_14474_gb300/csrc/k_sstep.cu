@@ -290,8 +290,8 @@ __global__ void __launch_bounds__(kBlkThreads)
 constexpr int kGramCW = 8;                          // consumer warps
 constexpr int kGramTh = 32 * (kGramCW + 1);         // + the producer warp
 constexpr int kGramStage = 512;                     // states per stage
-constexpr int kGramMaxStages = 8;
-constexpr size_t kGramSmemBudget = 200 * 1024;      // stage buffers
+constexpr int kGramMaxStages = 16;
+constexpr size_t kGramSmemBudget = 208 * 1024;      // stage buffers
 constexpr int kGramErrTimeout = 1;                  // dev_error code of a wait that gave up
 // vectors per consumer warp and per group.  A thread holds 2 * VPW * S FP32
 // sums and as many float-float parts; with nine warps per SM (three on one of
@@ -639,7 +639,9 @@ cudaError_t block_gram_launch(const Mat& A, const float* basis, int64_t ld, int 
   per = (per + kGramStage - 1) / kGramStage * kGramStage;
   const int64_t used = (A.n + per - 1) / per;  // <= slots
   const int per_g = (nv + vg - 1) / vg;
-  const size_t stage_bytes = static_cast<size_t>(per_g + sb) * kGramStage * sizeof(float);
+  // copies per stage: the group's vectors, and W's when the group does not hold them
+  const int ncp_max = vg == 1 ? nv : per_g + sb;
+  const size_t stage_bytes = static_cast<size_t>(ncp_max) * kGramStage * sizeof(float);
   int nstages = static_cast<int>(kGramSmemBudget / stage_bytes);
   if (nstages > kGramMaxStages) nstages = kGramMaxStages;
   size_t smem = static_cast<size_t>(nstages) * stage_bytes;
