@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kBlkThreads)
 
 // ---------------------------------------------------------------------------
 // Gram pass, bulk-copy form (the default): one CTA per SM owns a contiguous
-// slot of states and walks it in stages of kGramStage states.  A producer warp
+// slot of states and walks it in stages of `stg` states.  A producer warp
 // copies each stage of every vector of the CTA's group (and of W, when the
 // group does not hold it) from HBM into shared memory with cp.async.bulk,
 // completing on the stage's mbarrier; the copies of up to `nstages` stages are
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBlkThreads)
 // ---------------------------------------------------------------------------
 constexpr int kGramCW = 8;                          // consumer warps
 constexpr int kGramTh = 32 * (kGramCW + 1);         // + the producer warp
-constexpr int kGramStage = 512;                     // states per stage
+constexpr int kGramStageMax = 2048;                 // states per stage, at most
 constexpr int kGramMaxStages = 16;
 constexpr size_t kGramSmemBudget = 208 * 1024;      // stage buffers
 constexpr int kGramErrTimeout = 1;                  // dev_error code of a wait that gave up
@@ -302,8 +302,8 @@ constexpr int gram_vpg(int S) { return kGramCW * gram_vpw(S); }
 template <int S>
 __global__ void __launch_bounds__(kGramTh, 1)
     k_block_gram(int64_t n, int64_t states_per_slot, const float* __restrict__ basis, int64_t ld,
-                 int k, int sb, int restart, int nstages, double* __restrict__ partials,
-                 DevState* __restrict__ st) {
+                 int k, int sb, int restart, int nstages, int stg,
+                 double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int NW = kGramCW, VPW = gram_vpw(S);
   extern __shared__ __align__(128) unsigned char gram_stage_dyn[];
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kGramTh, 1)
   const int ncp = ng + (w_in ? 0 : sb);
   const int64_t s_begin = slot * states_per_slot;
   const int64_t s_end = min(n, s_begin + states_per_slot);
-  const int64_t nch = s_end > s_begin ? (s_end - s_begin + kGramStage - 1) / kGramStage : 0;
+  const int64_t nch = s_end > s_begin ? (s_end - s_begin + stg - 1) / stg : 0;
   if (t == 0) {
     s_abort = 0;
     for (int b = 0; b < nstages; ++b) {
@@ -354,18 +354,18 @@ __global__ void __launch_bounds__(kGramTh, 1)
         s_abort = 1;
         break;
       }
-      const int64_t c0 = s_begin + c * kGramStage;
+      const int64_t c0 = s_begin + c * stg;
       const int64_t left = s_end - c0;
       // a short last stage rounds up to 16 bytes: the column's padding (ld >=
       // n rounded up to 64) or the next slot's states, masked by the consumers
-      const unsigned bytes = left >= kGramStage ? kGramStage * 4u
+      const unsigned bytes = left >= stg ? static_cast<unsigned>(stg) * 4u
                                                 : static_cast<unsigned>((left * 4 + 15) & ~15);
       if (lane == 0) mbar_arrive_expect_tx(&full[b], bytes * static_cast<unsigned>(ncp));
       __syncwarp();
-      float* dst = stages + static_cast<size_t>(b) * ncp * kGramStage;
+      float* dst = stages + static_cast<size_t>(b) * ncp * stg;
       for (int q = lane; q < ncp; q += 32) {
         const int v = q < ng ? g0 + q : k + 1 + (q - ng);
-        bulk_g2s(dst + static_cast<size_t>(q) * kGramStage, basis + v * ld + c0, bytes, &full[b]);
+        bulk_g2s(dst + static_cast<size_t>(q) * stg, basis + v * ld + c0, bytes, &full[b]);
       }
       issued = c + 1;
     }
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kGramTh, 1)
     };
     // one 128-state tile of a stage; MASKED: the stage ends inside the slot
     // and its entries from `left` on are zero
-    auto tile = [&](const float* stg, int tl, int64_t left, auto masked) {
+    auto tile = [&](const float* sp, int tl, int64_t left, auto masked) {
       constexpr bool MASKED = decltype(masked)::value;
       const int e = tl * 128 + 4 * lane;
       int lim = 4;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kGramTh, 1)
       float2 wa[S], wb[S];
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        const float4 w = i < sb ? ld4(stg + (w_off + i) * kGramStage + e)
+        const float4 w = i < sb ? ld4(sp + (w_off + i) * stg + e)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
         wa[i] = make_float2(w.x, w.y);
         wb[i] = make_float2(w.z, w.w);
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kGramTh, 1)
 #pragma unroll
       for (int u = 0; u < VPW; ++u) {
         if (vok[u]) {
-          const float4 x = ld4(stg + vloc[u] * kGramStage + e);
+          const float4 x = ld4(sp + vloc[u] * stg + e);
           const float2 xa = make_float2(x.x, x.y), xb = make_float2(x.z, x.w);
 #pragma unroll
           for (int i = 0; i < S; ++i)
@@ -440,26 +440,34 @@ __global__ void __launch_bounds__(kGramTh, 1)
         s_abort = 1;
         break;
       }
-      const float* stg = stages + static_cast<size_t>(b) * ncp * kGramStage;
-      const int64_t left = s_end - (s_begin + c * kGramStage);
-      if (left >= kGramStage) {
+      const float* sp = stages + static_cast<size_t>(b) * ncp * stg;
+      const int64_t left = s_end - (s_begin + c * stg);
+      if (left >= stg) {
+        // whole stage: groups of four tiles unrolled, so that a tile's loads
+        // overlap the previous tile's products
+        for (int tg = 0; tg < stg / 512; ++tg) {
 #pragma unroll
-        for (int tl = 0; tl < kGramStage / 128; ++tl)
-          tile(stg, tl, left, std::integral_constant<bool, false>{});
+          for (int q = 0; q < 4; ++q) tile(sp, 4 * tg + q, left, std::integral_constant<bool, false>{});
+          ftiles += 4;
+          if (ftiles == 8) {  // 16 products in each of the paired FP32 sums
+            ftiles = 0;
+            fold();
+          }
+        }
       } else {
-#pragma unroll
-        for (int tl = 0; tl < kGramStage / 128; ++tl)
-          tile(stg, tl, left, std::integral_constant<bool, true>{});
+        const int ntl = static_cast<int>((left + 127) / 128);
+        for (int tl = 0; tl < ntl; ++tl) {
+          tile(sp, tl, left, std::integral_constant<bool, true>{});
+          if (++ftiles == 8) {
+            ftiles = 0;
+            fold();
+          }
+        }
       }
       // this warp no longer reads the stage (__syncwarp orders the lanes'
       // reads before lane 0's release)
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      ftiles += kGramStage / 128;
-      if (ftiles >= 8) {
-        ftiles = 0;
-        fold();
-      }
     }
     fold();
     // warp sums (float-float) and the slot's partials
@@ -635,13 +643,18 @@ cudaError_t block_gram_launch(const Mat& A, const float* basis, int64_t ld, int 
   const int64_t cap = block_slots(A.num_sms, A.n);
   if (slots > cap) slots = cap;
   if (slots < 1) slots = 1;
-  int64_t per = (A.n + slots - 1) / slots;
-  per = (per + kGramStage - 1) / kGramStage * kGramStage;
-  const int64_t used = (A.n + per - 1) / per;  // <= slots
   const int per_g = (nv + vg - 1) / vg;
   // copies per stage: the group's vectors, and W's when the group does not hold them
   const int ncp_max = vg == 1 ? nv : per_g + sb;
-  const size_t stage_bytes = static_cast<size_t>(ncp_max) * kGramStage * sizeof(float);
+  // the largest stage (a multiple of 512 states) of which two fit: a bulk copy
+  // costs about the same however long it is, so long copies stream faster
+  int stg = static_cast<int>(kGramSmemBudget / (2 * sizeof(float) * ncp_max)) / 512 * 512;
+  if (stg > kGramStageMax) stg = kGramStageMax;
+  if (stg < 512) stg = 512;
+  int64_t per = (A.n + slots - 1) / slots;
+  per = (per + stg - 1) / stg * stg;
+  const int64_t used = (A.n + per - 1) / per;  // <= slots
+  const size_t stage_bytes = static_cast<size_t>(ncp_max) * stg * sizeof(float);
   int nstages = static_cast<int>(kGramSmemBudget / stage_bytes);
   if (nstages > kGramMaxStages) nstages = kGramMaxStages;
   size_t smem = static_cast<size_t>(nstages) * stage_bytes;
@@ -654,7 +667,7 @@ cudaError_t block_gram_launch(const Mat& A, const float* basis, int64_t ld, int 
   }();
   (void)attr;
   k_block_gram<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kGramTh, smem,
-                    s>>>(A.n, per, basis, ld, k, sb, restart, nstages, partials, st);
+                    s>>>(A.n, per, basis, ld, k, sb, restart, nstages, stg, partials, st);
   return cudaGetLastError();
 }
 
