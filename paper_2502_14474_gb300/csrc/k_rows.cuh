@@ -448,6 +448,23 @@ __device__ __forceinline__ void vec_rows_f32(const int32_t* __restrict__ col,
                                                                  q[u].x * x(c[u].x))));
 }
 
+// ff_acc on two independent sums at once with the packed FP32x2 instructions:
+// each lane of the pair goes through exactly the operations of ff_acc, so the
+// results are bitwise those of two scalar calls.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void ff_acc2(float2& s_hi, float2& s_lo, float2 p, float2 vhi,
+                                        float2 vlo) {
+  const float2 ph = __fmul2_rn(p, vhi);
+  float2 pl = __ffma2_rn(p, vhi, neg2(ph));
+  pl = __ffma2_rn(p, vlo, pl);
+  const float2 t = __fadd2_rn(s_hi, ph);
+  const float2 bb = __fadd2_rn(t, neg2(s_hi));
+  const float2 e = __fadd2_rn(__fadd2_rn(s_hi, neg2(__fadd2_rn(t, neg2(bb)))),
+                              __fadd2_rn(ph, neg2(bb)));
+  s_hi = t;
+  s_lo = __fadd2_rn(s_lo, __fadd2_rn(e, pl));
+}
+
 template <int VW, typename GX>
 __device__ __forceinline__ void vec_rows_ff(const int32_t* __restrict__ col,
                                             const float* __restrict__ val, GX V,
@@ -465,16 +482,39 @@ __device__ __forceinline__ void vec_rows_ff(const int32_t* __restrict__ col,
       q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  if constexpr (VW % 2 == 0) {
+    // rows u and u + 1 side by side in the packed instructions
 #pragma unroll
-  for (int u = 0; u < VW; ++u) {
-    float h = 0.f, l = 0.f;
-    const float2 v0 = V(c[u].x), v1 = V(c[u].y), v2 = V(c[u].z), v3 = V(c[u].w);
-    ff_acc(h, l, q[u].x, v0.x, v0.y);
-    ff_acc(h, l, q[u].y, v1.x, v1.y);
-    ff_acc(h, l, q[u].z, v2.x, v2.y);
-    ff_acc(h, l, q[u].w, v3.x, v3.y);
-    ph[u] = h;
-    pl[u] = l;
+    for (int u = 0; u < VW; u += 2) {
+      float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+      const float2 a0 = V(c[u].x), a1 = V(c[u].y), a2 = V(c[u].z), a3 = V(c[u].w);
+      const float2 b0 = V(c[u + 1].x), b1 = V(c[u + 1].y), b2 = V(c[u + 1].z),
+                   b3 = V(c[u + 1].w);
+      ff_acc2(h, l, make_float2(q[u].x, q[u + 1].x), make_float2(a0.x, b0.x),
+              make_float2(a0.y, b0.y));
+      ff_acc2(h, l, make_float2(q[u].y, q[u + 1].y), make_float2(a1.x, b1.x),
+              make_float2(a1.y, b1.y));
+      ff_acc2(h, l, make_float2(q[u].z, q[u + 1].z), make_float2(a2.x, b2.x),
+              make_float2(a2.y, b2.y));
+      ff_acc2(h, l, make_float2(q[u].w, q[u + 1].w), make_float2(a3.x, b3.x),
+              make_float2(a3.y, b3.y));
+      ph[u] = h.x;
+      pl[u] = l.x;
+      ph[u + 1] = h.y;
+      pl[u + 1] = l.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+      float h = 0.f, l = 0.f;
+      const float2 v0 = V(c[u].x), v1 = V(c[u].y), v2 = V(c[u].z), v3 = V(c[u].w);
+      ff_acc(h, l, q[u].x, v0.x, v0.y);
+      ff_acc(h, l, q[u].y, v1.x, v1.y);
+      ff_acc(h, l, q[u].z, v2.x, v2.y);
+      ff_acc(h, l, q[u].w, v3.x, v3.y);
+      ph[u] = h;
+      pl[u] = l;
+    }
   }
 }
 
