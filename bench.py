@@ -49,6 +49,10 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--profile-bellman", type=int, default=0,
                    help="only run N float-float Bellman backups (for ncu captures)")
+    p.add_argument("--fp-rates", action="store_true",
+                   help="time dense FP64 and FP32 (no TF32) matrix products through torch "
+                        "(cuBLAS) and print the achieved rates: the measured basis for doing "
+                        "the high-precision arithmetic in float-float on the FP32 pipes")
     p.add_argument("--profile-solve", action="store_true",
                    help="one solve, nothing else (for ncu launch lists)")
     p.add_argument("--no-profile", action="store_true",
@@ -527,10 +531,39 @@ def run_serve(args):
     return 0
 
 
+def run_fp_rates():
+    """Achieved dense FP64 and FP32 (CUDA-core) FMA rates of this GPU, from cuBLAS
+    GEMMs of 8192^3 (2 N^3 flops each), best of 5 after 2 warm-ups, CUDA events."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        n = 8192
+        a = torch.rand(n, n, dtype=dt, device="cuda")
+        b = torch.rand(n, n, dtype=dt, device="cuda")
+        best = None
+        for it in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.mm(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if it >= 2:
+                best = ms if best is None else min(best, ms)
+        out[name + "_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        del a, b
+    out["fp32_over_fp64"] = out["fp32_tflops"] / out["fp64_tflops"]
+    print(json.dumps({"fp_rates": out, "how": "torch.mm 8192^3, TF32 off, best of 5"}))
+    return 0
+
+
 def main():
     global WORKLOAD
     args = _args()
     WORKLOAD = args.workload
+    if args.fp_rates:
+        return run_fp_rates()
     if args.max_inner is None:
         args.max_inner = 100 if args.workload == "grid4096" else 10000
     if args.workload == "batch512":
@@ -587,26 +620,31 @@ def main():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        # an event between consecutive solves as well: the per-solve times give
+        # the median and spread of the step (events cost nothing inside a solve)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
         out = []
-        for _ in range(args.steps):
+        for i in range(args.steps):
             V_last, pi_last, st_ = h.solve(**opts)
             out.append(st_)
             last[:] = [V_last, pi_last]
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        elapsed = e0.elapsed_time(e1)
+        elapsed = ev[0].elapsed_time(ev[-1])
+        step_ms[:] = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
         prof_ = h.profile_read()
         h.profile(False)
         return elapsed, out, prof_
 
     last = []
+    step_ms = []
     sampler.start()
     time.sleep(0.3)
     ms, stats, prof_plain = timed(False)
+    steps_plain = list(step_ms)
     V_res = last[0].cpu().numpy()
     pi_res = last[1].cpu().numpy()
     clocks = sampler.stop()
@@ -697,7 +735,11 @@ def main():
         st0 = stats[-1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "step_ms": {"each": [round(x, 3) for x in steps_plain],
+                        "median": statistics.median(steps_plain),
+                        "min": min(steps_plain), "max": max(steps_plain)},
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": host.name, "n_states": host.n, "m": host.m, "nnz": nnz,
                        "gamma": host.gamma, "seed": 2 if args.workload == "banded4m" else 3,

@@ -445,11 +445,20 @@ __global__ void __launch_bounds__(kGramTh, 1)
       if (left >= stg) {
         // whole stage: groups of four tiles unrolled, so that a tile's loads
         // overlap the previous tile's products
-        for (int tg = 0; tg < stg / 512; ++tg) {
+        const int ntl = stg / 128;
+        int tl = 0;
+        for (; tl + 4 <= ntl; tl += 4) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) tile(sp, 4 * tg + q, left, std::integral_constant<bool, false>{});
+          for (int q = 0; q < 4; ++q) tile(sp, tl + q, left, std::integral_constant<bool, false>{});
           ftiles += 4;
-          if (ftiles == 8) {  // 16 products in each of the paired FP32 sums
+          if (ftiles >= 8) {  // 16 products in each of the paired FP32 sums
+            ftiles = 0;
+            fold();
+          }
+        }
+        for (; tl < ntl; ++tl) {
+          tile(sp, tl, left, std::integral_constant<bool, false>{});
+          if (++ftiles >= 8) {
             ftiles = 0;
             fold();
           }
@@ -458,7 +467,7 @@ __global__ void __launch_bounds__(kGramTh, 1)
         const int ntl = static_cast<int>((left + 127) / 128);
         for (int tl = 0; tl < ntl; ++tl) {
           tile(sp, tl, left, std::integral_constant<bool, true>{});
-          if (++ftiles == 8) {
+          if (++ftiles >= 8) {
             ftiles = 0;
             fold();
           }
