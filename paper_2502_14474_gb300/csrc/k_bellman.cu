@@ -528,6 +528,12 @@ __device__ __forceinline__ void ring_fill_split(float* ring_hi, float* ring_lo, 
   }
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16) from global memory into L2.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+constexpr int kPrefetchPasses = 2;
+
 // Shared memory: the ring (R float2 for the float-float pass; with SCREEN R
 // high parts, then R low parts, so that the screen reads 4-byte words; R
 // floats for FP32), then the tile: the Q tile q_hi[T*m] (and q_lo[T*m]) of
@@ -568,6 +574,7 @@ __global__ void __launch_bounds__(NT)
   double my_max = 0.0, my_sq = 0.0;
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  const int64_t row_end = min(t_end * T, P.n) * m;  // end of this CTA's rows
   auto fill = [&](int64_t lo, int64_t hi) {
     if constexpr (SCREEN)
       ring_fill_split<NT>(ring, ring_lo, mask, static_cast<const float2*>(Vin), lo, hi);
@@ -592,8 +599,19 @@ __global__ void __launch_bounds__(NT)
                                   q_hi, q_lo, b_arg);
     } else if (fast) {
       if constexpr (VW <= 4) {
-        for (int base = 0; base < RT; base += NT)
+        for (int base = 0; base < RT; base += NT) {
+          // the CTA's rows are one contiguous run of the packed array (a row
+          // of 4*VW entries is VW groups of 32 bytes): ask L2 for the rows
+          // kPrefetchPasses passes ahead with one bulk prefetch, so that the
+          // row loads of those passes find their lines in L2
+          if (threadIdx.x == 0) {
+            const int64_t pr = r0 + base + kPrefetchPasses * NT;
+            const int64_t pe = min(row_end, pr + NT);
+            if (pr < pe)
+              prefetch_l2_bulk(P.col + pr * 8 * VW, static_cast<unsigned>((pe - pr) * 32 * VW));
+          }
           bellman_pass_fast<FF, VW>(P, gx, r0, base + vec * VW, rows_here, lane, QS, q_hi, q_lo);
+        }
       }
     } else if (VW == 1) {
       for (int base = 0; base < RT; base += 2 * NT)
