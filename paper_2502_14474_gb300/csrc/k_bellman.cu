@@ -533,13 +533,18 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 constexpr int kPrefetchPasses = 2;
+// Entries [e0, e1) of the packed array (32-byte groups of 4 entries) into L2.
+__device__ __forceinline__ void prefetch_entries_l2(const int32_t* pk, int64_t e0, int64_t e1) {
+  const int64_t g0 = e0 >> 2, g1 = (e1 + 3) >> 2;
+  prefetch_l2_bulk(pk + g0 * 8, static_cast<unsigned>((g1 - g0) * 32));
+}
 
 // Shared memory: the ring (R float2 for the float-float pass; with SCREEN R
 // high parts, then R low parts, so that the screen reads 4-byte words; R
 // floats for FP32), then the tile: the Q tile q_hi[T*m] (and q_lo[T*m]) of
 // the full pass, or with SCREEN each state's winner b_hi[T], b_lo[T], b_arg[T].
 template <bool FF, typename IdxT, int VW, int NT, bool SCREEN>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, FF ? 1 : 2)
     k_bellman_win(Csr<IdxT> P, Grid G, int64_t band, int ring_log2, const void* __restrict__ Vin,
                   void* __restrict__ Vout, int32_t* __restrict__ pi_out,
                   float* __restrict__ r_out, double* __restrict__ partials,
@@ -575,6 +580,7 @@ __global__ void __launch_bounds__(NT)
   const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
   const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
   const int64_t row_end = min(t_end * T, P.n) * m;  // end of this CTA's rows
+  int64_t pf_e0 = 0, pf_e1 = 0;                      // thread 0: entries to prefetch next
   auto fill = [&](int64_t lo, int64_t hi) {
     if constexpr (SCREEN)
       ring_fill_split<NT>(ring, ring_lo, mask, static_cast<const float2*>(Vin), lo, hi);
@@ -614,9 +620,24 @@ __global__ void __launch_bounds__(NT)
         }
       }
     } else if (VW == 1) {
-      for (int base = 0; base < RT; base += 2 * NT)
+      for (int base = 0; base < RT; base += 2 * NT) {
+        // rows of other lengths: thread 0 reads the entry bounds of the rows
+        // kPrefetchPasses + 1 passes ahead during this pass (the loads overlap
+        // it) and prefetches them into L2 at the start of the next
+        if (threadIdx.x == 0) {
+          if (pf_e1 > pf_e0) prefetch_entries_l2(P.col, pf_e0, pf_e1);
+          const int64_t ra = r0 + base + (kPrefetchPasses + 1) * 2 * NT;
+          const int64_t rb = min(row_end, ra + 2 * NT);
+          pf_e0 = pf_e1 = 0;
+          if (ra < rb) {
+            int64_t e_dummy;
+            row_bounds<IdxT>(P.rp, P.uniform_len, ra, pf_e0, e_dummy);
+            row_bounds<IdxT>(P.rp, P.uniform_len, rb - 1, e_dummy, pf_e1);
+          }
+        }
         bellman_pass_g1x2<FF>(P, gx, r0, base + threadIdx.x, base + NT + threadIdx.x, rows_here,
                               QS, q_hi, q_lo);
+      }
     } else
     for (int base = 0; base < RT; base += NV) {
       const int lr = base + vec;
