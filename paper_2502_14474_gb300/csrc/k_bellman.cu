@@ -75,8 +75,68 @@ __device__ __forceinline__ void bellman_pass_fast(const Csr<IdxT>& P, GX gx, int
   }
 }
 
+// The float-float sums of a thread's two short rows side by side in the packed
+// FP32x2 instructions (ff_acc2).  Both rows walk the eight slots of their first
+// two packed groups; a slot outside a row adds p = 0 times x = 0, which leaves
+// the row's sum unchanged (TwoSum of s and +0 is s and 0), so each sum equals
+// that of row_pre_dot_ff up to the sign of an exactly zero sum.  The slots of
+// rows longer than two groups follow one row at a time, as there.
+template <typename GX>
+__device__ __forceinline__ void row_pre_dot_ff2(const int32_t* __restrict__ col,
+                                                const float* __restrict__ val, GX V,
+                                                const RowPre<float> (&R)[2], float (&hi)[2],
+                                                float (&lo)[2]) {
+  int o[2], end[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    o[u] = static_cast<int>(R[u].b & 3);
+    end[u] = o[u] + static_cast<int>(R[u].e - R[u].b);
+  }
+  const int ca[8] = {R[0].c0.x, R[0].c0.y, R[0].c0.z, R[0].c0.w,
+                     R[0].c1.x, R[0].c1.y, R[0].c1.z, R[0].c1.w};
+  const int cb[8] = {R[1].c0.x, R[1].c0.y, R[1].c0.z, R[1].c0.w,
+                     R[1].c1.x, R[1].c1.y, R[1].c1.z, R[1].c1.w};
+  const float pa[8] = {R[0].v0.x, R[0].v0.y, R[0].v0.z, R[0].v0.w,
+                       R[0].v1.x, R[0].v1.y, R[0].v1.z, R[0].v1.w};
+  const float pb[8] = {R[1].v0.x, R[1].v0.y, R[1].v0.z, R[1].v0.w,
+                       R[1].v1.x, R[1].v1.y, R[1].v1.z, R[1].v1.w};
+  float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const bool va = q >= o[0] && q < end[0], vb = q >= o[1] && q < end[1];
+    const float2 xa = V(ca[q]), xb = V(cb[q]);
+    ff_acc2(h, l, make_float2(va ? pa[q] : 0.f, vb ? pb[q] : 0.f),
+            make_float2(va ? xa.x : 0.f, vb ? xb.x : 0.f),
+            make_float2(va ? xa.y : 0.f, vb ? xb.y : 0.f));
+  }
+  hi[0] = h.x;
+  lo[0] = l.x;
+  hi[1] = h.y;
+  lo[1] = l.y;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int64_t e = R[u].e;
+    for (int64_t g = (R[u].b >> 2) + 2; (g << 2) < e; ++g) {
+      const int64_t j0 = g << 2;
+      const int4 c = ldcol4(col, j0);
+      const float4 p = Ld<float>::four(val, j0);
+      const int cq[4] = {c.x, c.y, c.z, c.w};
+      const float pq[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (j0 + q < e) {
+          const float2 v = V(cq[q]);
+          ff_acc(hi[u], lo[u], pq[q], v.x, v.y);
+        }
+      }
+    }
+  }
+}
+
 // One thread per row, two rows per thread in flight (short rows, VW == 1).
-template <bool FF, typename IdxT, typename GX>
+// PACKED: the float-float sums of the two rows in packed instructions
+// (row_pre_dot_ff2; more registers, so only where the CTA has them).
+template <bool FF, typename IdxT, typename GX, bool PACKED = false>
 __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int64_t r0, int lr_a,
                                                   int lr_b, int64_t rows_here, int QS, float* q_hi,
                                                   float* q_lo) {
@@ -92,8 +152,12 @@ __device__ __forceinline__ void bellman_pass_g1x2(const Csr<IdxT>& P, GX gx, int
       RowPre<float> R[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) row_pre<float>(P.col, P.val, b[u], e[u], R[u]);
+      if constexpr (PACKED) {
+        row_pre_dot_ff2(P.col, P.val, gx, R, hi, lo);
+      } else {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) row_pre_dot_ff(P.col, P.val, gx, R[u], hi[u], lo[u]);
+        for (int u = 0; u < 2; ++u) row_pre_dot_ff(P.col, P.val, gx, R[u], hi[u], lo[u]);
+      }
     } else {
 #pragma unroll
       for (int u = 0; u < 2; ++u)
@@ -635,8 +699,9 @@ __global__ void __launch_bounds__(NT, FF ? 1 : 2)
             row_bounds<IdxT>(P.rp, P.uniform_len, rb - 1, e_dummy, pf_e1);
           }
         }
-        bellman_pass_g1x2<FF>(P, gx, r0, base + threadIdx.x, base + NT + threadIdx.x, rows_here,
-                              QS, q_hi, q_lo);
+        bellman_pass_g1x2<FF, IdxT, decltype(gx), true>(P, gx, r0, base + threadIdx.x,
+                                                         base + NT + threadIdx.x, rows_here, QS,
+                                                         q_hi, q_lo);
       }
     } else
     for (int base = 0; base < RT; base += NV) {
