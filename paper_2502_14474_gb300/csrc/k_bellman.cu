@@ -802,6 +802,95 @@ __global__ void __launch_bounds__(NT, FF ? 1 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Policy residual with the value window in shared memory (banded matrices):
+// the ring of k_bellman_win, a CTA walking contiguous tiles of NT states with
+// one state per thread, for rows of 4*VW aligned entries in the vector form of
+// k_policy_residual_fast (VW states per vector, a reduce-scatter).  The
+// float-float row sums are those of the global kernel (same entries, same
+// order, same operations).  (Short rows stay on the global kernel: there the
+// action-major copy already makes neighbouring gathers hit L1/L2, and a window
+// version measured slower, 0.528 against 0.478 ms on the 4096^2 grid.)
+// ---------------------------------------------------------------------------
+template <typename IdxT, int VW, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_policy_residual_win(Csr<IdxT> P, Grid G, int64_t band, int ring_log2,
+                          const int32_t* __restrict__ pi, const float2* __restrict__ V,
+                          float* __restrict__ r_out, double* __restrict__ partials,
+                          DevState* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  const int R = 1 << ring_log2;
+  const int mask = R - 1;
+  float2* ring = reinterpret_cast<float2*>(smem_raw);
+  const RingFF gx{ring, mask};
+  const int T = G.tile_states;  // == NT
+  static_assert(VW <= 4, "rows of 4*VW aligned entries");
+  const int lane = threadIdx.x % VW;
+  double my_max = 0.0, my_sq = 0.0;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * G.tiles_per_block;
+  const int64_t t_end = min(G.n_tiles, t_begin + G.tiles_per_block);
+  if (t_begin < t_end) {
+    const int64_t s_first = t_begin * T;
+    ring_fill<NT>(ring, mask, V, max(int64_t(0), s_first - band), min(P.n, s_first + T + band));
+  }
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t s0 = tile * T;
+    __syncthreads();  // window of this tile complete
+    if (tile + 1 < t_end) ring_fill<NT>(ring, mask, V, s0 + T + band, min(P.n, s0 + 2 * T + band));
+    const int64_t s = s0 + threadIdx.x;
+    const bool valid = s < P.n;
+    const int32_t a = valid ? __ldg(pi + s) : 0;
+    float hi, lo;
+    {
+      const int64_t rb = policy_row(P, s, a) * P.uniform_len;
+      int64_t b[VW];
+      bool vd[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        b[u] = __shfl_sync(0xffffffffu, rb, u, VW);
+        vd[u] = __shfl_sync(0xffffffffu, valid ? 1 : 0, u, VW) != 0;
+      }
+      float ph[VW], pl[VW];
+      vec_rows_ff<VW>(P.col, P.val, gx, b, vd, lane, ph, pl);
+      reduce_scatter_ff<VW>(ph, pl, lane, hi, lo);
+    }
+    if (valid) {
+      const int64_t r = s * P.m + a;  // cost row
+      const ff sum = ff_norm(hi, lo);
+      const ff gq = ff_norm(__ldcs(P.g + r), P.g_lo ? __ldcs(P.g_lo + r) : 0.f);
+      const ff q = ff_add(ff_mul(sum, ff{P.gamma_hi, P.gamma_lo}), gq);
+      const float2 v = ring[s & mask];
+      const float rr = ff_diff_to_float(q.hi, q.lo, v.x, v.y);
+      r_out[s] = rr;
+      const double rd = static_cast<double>(rr);
+      my_max = fmax(my_max, fabs(rd));
+      my_sq += rd * rd;
+    }
+  }
+  const double bmax = block_max_nt<NT>(my_max, red);
+  const double bsq = block_sum_nt<NT>(my_sq, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bmax;
+    partials[2 * blockIdx.x + 1] = bsq;
+  }
+  if (last_block(&st->counter[kCntPolicy])) {
+    double mx = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += NT) {
+      mx = fmax(mx, __ldcg(partials + 2 * i));
+      sq += __ldcg(partials + 2 * i + 1);
+    }
+    mx = block_max_nt<NT>(mx, red);
+    sq = block_sum_nt<NT>(sq, red);
+    if (threadIdx.x == 0) {
+      st->res_inf = mx;
+      st->res_2 = sqrt(sq);
+      st->counter[kCntPolicy] = 0;
+      gmres_begin(st, sqrt(sq));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // BiCGStab (van der Vorst 1992) on (I - gamma P_pi) d = r: the policy SpMV
 // y = x - gamma P_pi x over the FP32 probabilities (row s*m + pi(s) read from
 // the CSR, or from the action-major copy), with <y, w> and <y, y> reduced in a
@@ -1044,6 +1133,26 @@ cudaError_t launch_bellman(const Mat& A, bool ff, const void* V, void* V_out, in
 template <typename IdxT, int VW>
 static cudaError_t presid_vw(const Mat& A, const int32_t* pi, const float2* V, float* r,
                              double* partials, DevState* st, cudaStream_t s) {
+  if constexpr (VW <= 4) {
+    // banded rows of 4*VW aligned entries: the window of V in shared memory
+    const bool fast_rows = A.uniform_len == 4 * VW && A.vec4 && !A.val_lo && A.am_len == 0;
+    if (A.window && fast_rows) {
+      constexpr int NT = 1024;
+      const int lg = window_log2(A.band, NT, 8, 128 * 1024);
+      if (lg > 0) {
+        auto kern = k_policy_residual_win<IdxT, VW, NT>;
+        const size_t smem = (size_t(1) << lg) * sizeof(float2);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+        const Grid G = make_grid((A.n + NT - 1) / NT, A.num_sms, NT);
+        Csr<IdxT> P = make_csr<IdxT>(A);
+        use_policy_copy(P, A);
+        kern<<<static_cast<unsigned>(n_blocks(G)), NT, smem, s>>>(P, G, A.band, lg, pi, V, r,
+                                                                  partials, st);
+        return cudaGetLastError();
+      }
+    }
+  }
   if constexpr (VW <= 4) {
     if (A.uniform_len == 4 * VW && A.vec4 && !A.val_lo && A.am_len == 0) {
       auto kern = k_policy_residual_fast<IdxT, VW>;
