@@ -40,7 +40,7 @@
  * Bellman residual, the outer iterate of mdp_solve and the refinement residual
  * are evaluated in float-float arithmetic (an unevaluated sum hi + lo of two
  * FP32 numbers, ~48 significant bits); the GMRES inner solve runs in FP32 (or
- * BF16/FP16 probabilities with a per-row FP32 renormalisation); the GMRES
+ * BF16/FP16 probabilities renormalised per row); the GMRES
  * Hessenberg/Givens least-squares and all norms run in FP64.
  */
 #ifndef MDP_GB300_MDP_H
@@ -174,8 +174,11 @@ typedef struct {
  *   cost      MDP_F32 or MDP_F64 [n*m], finite.
  *   gamma     discount factor, 0 <= gamma < 1.
  *   store_t   MDP_F32: inner solve on FP32 probabilities; MDP_BF16 / MDP_F16:
- *             also keep a 16-bit copy with per-row FP32 renormalisation
- *             c_r = 1 / sum_e q(P_e) for the low-precision inner solve.
+ *             also keep a 16-bit copy of the probabilities q(P_e) for the
+ *             low-precision inner solve, renormalised per row: when the band
+ *             fits int16 column offsets the packed copy divides each row sum
+ *             by sum_e q(P_e) on the fly (no stored factor); otherwise a
+ *             stored FP32 factor c_r = 1 / sum_e q(P_e) per row.
  *   stream    cudaStream_t (NULL = default stream); flags: MDP_FLAG_*.
  * Errors: MDP_ERR_ARG, MDP_ERR_BAD_CSR, MDP_ERR_NOT_STOCHASTIC, MDP_ERR_NONFINITE,
  * MDP_ERR_OOM, MDP_ERR_CUDA.  Synchronises the stream (validation result).
