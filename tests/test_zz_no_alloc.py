@@ -47,7 +47,8 @@ def test_noalloc_matches_handle_path_two_calls():
         a = V_out.double().cpu().numpy()
         b = ref["V"].double().cpu().numpy()
         assert np.max(np.abs(a - b)) <= 2 * tol
-        _, pi, Q, _ = oracle.bellman(mdp, Vd, want_q=True)
+        TV, pi, Q, _ = oracle.bellman(mdp, Vd, want_q=True)
+        assert np.max(np.abs(a - TV)) <= tol  # the oracle's FP64 T V itself
         check_greedy(pi_out.cpu().numpy(), pi, Q, tol)
         ra = r_out.double().cpu().numpy()
         rb = ref["r"].double().cpu().numpy()
