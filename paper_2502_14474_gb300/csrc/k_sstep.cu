@@ -302,7 +302,7 @@ constexpr int gram_vpg(int S) { return kGramCW * gram_vpw(S); }
 template <int S>
 __global__ void __launch_bounds__(kGramTh, 1)
     k_block_gram(int64_t n, int64_t states_per_slot, const float* __restrict__ basis, int64_t ld,
-                 int k, int sb, int restart, int nstages, int stg,
+                 int k, int sb, int restart, int nstages, int stg, int stall,
                  double* __restrict__ partials, DevState* __restrict__ st) {
   if (!st->active) return;
   constexpr int NW = kGramCW, VPW = gram_vpw(S);
@@ -346,8 +346,10 @@ __global__ void __launch_bounds__(kGramTh, 1)
   }
   if (warp == NW) {
     // ---- producer: stage c into buffer c % nstages once its last reader left
+    // (`stall`, a test of the bounded waits: no stage is ever armed, so every
+    // consumer's wait runs out and the launch reports it)
     int64_t issued = 0;
-    for (int64_t c = 0; c < nch; ++c) {
+    for (int64_t c = 0; c < (stall ? 0 : nch); ++c) {
       const int b = static_cast<int>(c % nstages);
       if (c >= nstages &&
           !mbar_wait(&empty[b], static_cast<unsigned>((c / nstages - 1) & 1), &s_abort)) {
@@ -675,8 +677,10 @@ cudaError_t block_gram_launch(const Mat& A, const float* basis, int64_t ld, int 
     return true;
   }();
   (void)attr;
+  // MDP_TEST_STALL_GRAM: the failure test of the bounded barrier waits
+  const int stall = getenv("MDP_TEST_STALL_GRAM") ? 1 : 0;
   k_block_gram<S><<<dim3(static_cast<unsigned>(used), static_cast<unsigned>(vg)), kGramTh, smem,
-                    s>>>(A.n, per, basis, ld, k, sb, restart, nstages, stg, partials, st);
+                    s>>>(A.n, per, basis, ld, k, sb, restart, nstages, stg, stall, partials, st);
   return cudaGetLastError();
 }
 
