@@ -28,7 +28,10 @@ namespace mdpk {
 // the row passes writes the m actions of 32/m consecutive states at once; with
 // stride = 32/m (mod 32) their 32 words fall in 32 different banks (a stride
 // that is a multiple of 32 put the m actions of a state in one bank).
+// Short tiles (many actions) keep the plain stride: the padding would add up
+// to 31 words per action to a tile of a few states.
 __host__ __device__ __forceinline__ int qtile_stride(int T, int m) {
+  if (T < 64) return T;
   const int target = (32 % m == 0) ? (32 / m) & 31 : 1;
   return T + (((target - T) % 32) + 32) % 32;
 }
@@ -1083,7 +1086,10 @@ static cudaError_t bellman_vw(const Mat& A, const void* V, void* V_out, int32_t*
     constexpr int NT = FF ? kWinFFThreads : 512;
     const int T = win_tile(NT, A.m, FF);
     const int lg = window_log2(A.band, T, FF ? 8 : 4, 128 * 1024);
-    if (lg > 0) {
+    // the ring and the Q tile must fit one CTA's shared memory (227 KB)
+    const size_t win_smem = (size_t(1) << lg) * (FF ? 8 : 4) +
+                            static_cast<size_t>(qtile_stride(T, A.m)) * A.m * (FF ? 8 : 4);
+    if (lg > 0 && win_smem <= 227 * 1024) {
       if constexpr (FF && VW <= 4) {
         if (screened(A, VW))
           return bellman_win<FF, IdxT, VW, NT, true>(A, lg, T, V, V_out, pi, r, partials, st,

@@ -79,6 +79,18 @@ def test_grid_world_small(path):
     _compare(mdp, V, path)
 
 
+@pytest.mark.parametrize("path", ["f32", "ff"])
+def test_many_actions(path):
+    """Short Q tiles: 40 actions on random rows (tiles of a few states, no
+    window) and 100 actions on banded rows (the shared-memory window with its
+    largest Q tile)."""
+    rng = np.random.default_rng(12)
+    for mdp in (synth.random_sparse(3001, 40, 6, 1.0, 0.95, seed=13, dtype=np.float32),
+                synth.banded(40000, 100, 16, 200, 0.5, 0.99, seed=14, dtype=np.float32)):
+        V = rng.random(mdp.n) * 20
+        _compare(mdp, V, path)
+
+
 def test_ties_take_lowest_action():
     rng = np.random.default_rng(5)
     n, m = 300, 6
